@@ -1,0 +1,99 @@
+"""Seeded input generators: published SplitMix64 vectors, determinism, shapes."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2203_13005_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_published_vectors():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "splitmix64.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for seed, i, val in rows:
+        assert synth.u64(int(seed), int(i)) == int(val)
+
+
+def test_stream_matches_scalar():
+    s = synth.stream_u64(99, 5, 7)
+    assert [int(x) for x in s] == [synth.u64(99, 5 + i) for i in range(7)]
+    u = synth.stream_unit(99, 5, 7)
+    assert np.all((u >= 0) & (u < 1))
+    assert np.array_equal(u, (s >> np.uint64(11)).astype(np.float64) * 2.0**-53)
+
+
+def test_rmat_deterministic_and_shaped():
+    s1, d1 = synth.rmat(12, 1 << 16, 7)
+    s2, d2 = synth.rmat(12, 1 << 16, 7)
+    assert np.array_equal(s1, s2) and np.array_equal(d1, d2)
+    assert s1.max() < 4096 and d1.max() < 4096
+    # top bit of (src, dst) follows the quadrant probabilities (a, b, c, d)
+    top_s = (s1 >> 11) & 1
+    top_d = (d1 >> 11) & 1
+    n = len(s1)
+    frac = {q: np.mean((top_s == q[0]) & (top_d == q[1])) for q in [(0, 0), (0, 1), (1, 0), (1, 1)]}
+    assert abs(frac[(0, 0)] - 0.57) < 0.01
+    assert abs(frac[(0, 1)] - 0.19) < 0.01
+    assert abs(frac[(1, 0)] - 0.19) < 0.01
+    assert abs(frac[(1, 1)] - 0.05) < 0.01
+    s3, _ = synth.rmat(12, 1 << 16, 8)
+    assert not np.array_equal(s1, s3)
+
+
+def test_rmat_prefix_stable():
+    # edge i depends only on (seed, i): a shorter run is a prefix of a longer one
+    s1, d1 = synth.rmat(10, 1000, 3)
+    s2, d2 = synth.rmat(10, 5000, 3)
+    assert np.array_equal(s1, s2[:1000]) and np.array_equal(d1, d2[:1000])
+
+
+def test_er_symmetric_no_self_loops():
+    s, d = synth.erdos_renyi(1000, 20000, 11)
+    assert len(s) == 40000
+    assert np.all(s != d)
+    assert np.array_equal(s[0::2], d[1::2]) and np.array_equal(d[0::2], s[1::2])
+    assert s.max() < 1000
+    # uniform endpoints: each vertex appears ~40 times
+    c = np.bincount(s, minlength=1000)
+    assert 20 < c.mean() < 60
+
+
+def test_er_tiny_n():
+    s, d = synth.erdos_renyi(2, 100, 5)
+    assert np.all(s != d) and set(np.unique(s)) <= {0, 1}
+
+
+def test_weights_range():
+    w = synth.weights(100000, 1, 100, 3)
+    assert w.min() == 1 and w.max() == 100
+    assert abs(w.mean() - 50.5) < 0.5
+
+
+def test_sample_sources():
+    s, d = synth.rmat(10, 1 << 14, 1)
+    src = synth.sources_with_out_edges(1024, s, 64, 4)
+    assert len(set(src.tolist())) == 64
+    outdeg = np.bincount(s, minlength=1024)
+    assert np.all(outdeg[src] > 0)
+    assert np.array_equal(src, synth.sources_with_out_edges(1024, s, 64, 4))
+    with pytest.raises(ValueError):
+        synth.sample_vertices(10, np.zeros(10, dtype=bool), 1, 0)
+
+
+def test_poisson_arrivals():
+    t = synth.poisson_arrivals(2000.0, 2.0, 5)
+    assert np.all(np.diff(t) > 0) and t[-1] < 2.0
+    assert abs(len(t) - 4000) < 4 * np.sqrt(4000)
+
+
+def test_workload_sizes():
+    w = synth.SSSP_RMAT16
+    assert (w.n_vertices, w.n_edges, w.w_lo, w.w_hi) == (65536, 1048576, 1, 100)
+    assert synth.PAGERANK_RMAT22.n_vertices == 4194304 and synth.PAGERANK_RMAT22.n_edges == 67108864
+    assert synth.CC_ER24_P8.n_edges == 268435456 and synth.CC_ER24_P8.parts == 8
+    assert synth.MSSSP_RMAT24.n_vertices == 16777216 and synth.MSSSP_RMAT24.w_hi == 255
+    small = w.scaled(8)
+    assert small.n_vertices == 256 and small.n_edges == 4096
