@@ -1,0 +1,315 @@
+"""Benchmark of the GAS superstep engine: PageRank on R-MAT scale 22.
+
+One step = one complete PageRank run through the C-ABI (gxp_begin + 20
+supersteps of MSGGen/MSGMerge/MSGApply) on 4,194,304 vertices and 67,108,864
+edges, d = 0.85. The metric is GTEPS (edges scanned per second over all
+supersteps) and the HBM-roofline fraction of the superstep kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gxp|reference]
+
+--impl reference times the CPU oracle (the plain fp64 C loop) on a bounded
+sample of the same workload: each step is one full-graph PageRank superstep.
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+REPO = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, REPO)
+
+from paper_2203_13005_gb300 import synth  # noqa: E402
+
+METRIC = "GTEPS & % HBM roofline per GAS superstep"
+ITERS = 20
+DAMPING = 0.85
+WL = synth.PAGERANK_RMAT22
+PROFILE = os.path.join(REPO, "profiles", "superstep_pagerank_rmat22.txt")
+KERNEL_SRC = os.path.join(REPO, "paper_2203_13005_gb300", "csrc", "superstep.cu")
+
+
+def algorithmic_bytes(n_vertices: int, n_edges: int) -> int:
+    """Bytes one PageRank superstep must move at minimum: per edge the source
+    index (4) and the gathered contribution (4); per vertex col_ptr (4),
+    out-degree (4), old rank (4), new rank (4), new contribution (4)."""
+    return 8 * n_edges + 20 * n_vertices
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(REPO, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (its sha256 is recorded there); else None."""
+    if not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    for ln in open(PROFILE):
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if kv.get("kernel_source_sha256") != sha or "dram_bytes_per_launch" not in kv:
+        return None
+    return float(kv["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, single-threaded fp64 C, on host cores."""
+    if rank != 0:
+        return
+    import oracle
+    src, dst, _ = WL.edges()
+    n, m = WL.n_vertices, WL.n_edges
+    outdeg_unused = None  # noqa: F841  (the oracle counts out-degrees itself)
+    r = np.full(n, 1.0 / n)
+    for _ in range(args.warmup):
+        r, _, _ = oracle.pagerank_step(n, src, dst, r, DAMPING)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, _, _ = oracle.pagerank_step(n, src, dst, r, DAMPING)
+    dt = time.perf_counter() - t0
+    gteps = args.steps * m / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WL.name, "vertices": n, "edges": m, "damping": DAMPING,
+                   "step": "one PageRank superstep over the full graph (oracle)"},
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full-graph fp64 supersteps of {WL.name}"},
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(src, dst, n, m):
+    """Oracle PageRank on this host: a bounded sample of 3 full-graph supersteps."""
+    import oracle
+    k = 3
+    t0 = time.perf_counter()
+    oracle.pagerank(n, src, dst, DAMPING, k)
+    dt = time.perf_counter() - t0
+    return {"value": k * m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{k} fp64 supersteps of {WL.name} (single thread, incl. its out-degree pass)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gxp", choices=["gxp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2203_13005_gb300 import gxp
+
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    src, dst, _ = WL.edges()
+    n, m = WL.n_vertices, WL.n_edges
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(src, dst, n, m)
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = gxp.Context(local)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.create_graph(n, 1)
+    ctx.load_coo(src, dst)
+    g, mm, a = gxp.TEMPLATES[gxp.GXP_ALGO_PAGERANK]
+    lib, h = ctx.lib, ctx.h
+
+    def one_step(evs=None):
+        rc = lib.gxp_begin(h, gxp.GXP_ALGO_PAGERANK, 0, DAMPING)
+        if rc:
+            ctx._ck(rc)
+        for i in range(ITERS):
+            if evs is not None:
+                evs[i][0].record(stream)
+            rc = lib.gxp_superstep(h, gxp.GXP_ALGO_PAGERANK, g, mm, a, None)
+            if rc:
+                ctx._ck(rc)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    torch.cuda.synchronize()
+    # per-superstep kernel events of every timed step
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(ITERS)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for s in range(args.steps):
+            one_step(evs[s])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms_total = t_start.elapsed_time(t_end)
+    kernel_ms = [b.elapsed_time(e) for step in evs for (b, e) in step]
+    if pg:
+        t = torch.tensor([ms_total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    gteps = world * ITERS * m / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: CSC from pinned host
+    # memory -> load -> 20 supersteps -> ranks back into pinned host memory
+    order = np.argsort(dst, kind="stable")
+    col_ptr = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+    np.cumsum(np.bincount(dst, minlength=n), out=col_ptr.numpy()[1:])
+    csc_src = torch.from_numpy(np.ascontiguousarray(src[order]).view(np.int32)).pin_memory()
+    ranks_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    del order
+    e2e_times = []
+    ctx2 = gxp.Context(local)
+    ctx2.set_stream(stream.cuda_stream)
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.create_graph(n, 1)
+        ctx2.load_partition(0, gxp.GXP_FMT_CSC, m, col_ptr, csc_src)
+        ctx2.run(gxp.GXP_ALGO_PAGERANK, damping=DAMPING, max_steps=ITERS)
+        ctx2.values(out=ranks_h)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times)
+    ctx2.close()
+
+    if rank == 0:
+        peaks = measured_peaks()
+        bytes_launch = algorithmic_bytes(n, m)
+        avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
+        achieved = bytes_launch / avg_kernel_s / 1e9
+        traffic = profiled_traffic()
+        line = {
+            "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WL.name, "vertices": n, "edges": m, "supersteps_per_step": ITERS,
+                       "damping": DAMPING, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2: 256 MiB of edge indices per superstep vs 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_launch,
+                         "kernel": "k_superstep<PR>", "avg_launch_us": avg_kernel_s * 1e6},
+            "e2e": {"value": ITERS * m / e2e_s / 1e9, "unit": "GTEPS",
+                    "h2d_bytes_per_step": 8 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n,
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": args.steps * (ITERS + 1),
+            "clocks": clk.summary(),
+        }
+        if base is not None:
+            line["cpu_baseline"] = base
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * gxp.h — C-ABI of the GB300 GAS superstep engine (libgxp.so).
+ *
+ * The engine runs the per-superstep iteration of GX-Plug's daemon
+ * (Section II-A1 and IV-A1: the algorithm template MSGGen / MSGMerge /
+ * MSGApply) over graph partitions held on one GPU, with the paper's
+ * synchronization caching and skipping between partitions (Section III-B,
+ * Algorithm 3) and its pipeline shuffle for edge blocks streamed from host
+ * memory (Section III-A, Algorithms 1-2, Lemma 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns gxp_status; none aborts, throws or exits.
+ *   gxp_status_string() names a code; gxp_last_error() gives the detail of
+ *   the last failure on a context.
+ * - Validation errors (GXP_E_INVAL, GXP_E_UNSUPPORTED, GXP_E_STATE) are
+ *   returned synchronously and leave the context unchanged.
+ * - Errors raised asynchronously on the GPU (a CUDA fault, a device-side
+ *   bounds check, a device wait that ran out of time) are returned by the
+ *   next call that synchronizes with the device. After GXP_E_CUDA,
+ *   GXP_E_TIMEOUT or GXP_E_BOUNDS the context is poisoned: later calls return
+ *   GXP_E_STATE until gxp_destroy().
+ * - Pointers: unless a flag says otherwise, array arguments may be host or
+ *   device pointers (the library copies through unified addressing). Input
+ *   arrays are copied; the caller keeps ownership and may free them when the
+ *   call returns. Output arrays are caller-allocated.
+ * - Vertex ids are uint32 (at most 2^32 - 2 vertices: 0xFFFFFFFF is the
+ *   "infinite" distance of SSSP); edge counts are uint64, at most 2^32 - 1
+ *   edges per partition.
+ * - One host thread at a time per context, except gxp_query_submit /
+ *   gxp_query_poll, which are thread-safe.
+ */
+#ifndef GXP_H
+#define GXP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GXP_API __attribute__((visibility("default")))
+
+typedef enum gxp_status {
+    GXP_OK = 0,
+    GXP_E_INVAL = 1,        /* bad argument: null pointer, size, range, format */
+    GXP_E_NOMEM = 2,        /* device or pinned host allocation failed, or over mem_budget */
+    GXP_E_CUDA = 3,         /* a CUDA runtime call or kernel failed */
+    GXP_E_TIMEOUT = 4,      /* a device-side wait exceeded timeout_ns */
+    GXP_E_BOUNDS = 5,       /* a device-side bounds check found an out-of-range index */
+    GXP_E_STATE = 6,        /* call out of order, or context poisoned by an earlier error */
+    GXP_E_UNSUPPORTED = 7,  /* valid but not implemented combination */
+    GXP_E_BUSY = 8          /* no free query slot / queue full (serving) */
+} gxp_status;
+
+typedef enum gxp_algo {
+    GXP_ALGO_SSSP = 0,      /* Bellman-Ford shortest paths (Section V-A) */
+    GXP_ALGO_CC = 1,        /* min-label propagation = weakly connected components */
+    GXP_ALGO_PAGERANK = 2,  /* PageRank with dangling-mass redistribution */
+    GXP_ALGO_PPR = 3        /* personalized PageRank (serving and batches only) */
+} gxp_algo;
+
+/* The three template functions of Section IV-A1, as built-in operators. */
+typedef enum gxp_msggen {
+    GXP_GEN_RELAX = 0,      /* m = d[u] + w(u,v), saturating at 0xFFFFFFFE; none if d[u] = INF */
+    GXP_GEN_LABEL = 1,      /* m = l[u] */
+    GXP_GEN_CONTRIB = 2     /* m = r[u] / outdeg(u), fp32 */
+} gxp_msggen;
+
+typedef enum gxp_merge {
+    GXP_MERGE_MIN = 0,      /* uint32 minimum, exact */
+    GXP_MERGE_SUM = 1       /* fp32 sum in a fixed order (deterministic) */
+} gxp_merge;
+
+typedef enum gxp_apply {
+    GXP_APPLY_MIN = 0,      /* x' = min(x, m); changed if x' != x */
+    GXP_APPLY_PAGERANK = 1  /* r' = (1-d)/N + d (m + D/N), D = dangling mass */
+} gxp_apply;
+
+typedef enum gxp_format {
+    GXP_FMT_COO = 0,        /* idx0 = src[n_edges] (uint32 global), idx1 = dst[n_edges] (uint32 global) */
+    GXP_FMT_CSC = 1,        /* idx0 = col_ptr[n_local + 1] (uint64, starts at 0), idx1 = src[n_edges] (uint32 global);
+                               edges of local dst v are src[col_ptr[v] .. col_ptr[v+1]) */
+    GXP_FMT_CSR = 2         /* idx0 = row_ptr[n_vertices + 1] (uint64) over global sources,
+                               idx1 = dst[n_edges] (uint32 global, all inside the partition) */
+} gxp_format;
+
+typedef enum gxp_dtype { GXP_U32 = 0, GXP_F32 = 1, GXP_F64 = 2 } gxp_dtype;
+
+typedef struct gxp_config {
+    uint64_t mem_budget;        /* bytes of device memory the context may hold; 0 = no limit */
+    uint32_t tile_items;        /* merge items (vertices + edges) per edge block; 0 = 2048 */
+    uint32_t hub_items;         /* vertices with more in-edges than this are split across
+                                   blocks; 0 = tile_items / 2 */
+    uint64_t timeout_ns;        /* limit for any device-side wait; 0 = 2e9 (2 s) */
+    uint32_t check_bounds;      /* 1: kernels range-check every gathered index */
+    uint32_t max_slots;         /* query slots for serving / batches; 0 = 64 */
+    uint32_t pipeline_depth;    /* ring slots of the pipeline shuffle; 0 = 3 */
+    uint32_t reserved[7];
+} gxp_config;
+
+/* Fill *cfg with the defaults above (all zero = defaults). */
+GXP_API void gxp_config_default(gxp_config* cfg);
+
+typedef struct gxp_ctx gxp_ctx;
+
+typedef struct gxp_stats {
+    uint64_t supersteps;            /* supersteps run since the last gxp_begin */
+    uint64_t edges_scanned;         /* edges read by supersteps since gxp_begin */
+    uint64_t last_changed;          /* vertices changed by the last superstep */
+    uint64_t last_boundary_changed; /* of which boundary vertices uploaded by its sync */
+    uint64_t syncs_done;            /* exchanges performed (Algorithm 3) */
+    uint64_t syncs_skipped;         /* exchanges skipped (Section III-B3) */
+    uint64_t sync_pairs;            /* (id, value) pairs moved by all syncs */
+    double   last_l1_delta;         /* PageRank: sum |r_{t+1} - r_t| of the last superstep */
+    double   last_dangling;         /* PageRank: dangling mass D of the current ranks */
+    double   last_superstep_ms;     /* device time of the last superstep incl. its sync */
+    uint64_t device_bytes;          /* device memory held by the context */
+    uint64_t reserved[6];
+} gxp_stats;
+
+/* ------------------------------------------------------------ lifecycle -- */
+
+/* Create a context on CUDA device `device` (Section IV-C: the device is
+ * initialised once and reused by every later call). cfg may be NULL. */
+GXP_API gxp_status gxp_init(int device, const gxp_config* cfg, gxp_ctx** out);
+
+/* Release every resource of the context. NULL is a no-op. */
+GXP_API void gxp_destroy(gxp_ctx* ctx);
+
+GXP_API const char* gxp_status_string(gxp_status s);
+GXP_API const char* gxp_last_error(const gxp_ctx* ctx);
+
+/* Use `stream` (a cudaStream_t, or NULL for the context's own stream) for
+ * all later device work of the context. */
+GXP_API gxp_status gxp_set_stream(gxp_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------- graph -- */
+
+/* Declare the graph: n_vertices in total, split into n_parts partitions that
+ * own contiguous destination-id ranges [part_begin[p], part_begin[p+1])
+ * (Section II-B: the upper system partitions the graph across nodes).
+ * part_begin has n_parts + 1 entries, part_begin[0] = 0,
+ * part_begin[n_parts] = n_vertices, non-decreasing; NULL = even split.
+ * Drops any previously loaded graph. */
+GXP_API gxp_status gxp_create_graph(gxp_ctx* ctx, uint64_t n_vertices, uint32_t n_parts,
+                                    const uint64_t* part_begin);
+
+/* Load the in-edges of partition `part` (every edge whose destination the
+ * partition owns) in format `fmt` (see gxp_format), with optional uint32
+ * weights (NULL = unweighted; weights are in the order of idx1 for CSC/CSR and
+ * of the edge list for COO). The engine builds its dst-sorted edge blocks and
+ * the vertex-edge mapping table from it (Section II-B: fixed-size edge blocks
+ * paired with vertex blocks). Ownership of the arrays stays with the caller.
+ * Errors: GXP_E_INVAL for an out-of-range id, a destination outside the
+ * partition, a non-monotone offset array, or more than 2^32-1 edges. */
+GXP_API gxp_status gxp_load_partition(gxp_ctx* ctx, uint32_t part, gxp_format fmt,
+                                      uint64_t n_edges, const void* idx0, const uint32_t* idx1,
+                                      const uint32_t* weights);
+
+/* ------------------------------------------------------- vertex values -- */
+
+/* Start an algorithm: set every partition's vertex values to its initial
+ * state — SSSP: d[source] = 0, else 0xFFFFFFFF; CC: l[v] = v; PageRank:
+ * r[v] = 1/N — and reset the superstep counters. `source` is ignored for CC
+ * and PageRank. damping is used by PageRank/PPR (e.g. 0.85). Builds the
+ * partition caches (ghost/mirror tables) on first use. */
+GXP_API gxp_status gxp_begin(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping);
+
+/* Copy the current values of the vertices owned by `part` (in local order,
+ * n = owned count) to `out`: uint32 for SSSP/CC, fp32 ranks for PageRank.
+ * part = UINT32_MAX copies all partitions in global id order (n = n_vertices). */
+GXP_API gxp_status gxp_get_values(gxp_ctx* ctx, uint32_t part, void* out, uint64_t n);
+
+/* Overwrite the current values (same layout as gxp_get_values) and mark every
+ * vertex changed, e.g. to resume from a checkpoint. Requires gxp_begin. */
+GXP_API gxp_status gxp_set_values(gxp_ctx* ctx, uint32_t part, const void* in, uint64_t n);
+
+/* ------------------------------------------------------------ superstep -- */
+
+/* One superstep over every partition (Section IV-A1, BSP order Gen -> Merge
+ * -> Apply): for each in-edge (u, v) of each owned vertex v, generate a
+ * message from u's value (msggen), combine the messages by destination
+ * (merge), then apply the result to v's value (apply), marking v in the
+ * changed-vertex bitmap when its value changes. With more than one
+ * partition it then synchronizes: each partition uploads only its changed
+ * boundary vertices (lazy uploading, Algorithm 3) into the caches of the
+ * others, and the exchange is skipped when there are none anywhere
+ * (Section III-B3). Supported templates: SSSP = (RELAX, MIN, MIN),
+ * CC = (LABEL, MIN, MIN), PageRank = (CONTRIB, SUM, PAGERANK); others return
+ * GXP_E_UNSUPPORTED. `algo` must match gxp_begin. If n_changed is non-NULL
+ * the call waits for the device and stores the number of vertices whose
+ * value changed; otherwise it returns once the work is enqueued. */
+GXP_API gxp_status gxp_superstep(gxp_ctx* ctx, gxp_algo algo, gxp_msggen msggen,
+                                 gxp_merge merge, gxp_apply apply, uint64_t* n_changed);
+
+/* The global data queue entries of partition `part` from the last superstep
+ * (Algorithm 3): the (id, value) pairs of its vertices that changed and are
+ * cached by another partition, ascending by global id. *n_out receives the
+ * count; if it exceeds `cap` nothing is copied and GXP_E_INVAL is returned.
+ * *skipped (nullable) is 1 when the last exchange was skipped (no partition
+ * had a changed boundary vertex). ids: uint32[cap]; vals: uint32 or fp32[cap].
+ * Either of ids / vals may be NULL when cap is 0 (count query). */
+GXP_API gxp_status gxp_sync(gxp_ctx* ctx, uint32_t part, uint32_t* ids, void* vals,
+                            uint64_t cap, uint64_t* n_out, int* skipped);
+
+/* Iteration control (Section II-C2): run supersteps until one changes no
+ * vertex (SSSP, CC) or exactly max_steps of them (PageRank). Starts with
+ * gxp_begin(algo, source, damping). *steps_done (nullable) counts supersteps
+ * run, including the final one that changed nothing. */
+GXP_API gxp_status gxp_run(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping,
+                           uint32_t max_steps, uint32_t* steps_done);
+
+GXP_API gxp_status gxp_stats_get(gxp_ctx* ctx, gxp_stats* out);
+
+/* ----------------------------------------------- block-size model (a8) -- */
+
+/* Lemma 1 (Section III-A, "Block Size Selection"): with per-entity download,
+ * compute and upload costs k1, k2, k3, per-block call cost a and d entities,
+ * return the integer block size *b and count *s (s >= 2) that minimise the
+ * pipeline-time equation among the rounded candidates floor/ceil(s_opt) and
+ * floor/ceil(b_opt), and the equation's estimate *t. Host-only arithmetic. */
+GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double a, uint64_t d,
+                                        uint64_t* b, uint64_t* s, double* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GXP_H */

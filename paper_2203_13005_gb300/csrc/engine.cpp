@@ -1,0 +1,655 @@
+// Host runtime of the superstep engine: graph loading (COO/CSC/CSR -> per
+// partition dst-sorted CSC with local source ids), device residency, the
+// superstep/sync/iteration control (Section II-C), and statistics.
+#include "engine.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+namespace gxp {
+
+void fail(gxp_status code, const std::string& msg) { throw Error{code, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();   // clear the non-sticky allocation error
+        fail(GXP_E_NOMEM, std::string(what) + ": out of device memory");
+    }
+    fail(GXP_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+constexpr uint32_t kDefaultTile = 2048;
+
+inline size_t pad4(size_t n) { return ((n + 3) & ~size_t(3)) + 4; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ setup
+
+Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
+    gxp_config_default(&cfg_);
+    if (cfg) cfg_ = *cfg;
+    if (cfg_.tile_items == 0) cfg_.tile_items = kDefaultTile;
+    if (cfg_.hub_items == 0) cfg_.hub_items = cfg_.tile_items / 4;
+    if (cfg_.hub_items >= cfg_.tile_items) cfg_.hub_items = cfg_.tile_items - 1;
+    if (cfg_.timeout_ns == 0) cfg_.timeout_ns = 2000000000ull;
+    if (cfg_.max_slots == 0) cfg_.max_slots = 64;
+    if (cfg_.pipeline_depth == 0) cfg_.pipeline_depth = 3;
+    if ((uint64_t)cfg_.tile_items + cfg_.hub_items > (uint64_t)kMaxTileItems)
+        fail(GXP_E_INVAL, "tile_items + hub_items must not exceed " + std::to_string(kMaxTileItems));
+    int n_dev = 0;
+    cuda_check(cudaGetDeviceCount(&n_dev), "cudaGetDeviceCount");
+    if (device < 0 || device >= n_dev) fail(GXP_E_INVAL, "no such CUDA device");
+    cuda_check(cudaSetDevice(device), "cudaSetDevice");
+    cuda_check(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking), "cudaStreamCreate");
+    stream_ = own_stream_;
+    cuda_check(cudaEventCreate(&ev_a_), "cudaEventCreate");
+    cuda_check(cudaEventCreate(&ev_b_), "cudaEventCreate");
+}
+
+Engine::~Engine() {
+    cudaSetDevice(device_);
+    if (stream_) cudaStreamSynchronize(stream_);
+    free_graph_device();
+    if (ev_a_) cudaEventDestroy(ev_a_);
+    if (ev_b_) cudaEventDestroy(ev_b_);
+    if (own_stream_) cudaStreamDestroy(own_stream_);
+}
+
+void* Engine::dalloc(size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    if (cfg_.mem_budget && graph_bytes_ + bytes > cfg_.mem_budget)
+        fail(GXP_E_NOMEM, "allocation exceeds the context's mem_budget");
+    void* p = nullptr;
+    cuda_check(cudaMalloc(&p, bytes), "cudaMalloc");
+    graph_allocs_.push_back(p);
+    graph_bytes_ += bytes;
+    return p;
+}
+
+void Engine::free_graph_device() {
+    for (void* p : graph_allocs_) cudaFree(p);
+    graph_allocs_.clear();
+    graph_bytes_ = 0;
+    for (auto& hp : parts_) {
+        hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
+    }
+    finalized_ = false;
+    begun_ = false;
+}
+
+void Engine::copy_in(void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return;
+    if (is_device_ptr(src)) cuda_check(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost), "copy input");
+    else std::memcpy(dst, src, bytes);
+}
+
+void Engine::check_device_error() {
+    uint32_t err = 0;
+    if (d_err_) cuda_check(cudaMemcpy(&err, d_err_, 4, cudaMemcpyDeviceToHost), "read error word");
+    if (err & kErrTimeout) fail(GXP_E_TIMEOUT, "a device-side wait exceeded timeout_ns");
+    if (err & kErrBounds) fail(GXP_E_BOUNDS, "a device-side bounds check failed");
+}
+
+// ------------------------------------------------------------------ graph
+
+void Engine::create_graph(uint64_t n, uint32_t n_parts, const uint64_t* part_begin) {
+    if (n == 0 || n >= 0xFFFFFFFFull) fail(GXP_E_INVAL, "n_vertices must be in [1, 2^32 - 2]");
+    if (n_parts == 0 || n_parts > 4096) fail(GXP_E_INVAL, "n_parts must be in [1, 4096]");
+    std::vector<uint64_t> b(n_parts + 1);
+    if (part_begin) {
+        std::vector<uint64_t> tmp(n_parts + 1);
+        copy_in(tmp.data(), part_begin, sizeof(uint64_t) * (n_parts + 1));
+        b = tmp;
+        if (b[0] != 0 || b[n_parts] != n) fail(GXP_E_INVAL, "part_begin must start at 0 and end at n_vertices");
+        for (uint32_t p = 0; p < n_parts; ++p)
+            if (b[p + 1] < b[p]) fail(GXP_E_INVAL, "part_begin must be non-decreasing");
+    } else {
+        for (uint32_t p = 0; p <= n_parts; ++p) b[p] = n * p / n_parts;
+    }
+    if (stream_) cudaStreamSynchronize(stream_);
+    free_graph_device();
+    parts_.assign(n_parts, HostPart{});
+    for (uint32_t p = 0; p < n_parts; ++p) {
+        parts_[p].v_begin = (uint32_t)b[p];
+        parts_[p].n_own = (uint32_t)(b[p + 1] - b[p]);
+    }
+    n_vertices_ = n;
+    n_parts_ = n_parts;
+    have_graph_ = true;
+}
+
+// Build a partition from its dst-sorted in-edge lists with global source ids.
+static void build_local(HostPart& hp, uint64_t n_vertices, bool many_parts,
+                        std::vector<uint32_t>&& col_ptr, std::vector<uint32_t>&& gsrc,
+                        std::vector<uint32_t>&& w) {
+    const uint32_t lo = hp.v_begin, hi = hp.v_begin + hp.n_own;
+    hp.ghost_gid.clear();
+    if (many_parts) {
+        // cached remote sources: sorted unique ids outside [lo, hi)
+        const size_t words = (n_vertices + 63) / 64;
+        std::vector<uint64_t> mark(words, 0);
+        for (uint32_t g : gsrc)
+            if (g < lo || g >= hi) mark[g >> 6] |= 1ull << (g & 63);
+        std::vector<uint32_t> rank(words + 1, 0);
+        for (size_t i = 0; i < words; ++i) rank[i + 1] = rank[i] + (uint32_t)__builtin_popcountll(mark[i]);
+        hp.ghost_gid.reserve(rank[words]);
+        for (size_t i = 0; i < words; ++i) {
+            uint64_t m = mark[i];
+            while (m) {
+                const int b = __builtin_ctzll(m);
+                m &= m - 1;
+                hp.ghost_gid.push_back((uint32_t)(i * 64 + b));
+            }
+        }
+        for (uint32_t& g : gsrc) {
+            if (g >= lo && g < hi) {
+                g -= lo;
+            } else {
+                const uint64_t bits = mark[g >> 6] & ((1ull << (g & 63)) - 1ull);
+                g = hp.n_own + rank[g >> 6] + (uint32_t)__builtin_popcountll(bits);
+            }
+        }
+    } else {
+        for (uint32_t& g : gsrc) g -= lo;   // lo == 0, every source is owned
+    }
+    hp.col_ptr = std::move(col_ptr);
+    hp.src = std::move(gsrc);
+    hp.w = std::move(w);
+    hp.loaded = true;
+}
+
+void Engine::load_partition(uint32_t part, gxp_format fmt, uint64_t n_edges, const void* idx0,
+                            const uint32_t* idx1, const uint32_t* weights) {
+    if (!have_graph_) fail(GXP_E_STATE, "gxp_create_graph must come first");
+    if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
+    if (n_edges > 0xFFFFFFFFull) fail(GXP_E_INVAL, "more than 2^32-1 edges in one partition");
+    if (n_edges && (!idx0 || !idx1)) fail(GXP_E_INVAL, "null edge array");
+    HostPart& hp = parts_[part];
+    const uint32_t lo = hp.v_begin, n_own = hp.n_own;
+    const uint64_t V = n_vertices_;
+    std::vector<uint32_t> col_ptr(n_own + 1, 0), gsrc(n_edges), w;
+    if (weights) w.resize(n_edges);
+
+    if (fmt == GXP_FMT_COO || fmt == GXP_FMT_CSR) {
+        std::vector<uint32_t> src(n_edges), dst(n_edges), win;
+        if (fmt == GXP_FMT_COO) {
+            if (n_edges == 0 && idx0 == nullptr) {
+            } else {
+                copy_in(src.data(), idx0, 4 * n_edges);
+            }
+        } else {
+            std::vector<uint64_t> row_ptr(V + 1);
+            copy_in(row_ptr.data(), idx0, 8 * (V + 1));
+            if (row_ptr[0] != 0 || row_ptr[V] != n_edges) fail(GXP_E_INVAL, "CSR row_ptr must run from 0 to n_edges");
+            for (uint64_t u = 0; u < V; ++u) {
+                if (row_ptr[u + 1] < row_ptr[u]) fail(GXP_E_INVAL, "CSR row_ptr not monotone");
+                for (uint64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) src[e] = (uint32_t)u;
+            }
+        }
+        if (n_edges) copy_in(dst.data(), idx1, 4 * n_edges);
+        if (weights) {
+            win.resize(n_edges);
+            copy_in(win.data(), weights, 4 * n_edges);
+        }
+        for (uint64_t e = 0; e < n_edges; ++e) {
+            if (src[e] >= V) fail(GXP_E_INVAL, "source id out of range");
+            if (dst[e] < lo || dst[e] - lo >= n_own) fail(GXP_E_INVAL, "destination outside the partition");
+            col_ptr[dst[e] - lo + 1]++;
+        }
+        for (uint32_t v = 0; v < n_own; ++v) col_ptr[v + 1] += col_ptr[v];
+        std::vector<uint32_t> pos(col_ptr.begin(), col_ptr.end() - 1);
+        for (uint64_t e = 0; e < n_edges; ++e) {   // stable counting sort by destination
+            const uint32_t p = pos[dst[e] - lo]++;
+            gsrc[p] = src[e];
+            if (weights) w[p] = win[e];
+        }
+    } else if (fmt == GXP_FMT_CSC) {
+        std::vector<uint64_t> cp(n_own + 1);
+        copy_in(cp.data(), idx0, 8 * (size_t)(n_own + 1));
+        if (cp[0] != 0 || cp[n_own] != n_edges) fail(GXP_E_INVAL, "CSC col_ptr must run from 0 to n_edges");
+        for (uint32_t v = 0; v < n_own; ++v) {
+            if (cp[v + 1] < cp[v]) fail(GXP_E_INVAL, "CSC col_ptr not monotone");
+            col_ptr[v + 1] = (uint32_t)cp[v + 1];
+        }
+        if (n_edges) copy_in(gsrc.data(), idx1, 4 * n_edges);
+        if (weights) copy_in(w.data(), weights, 4 * n_edges);
+        for (uint64_t e = 0; e < n_edges; ++e)
+            if (gsrc[e] >= V) fail(GXP_E_INVAL, "source id out of range");
+    } else {
+        fail(GXP_E_INVAL, "unknown format");
+    }
+    if (stream_) cudaStreamSynchronize(stream_);
+    if (finalized_) free_graph_device();
+    build_local(hp, V, n_parts_ > 1, std::move(col_ptr), std::move(gsrc), std::move(w));
+}
+
+// Upload every partition, cut edge blocks, count out-degrees, build caches.
+void Engine::finalize() {
+    for (uint32_t p = 0; p < n_parts_; ++p)
+        if (!parts_[p].loaded) fail(GXP_E_STATE, "partition " + std::to_string(p) + " not loaded");
+    cuda_check(cudaStreamSynchronize(stream_), "sync");
+    free_graph_device();
+    const uint32_t V = (uint32_t)n_vertices_;
+    const uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
+    max_items_ = T + H;
+
+    n_tiles_ = 0;
+    n_ghost_total_ = 0;
+    total_edges_ = 0;
+    weighted_ = true;
+    uint32_t max_nt = 0;
+    for (auto& hp : parts_) {
+        hp.n_tiles = tile_count(hp.n_own, hp.src.size(), T);
+        hp.tile_base = n_tiles_;
+        n_tiles_ += hp.n_tiles;
+        max_nt = std::max(max_nt, hp.n_tiles);
+        hp.ghost_base = n_ghost_total_;
+        if ((uint64_t)n_ghost_total_ + hp.ghost_gid.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many cached vertices");
+        n_ghost_total_ += (uint32_t)hp.ghost_gid.size();
+        total_edges_ += hp.src.size();
+        if (hp.w.empty() && !hp.src.empty()) weighted_ = false;
+    }
+    std::vector<PartDev> pd(n_parts_);
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        HostPart& hp = parts_[p];
+        const size_t ne = hp.src.size();
+        hp.d_col_ptr = (uint32_t*)dalloc(4 * pad4(hp.n_own + 1));
+        hp.d_src = (uint32_t*)dalloc(4 * pad4(ne));
+        cuda_check(cudaMemsetAsync(hp.d_col_ptr, 0, 4 * pad4(hp.n_own + 1), stream_), "memset");
+        cuda_check(cudaMemsetAsync(hp.d_src, 0, 4 * pad4(ne), stream_), "memset");
+        cuda_check(cudaMemcpyAsync(hp.d_col_ptr, hp.col_ptr.data(), 4 * (hp.n_own + 1), cudaMemcpyHostToDevice, stream_), "upload col_ptr");
+        if (ne) cuda_check(cudaMemcpyAsync(hp.d_src, hp.src.data(), 4 * ne, cudaMemcpyHostToDevice, stream_), "upload src");
+        if (!hp.w.empty()) {
+            hp.d_w = (uint32_t*)dalloc(4 * pad4(ne));
+            cuda_check(cudaMemsetAsync(hp.d_w, 0, 4 * pad4(ne), stream_), "memset");
+            cuda_check(cudaMemcpyAsync(hp.d_w, hp.w.data(), 4 * ne, cudaMemcpyHostToDevice, stream_), "upload w");
+        }
+        pd[p] = PartDev{hp.d_col_ptr, hp.d_src, hp.d_w, hp.n_own, hp.v_begin,
+                        (uint32_t)hp.ghost_gid.size(), hp.ghost_base, (uint64_t)ne};
+    }
+    d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
+    cuda_check(cudaMemcpyAsync(d_parts_, pd.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_), "upload parts");
+
+    d_ghost_gid_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
+    d_ghost_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
+    for (auto& hp : parts_)
+        if (!hp.ghost_gid.empty())
+            cuda_check(cudaMemcpyAsync(d_ghost_gid_ + hp.ghost_base, hp.ghost_gid.data(), 4 * hp.ghost_gid.size(),
+                                       cudaMemcpyHostToDevice, stream_), "upload ghost ids");
+
+    // edge blocks
+    d_tiles_ = (Tile*)dalloc(sizeof(Tile) * std::max<uint32_t>(n_tiles_, 1));
+    uint64_t* d_cuts = nullptr;
+    cuda_check(cudaMalloc(&d_cuts, 8 * ((size_t)max_nt + 2)), "cudaMalloc cuts");
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        HostPart& hp = parts_[p];
+        cudaError_t e = launch_build_tiles(hp.d_col_ptr, hp.n_own, (uint32_t)hp.src.size(), T, H, p,
+                                           hp.tile_base, hp.n_tiles, d_tiles_ + hp.tile_base, d_cuts, stream_);
+        if (e != cudaSuccess) {
+            cudaFree(d_cuts);
+            cuda_check(e, "build tiles");
+        }
+    }
+    cuda_check(cudaStreamSynchronize(stream_), "build tiles");
+    cudaFree(d_cuts);
+    const size_t nt1 = std::max<uint32_t>(n_tiles_, 1);
+    d_part_head_ = (uint32_t*)dalloc(4 * nt1);
+    d_part_tail_ = (uint32_t*)dalloc(4 * nt1);
+    d_hub_cnt_ = (uint32_t*)dalloc(4 * nt1);
+    cuda_check(cudaMemsetAsync(d_hub_cnt_, 0, 4 * nt1, stream_), "memset");
+
+    // out-degrees over all partitions' edges
+    d_outdeg_ = (uint32_t*)dalloc(4 * (size_t)V);
+    cuda_check(cudaMemsetAsync(d_outdeg_, 0, 4 * (size_t)V, stream_), "memset");
+    for (uint32_t p = 0; p < n_parts_; ++p)
+        cuda_check(launch_outdeg(pd[p], parts_[p].d_src, d_ghost_gid_ + parts_[p].ghost_base, d_outdeg_, stream_),
+                   "out-degrees");
+
+    for (int b = 0; b < 2; ++b) {
+        d_own_[b] = (uint32_t*)dalloc(4 * (size_t)V);
+        d_rank_[b] = (float*)dalloc(4 * (size_t)V);
+    }
+    d_stats_ = (StepStats*)dalloc(sizeof(StepStats) * kStatRing);
+    d_err_ = (uint32_t*)dalloc(4);
+    cuda_check(cudaMemsetAsync(d_err_, 0, 4, stream_), "memset");
+    if (cfg_.check_bounds)
+        for (uint32_t p = 0; p < n_parts_; ++p)
+            cuda_check(launch_validate_csc(parts_[p].d_col_ptr, parts_[p].n_own, parts_[p].d_src, pd[p].n_edges,
+                                           parts_[p].n_own + pd[p].n_ghost, d_err_, stream_), "validate");
+    if (n_parts_ > 1) build_caches();
+    cuda_check(cudaStreamSynchronize(stream_), "finalize");
+    check_device_error();
+    finalized_ = true;
+}
+
+// Mirror table (where each owned vertex is cached), boundary bitmap and
+// global-data-queue layout for the sync of Algorithm 3.
+void Engine::build_caches() {
+    const uint32_t V = (uint32_t)n_vertices_;
+    std::vector<uint32_t> mptr((size_t)V + 1, 0);
+    for (auto& hp : parts_)
+        for (uint32_t g : hp.ghost_gid) mptr[(size_t)g + 1]++;
+    for (uint32_t v = 0; v < V; ++v) mptr[v + 1] += mptr[v];
+    std::vector<uint32_t> fill(mptr.begin(), mptr.end() - 1);
+    std::vector<uint32_t> midx(std::max<uint32_t>(mptr[V], 1));
+    for (auto& hp : parts_)
+        for (size_t s = 0; s < hp.ghost_gid.size(); ++s) midx[fill[hp.ghost_gid[s]]++] = hp.ghost_base + (uint32_t)s;
+    const size_t words = ((size_t)V + 31) / 32 + 2;
+    std::vector<uint32_t> bbits(words, 0);
+    uint64_t gdq_total = 0;
+    max_words_ = 0;
+    for (auto& hp : parts_) {
+        hp.n_boundary = 0;
+        for (uint32_t v = hp.v_begin; v < hp.v_begin + hp.n_own; ++v)
+            if (mptr[v + 1] > mptr[v]) {
+                bbits[v >> 5] |= 1u << (v & 31);
+                hp.n_boundary++;
+            }
+        hp.gdq_base = gdq_total;
+        gdq_total += hp.n_boundary;
+        const uint32_t wl = hp.v_begin >> 5, wh = (hp.v_begin + hp.n_own + 31) >> 5;
+        max_words_ = std::max(max_words_, hp.n_own ? wh - wl : 0u);
+    }
+    if (gdq_total > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "global data queue too large");
+    d_mirror_ptr_ = (uint32_t*)dalloc(4 * ((size_t)V + 1));
+    d_mirror_idx_ = (uint32_t*)dalloc(4 * midx.size());
+    d_boundary_ = (uint32_t*)dalloc(4 * words);
+    d_changed_ = (uint32_t*)dalloc(4 * words);
+    d_gdq_ids_ = (uint32_t*)dalloc(4 * std::max<uint64_t>(gdq_total, 1));
+    d_gdq_vals_ = (uint32_t*)dalloc(4 * std::max<uint64_t>(gdq_total, 1));
+    d_gdq_base_ = (uint64_t*)dalloc(8 * n_parts_);
+    std::vector<uint64_t> gb(n_parts_);
+    for (uint32_t p = 0; p < n_parts_; ++p) gb[p] = parts_[p].gdq_base;
+    sync_blocks_x_ = std::max<uint32_t>((max_words_ + 255) / 256, 1);
+    d_block_counts_ = (uint32_t*)dalloc(4 * (size_t)n_parts_ * sync_blocks_x_);
+    d_block_offsets_ = (uint32_t*)dalloc(4 * (size_t)n_parts_ * sync_blocks_x_);
+    d_part_counts_ = (uint32_t*)dalloc(4 * n_parts_);
+    d_done_ctr_ = (uint32_t*)dalloc(4);
+    cuda_check(cudaMemcpyAsync(d_mirror_ptr_, mptr.data(), 4 * mptr.size(), cudaMemcpyHostToDevice, stream_), "upload");
+    cuda_check(cudaMemcpyAsync(d_mirror_idx_, midx.data(), 4 * midx.size(), cudaMemcpyHostToDevice, stream_), "upload");
+    cuda_check(cudaMemcpyAsync(d_boundary_, bbits.data(), 4 * words, cudaMemcpyHostToDevice, stream_), "upload");
+    cuda_check(cudaMemcpyAsync(d_gdq_base_, gb.data(), 8 * n_parts_, cudaMemcpyHostToDevice, stream_), "upload");
+    cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * words, stream_), "memset");
+    cuda_check(cudaMemsetAsync(d_part_counts_, 0, 4 * n_parts_, stream_), "memset");
+    cuda_check(cudaMemsetAsync(d_done_ctr_, 0, 4, stream_), "memset");
+    // the host copies must outlive the async uploads
+    cuda_check(cudaStreamSynchronize(stream_), "upload caches");
+}
+
+// ------------------------------------------------------------- algorithms
+
+static Algo to_algo(gxp_algo a) {
+    switch (a) {
+        case GXP_ALGO_SSSP: return Algo::SSSP;
+        case GXP_ALGO_CC: return Algo::CC;
+        case GXP_ALGO_PAGERANK: return Algo::PR;
+        case GXP_ALGO_PPR: fail(GXP_E_UNSUPPORTED, "personalized PageRank runs through the query API");
+        default: fail(GXP_E_INVAL, "unknown algorithm");
+    }
+}
+
+void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
+    if (!have_graph_) fail(GXP_E_STATE, "no graph");
+    const Algo a = to_algo(algo);
+    if (a == Algo::SSSP && source >= n_vertices_) fail(GXP_E_INVAL, "source out of range");
+    if (a == Algo::PR && !(damping >= 0.0f && damping < 1.0f)) fail(GXP_E_INVAL, "damping must be in [0, 1)");
+    if (!finalized_) finalize();
+    if (a == Algo::SSSP && !weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights on every partition");
+    const uint32_t V = (uint32_t)n_vertices_;
+    cuda_check(cudaMemsetAsync(d_stats_, 0, sizeof(StepStats) * kStatRing, stream_), "memset");
+    cuda_check(launch_init_values(a, V, source, d_own_[0], d_rank_[0], d_outdeg_, d_stats_, stream_), "init values");
+    cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
+    if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
+    algo_ = a;
+    source_ = source;
+    damping_ = damping;
+    cur_ = 0;
+    step_ = accounted_ = 0;
+    st_ = gxp_stats{};
+    begun_ = true;
+}
+
+uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply ap, bool want) {
+    if (!begun_) fail(GXP_E_STATE, "gxp_begin must come first");
+    if (to_algo(algo) != algo_) fail(GXP_E_INVAL, "algorithm differs from the one begun");
+    const bool ok = (algo_ == Algo::SSSP && g == GXP_GEN_RELAX && m == GXP_MERGE_MIN && ap == GXP_APPLY_MIN) ||
+                    (algo_ == Algo::CC && g == GXP_GEN_LABEL && m == GXP_MERGE_MIN && ap == GXP_APPLY_MIN) ||
+                    (algo_ == Algo::PR && g == GXP_GEN_CONTRIB && m == GXP_MERGE_SUM && ap == GXP_APPLY_PAGERANK);
+    if (!ok) fail(GXP_E_UNSUPPORTED, "unsupported (msggen, merge, apply) template for this algorithm");
+    const int nx = cur_ ^ 1;
+    SuperstepArgs a{};
+    a.tiles = d_tiles_;
+    a.parts = d_parts_;
+    a.n_tiles = n_tiles_;
+    a.own_cur = d_own_[cur_];
+    a.own_nxt = d_own_[nx];
+    a.ghost = d_ghost_;
+    a.rank_cur = d_rank_[cur_];
+    a.rank_nxt = d_rank_[nx];
+    a.outdeg = d_outdeg_;
+    a.changed_bits = n_parts_ > 1 ? d_changed_ : nullptr;
+    a.part_head = d_part_head_;
+    a.part_tail = d_part_tail_;
+    a.hub_cnt = d_hub_cnt_;
+    a.stats_in = d_stats_ + (step_ % kStatRing);
+    a.stats_out = d_stats_ + ((step_ + 1) % kStatRing);
+    a.stats_clear = d_stats_ + ((step_ + 2) % kStatRing);
+    a.err = d_err_;
+    a.timeout_ns = cfg_.timeout_ns;
+    a.check_bounds = cfg_.check_bounds;
+    a.damping = damping_;
+    a.inv_n = 1.0 / (double)n_vertices_;
+    a.max_items = max_items_;
+    cuda_check(cudaEventRecord(ev_a_, stream_), "event");
+    cuda_check(launch_superstep(algo_, a, superstep_smem_bytes(algo_, max_items_), stream_), "superstep kernel");
+    if (n_parts_ > 1) {
+        SyncArgs s{};
+        s.parts = d_parts_;
+        s.n_parts = n_parts_;
+        s.changed_bits = d_changed_;
+        s.boundary_bits = d_boundary_;
+        s.own_val = d_own_[nx];
+        s.mirror_ptr = d_mirror_ptr_;
+        s.mirror_idx = d_mirror_idx_;
+        s.ghost = d_ghost_;
+        s.gdq_ids = d_gdq_ids_;
+        s.gdq_vals = d_gdq_vals_;
+        s.gdq_base = d_gdq_base_;
+        s.block_counts = d_block_counts_;
+        s.block_offsets = d_block_offsets_;
+        s.part_counts = d_part_counts_;
+        s.done_ctr = d_done_ctr_;
+        s.blocks_x = sync_blocks_x_;
+        s.stats_out = a.stats_out;
+        cuda_check(launch_sync(s, max_words_, stream_), "sync kernels");
+        cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)n_vertices_ + 31) / 32 + 2), stream_), "memset");
+    }
+    cuda_check(cudaEventRecord(ev_b_, stream_), "event");
+    cur_ = nx;
+    ++step_;
+    if (want || step_ - accounted_ >= 32) account(true);
+    return st_.last_changed;
+}
+
+// Fold the device-side stats of the supersteps not yet read into st_.
+void Engine::account(bool) {
+    if (accounted_ == step_) return;
+    cuda_check(cudaStreamSynchronize(stream_), "superstep");
+    check_device_error();
+    for (uint64_t t = accounted_ + 1; t <= step_; ++t) {
+        StepStats s;
+        cuda_check(cudaMemcpy(&s, d_stats_ + (t % kStatRing), sizeof(s), cudaMemcpyDeviceToHost), "read stats");
+        unsigned long long ch = 0, dg = 0, l1 = 0;
+        for (int i = 0; i < kStatLanes; ++i) {
+            ch += s.changed[i];
+            dg += s.dangling_fx[i];
+            l1 += s.l1_fx[i];
+        }
+        st_.supersteps++;
+        st_.edges_scanned += total_edges_;
+        st_.last_changed = ch;
+        if (algo_ == Algo::PR) {
+            st_.last_dangling = fx_to_double(dg);
+            st_.last_l1_delta = fx_to_double(l1);
+        }
+        if (n_parts_ > 1) {
+            st_.last_boundary_changed = s.boundary_changed;
+            st_.sync_pairs += s.boundary_changed;
+            if (s.skipped) st_.syncs_skipped++;
+            else st_.syncs_done++;
+        }
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) st_.last_superstep_ms = ms;
+    else cudaGetLastError();
+    accounted_ = step_;
+}
+
+void Engine::sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap, uint64_t* n_out, int* skipped) {
+    if (!begun_ || step_ == 0) fail(GXP_E_STATE, "no superstep has run");
+    if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
+    if (!n_out) fail(GXP_E_INVAL, "n_out is required");
+    account(true);
+    if (n_parts_ == 1) {
+        *n_out = 0;
+        if (skipped) *skipped = 1;
+        return;
+    }
+    StepStats s;
+    cuda_check(cudaMemcpy(&s, d_stats_ + (step_ % kStatRing), sizeof(s), cudaMemcpyDeviceToHost), "read stats");
+    uint32_t n = 0;
+    if (!s.skipped) cuda_check(cudaMemcpy(&n, d_part_counts_ + part, 4, cudaMemcpyDeviceToHost), "read count");
+    *n_out = n;
+    if (skipped) *skipped = s.skipped ? 1 : 0;
+    if (n > cap) fail(GXP_E_INVAL, "cap smaller than the number of uploaded pairs");
+    if (n == 0) return;
+    if (!ids || !vals) fail(GXP_E_INVAL, "null output array");
+    const uint64_t base = parts_[part].gdq_base;
+    cuda_check(cudaMemcpy(ids, d_gdq_ids_ + base, 4ull * n, cudaMemcpyDefault), "copy gdq ids");
+    cuda_check(cudaMemcpy(vals, d_gdq_vals_ + base, 4ull * n, cudaMemcpyDefault), "copy gdq values");
+}
+
+uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max_steps) {
+    begin(algo, source, damping);
+    const gxp_msggen g = algo_ == Algo::SSSP ? GXP_GEN_RELAX : algo_ == Algo::CC ? GXP_GEN_LABEL : GXP_GEN_CONTRIB;
+    const gxp_merge m = algo_ == Algo::PR ? GXP_MERGE_SUM : GXP_MERGE_MIN;
+    const gxp_apply ap = algo_ == Algo::PR ? GXP_APPLY_PAGERANK : GXP_APPLY_MIN;
+    uint32_t steps = 0;
+    if (algo_ == Algo::PR) {
+        for (; steps < max_steps; ++steps) superstep(algo, g, m, ap, false);
+        account(true);
+        return steps;
+    }
+    while (steps < max_steps) {
+        const uint64_t ch = superstep(algo, g, m, ap, true);
+        ++steps;
+        if (ch == 0) break;
+    }
+    return steps;
+}
+
+void Engine::get_values(uint32_t part, void* out, uint64_t n) {
+    if (!begun_) fail(GXP_E_STATE, "gxp_begin must come first");
+    if (!out) fail(GXP_E_INVAL, "null output");
+    uint64_t off = 0, cnt = n_vertices_;
+    if (part != 0xFFFFFFFFu) {
+        if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
+        off = parts_[part].v_begin;
+        cnt = parts_[part].n_own;
+    }
+    if (n != cnt) fail(GXP_E_INVAL, "n must equal the number of vertices requested");
+    const void* src = algo_ == Algo::PR ? (const void*)(d_rank_[cur_] + off) : (const void*)(d_own_[cur_] + off);
+    cuda_check(cudaMemcpyAsync(out, src, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
+    cuda_check(cudaStreamSynchronize(stream_), "copy values");
+    check_device_error();
+}
+
+void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
+    if (!begun_) fail(GXP_E_STATE, "gxp_begin must come first");
+    if (algo_ == Algo::PR) fail(GXP_E_UNSUPPORTED, "set_values is implemented for SSSP and CC");
+    if (!in) fail(GXP_E_INVAL, "null input");
+    uint64_t off = 0, cnt = n_vertices_;
+    if (part != 0xFFFFFFFFu) {
+        if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
+        off = parts_[part].v_begin;
+        cnt = parts_[part].n_own;
+    }
+    if (n != cnt) fail(GXP_E_INVAL, "n must equal the number of vertices given");
+    account(true);
+    cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
+    cuda_check(launch_init_ghosts(algo_, n_ghost_total_, d_ghost_gid_, d_own_[cur_], d_ghost_, stream_), "refresh caches");
+    cuda_check(cudaStreamSynchronize(stream_), "set values");
+}
+
+void Engine::stats(gxp_stats* out) {
+    if (begun_) account(true);
+    *out = st_;
+    out->device_bytes = graph_bytes_;
+}
+
+// ------------------------------------------------------ block-size model
+
+// Lemma 1 (Section III-A): per-entity costs k1 (download), k2 (compute),
+// k3 (upload), per-block call cost a, d entities. The pipeline-time equation
+//   T(b, s) = k1 b + max(k1 b, a + k2 b) + (s - 2) max(k1 b, a + k2 b, k3 b)
+//             + max(a + k2 b, k3 b) + k3 b
+// is minimised over b by the lemma's three cases; the integer choice scores
+// s in {floor, ceil}(d / b_opt) with b = d / s, and b in {floor, ceil}(b_opt)
+// with s = ceil(d / b), in the equation.
+static double pipeline_time(double b, double s, double k1, double k2, double k3, double a) {
+    const double tn = k1 * b, tc = a + k2 * b, tu = k3 * b;
+    return tn + std::max(tn, tc) + (s - 2.0) * std::max(std::max(tn, tc), tu) + std::max(tc, tu) + tu;
+}
+
+void block_size_model(double k1, double k2, double k3, double a, uint64_t d, uint64_t* b_out,
+                      uint64_t* s_out, double* t_out) {
+    if (!(k1 > 0 && k2 > 0 && k3 >= 0 && a >= 0) || d < 2 || !b_out || !s_out || !t_out)
+        fail(GXP_E_INVAL, "block-size model needs k1, k2 > 0, k3, a >= 0, d >= 2");
+    const double dd = (double)d;
+    const double q = std::sqrt(a * dd / (k1 + k3));
+    const double kmax = std::max(k1, std::max(k2, k3));
+    double b_opt = q;
+    if (k1 == kmax && k1 > k2 && a / (k1 - k2) < q) b_opt = a / (k1 - k2);
+    else if (k3 == kmax && k3 > k2 && a / (k3 - k2) < q) b_opt = a / (k3 - k2);
+    if (!(b_opt > 0)) b_opt = 1.0;
+    const double s_opt = dd / b_opt;
+    double best_t = std::numeric_limits<double>::infinity(), best_b = 0;
+    uint64_t best_s = 0;
+    auto consider = [&](double b, uint64_t s) {
+        const double t = pipeline_time(b, (double)s, k1, k2, k3, a);
+        if (t < best_t || (t == best_t && s < best_s)) {
+            best_t = t;
+            best_b = b;
+            best_s = s;
+        }
+    };
+    for (double sc : {std::floor(s_opt), std::ceil(s_opt)}) {
+        const uint64_t s = (uint64_t)std::min<double>(std::max<double>(sc, 2.0), dd);
+        consider(dd / (double)s, s);
+    }
+    for (double bc : {std::floor(b_opt), std::ceil(b_opt)}) {
+        const uint64_t b = (uint64_t)std::min<double>(std::max<double>(bc, 1.0), std::max<double>(std::floor(dd / 2), 1.0));
+        consider((double)b, std::max<uint64_t>(2, (d + b - 1) / b));
+    }
+    *b_out = (uint64_t)std::ceil(best_b - 1e-9);
+    *s_out = best_s;
+    *t_out = best_t;
+}
+
+}  // namespace gxp

@@ -1,0 +1,122 @@
+// Host-side engine behind the C-ABI: one context = one device, one graph of
+// partitions, one running algorithm. All device work goes through the
+// kernels declared in gxp_internal.hpp.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gxp_internal.hpp"
+
+namespace gxp {
+
+// Error carrying a gxp_status across the C++ layer; converted at the ABI.
+struct Error {
+    gxp_status code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(gxp_status code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+
+struct HostPart {
+    uint32_t v_begin = 0, n_own = 0;
+    bool loaded = false;
+    std::vector<uint32_t> col_ptr;    // [n_own + 1] local CSC offsets
+    std::vector<uint32_t> src;        // local source ids (own: gid - v_begin; ghost: n_own + slot)
+    std::vector<uint32_t> w;          // weights (empty = unweighted)
+    std::vector<uint32_t> ghost_gid;  // sorted global ids of the cached remote sources
+    // device copies (owned by Engine's allocation list)
+    uint32_t* d_col_ptr = nullptr;
+    uint32_t* d_src = nullptr;
+    uint32_t* d_w = nullptr;
+    uint32_t tile_base = 0, n_tiles = 0;
+    uint32_t ghost_base = 0;
+    uint64_t gdq_base = 0, n_boundary = 0;
+};
+
+class Engine {
+public:
+    Engine(int device, const gxp_config* cfg);
+    ~Engine();
+
+    void set_stream(cudaStream_t s) { stream_ = s ? s : own_stream_; }
+    cudaStream_t stream() const { return stream_; }
+
+    void create_graph(uint64_t n_vertices, uint32_t n_parts, const uint64_t* part_begin);
+    void load_partition(uint32_t part, gxp_format fmt, uint64_t n_edges, const void* idx0,
+                        const uint32_t* idx1, const uint32_t* weights);
+    void begin(gxp_algo algo, uint32_t source, float damping);
+    uint64_t superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a, bool want_changed);
+    void sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap, uint64_t* n_out, int* skipped);
+    uint32_t run(gxp_algo algo, uint32_t source, float damping, uint32_t max_steps);
+    void get_values(uint32_t part, void* out, uint64_t n);
+    void set_values(uint32_t part, const void* in, uint64_t n);
+    void stats(gxp_stats* out);
+
+    std::string last_error;
+    bool poisoned = false;
+
+    uint64_t n_vertices() const { return n_vertices_; }
+
+private:
+    void* dalloc(size_t bytes);
+    void free_graph_device();
+    void finalize();
+    void build_caches();
+    void account(bool force);
+    void check_device_error();
+    void copy_in(void* dst, const void* src, size_t bytes);   // host or device src -> host dst
+
+    int device_;
+    gxp_config cfg_;
+    cudaStream_t own_stream_ = nullptr, stream_ = nullptr;
+    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr;
+
+    // graph
+    uint64_t n_vertices_ = 0;
+    uint32_t n_parts_ = 0;
+    std::vector<HostPart> parts_;
+    bool have_graph_ = false, finalized_ = false;
+
+    // device graph-level buffers
+    std::vector<void*> graph_allocs_;
+    uint64_t graph_bytes_ = 0;
+    PartDev* d_parts_ = nullptr;
+    Tile* d_tiles_ = nullptr;
+    uint32_t n_tiles_ = 0, max_items_ = 0;
+    uint32_t *d_part_head_ = nullptr, *d_part_tail_ = nullptr, *d_hub_cnt_ = nullptr;
+    uint32_t* d_outdeg_ = nullptr;
+    uint32_t* d_own_[2] = {nullptr, nullptr};
+    float* d_rank_[2] = {nullptr, nullptr};
+    uint32_t* d_ghost_ = nullptr;
+    uint32_t* d_ghost_gid_ = nullptr;
+    uint32_t n_ghost_total_ = 0;
+    uint32_t *d_changed_ = nullptr, *d_boundary_ = nullptr;
+    uint32_t *d_mirror_ptr_ = nullptr, *d_mirror_idx_ = nullptr;
+    uint32_t *d_gdq_ids_ = nullptr, *d_gdq_vals_ = nullptr;
+    uint64_t* d_gdq_base_ = nullptr;
+    uint32_t *d_block_counts_ = nullptr, *d_block_offsets_ = nullptr, *d_part_counts_ = nullptr;
+    uint32_t* d_done_ctr_ = nullptr;
+    uint32_t sync_blocks_x_ = 0, max_words_ = 0;
+    StepStats* d_stats_ = nullptr;
+    uint32_t* d_err_ = nullptr;
+    bool weighted_ = false;
+
+    // algorithm state
+    bool begun_ = false;
+    Algo algo_ = Algo::SSSP;
+    uint32_t source_ = 0;
+    float damping_ = 0.85f;
+    int cur_ = 0;
+    uint64_t step_ = 0, accounted_ = 0;
+    gxp_stats st_{};
+    uint64_t total_edges_ = 0;
+};
+
+// Lemma 1 block-size model (host arithmetic).
+void block_size_model(double k1, double k2, double k3, double a, uint64_t d, uint64_t* b,
+                      uint64_t* s, double* t);
+
+}  // namespace gxp

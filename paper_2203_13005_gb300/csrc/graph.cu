@@ -1,0 +1,314 @@
+// Load-time and per-superstep helper kernels:
+//  * edge-block (tile) construction over a partition's CSC — the paired edge
+//    and vertex blocks of Section II-B, with hub vertices split;
+//  * out-degrees (PageRank's MSGGen divides by them);
+//  * initial vertex values and cache (ghost) fills;
+//  * synchronization caching and skipping between partitions (Section
+//    III-B, Algorithm 3): changed ∩ boundary -> global data queue (sorted by
+//    id) -> the caches of the partitions that read those vertices; the
+//    exchange is skipped on the device when the queue is empty everywhere.
+#include "gxp_internal.hpp"
+
+#include <algorithm>
+
+namespace gxp {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// -------------------------------------------------------------- tiles
+
+__device__ __forceinline__ uint64_t cut_pos(uint64_t c) { return (c >> 32) + (c & 0xFFFFFFFFull); }
+
+// Cut k of the merged sequence (vertex ends + edges) at diagonal k*T, snapped
+// back to the start of the vertex it falls in unless that vertex is a hub
+// (in-degree > H). Packed as (vertex << 32 | edge).
+__global__ void k_cuts(const uint32_t* __restrict__ col_ptr, uint32_t n, uint32_t n_edges,
+                       uint32_t T, uint32_t H, uint32_t nt, uint64_t* __restrict__ cuts) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nt) return;
+    const uint64_t total = (uint64_t)n + n_edges;
+    const uint64_t D = min((uint64_t)k * T, total);
+    // largest i in [0, n] with i + col_ptr[i] <= D
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo + 1u) / 2u;
+        if ((uint64_t)mid + col_ptr[mid] <= D) lo = mid;
+        else hi = mid - 1u;
+    }
+    const uint32_t i = lo;
+    uint64_t j = D - i;
+    if (i < n && j > col_ptr[i]) {
+        const uint32_t deg = col_ptr[i + 1] - col_ptr[i];
+        if (deg <= H) j = col_ptr[i];
+    }
+    cuts[k] = ((uint64_t)i << 32) | j;
+}
+
+__device__ uint32_t upper_bound_cut(const uint64_t* cuts, uint32_t nt, uint64_t p) {
+    // first k in [0, nt] with cut_pos(cuts[k]) > p (nt + 1 if none)
+    uint32_t lo = 0, hi = nt + 1u;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cut_pos(cuts[mid]) > p) hi = mid;
+        else lo = mid + 1u;
+    }
+    return lo;
+}
+
+__global__ void k_tiles(const uint32_t* __restrict__ col_ptr, uint32_t n, const uint64_t* __restrict__ cuts,
+                        uint32_t nt, uint32_t part, uint32_t tile_base, Tile* __restrict__ tiles) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const uint32_t i0 = (uint32_t)(cuts[k] >> 32), j0 = (uint32_t)cuts[k];
+    const uint32_t i1 = (uint32_t)(cuts[k + 1] >> 32), j1 = (uint32_t)cuts[k + 1];
+    const bool head = i0 < n && j0 > col_ptr[i0];
+    const bool tail = i1 < n && j1 > col_ptr[i1];
+    Tile t;
+    t.v0 = i0;
+    t.nv = i1 - i0 + (tail ? 1u : 0u);
+    t.e0 = j0;
+    t.ne = j1 - j0;
+    t.part = part;
+    t.flags = (head ? kHeadOpen : 0u) | (tail ? kTailOpen : 0u);
+    t.hub_t0 = kInf;
+    t.nparts = 0;
+    if (t.nv == 0u && t.ne == 0u) t.flags = 0u;
+    if (head) {
+        const uint64_t p_first = (uint64_t)i0 + col_ptr[i0];
+        t.hub_t0 = tile_base + upper_bound_cut(cuts, nt, p_first) - 1u;
+    }
+    if (tail && !(head && t.nv == 1u)) {
+        const uint64_t p_end = (uint64_t)i1 + col_ptr[i1 + 1];
+        const uint32_t t1 = upper_bound_cut(cuts, nt, p_end) - 1u;
+        t.nparts = t1 - k + 1u;
+    }
+    tiles[k] = t;
+}
+
+// ----------------------------------------------------------- out-degree
+
+__global__ void k_outdeg(const uint32_t* __restrict__ src, uint64_t n_edges, uint32_t n_own,
+                         uint32_t v_begin, const uint32_t* __restrict__ ghost_gid,
+                         uint32_t* __restrict__ outdeg) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_edges;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = src[e];
+        const uint32_t g = u < n_own ? v_begin + u : ghost_gid[u - n_own];
+        atomicAdd(&outdeg[g], 1u);
+    }
+}
+
+__global__ void k_validate(const uint32_t* __restrict__ col_ptr, uint32_t n_own,
+                           const uint32_t* __restrict__ src, uint64_t n_edges, uint32_t n_local,
+                           uint32_t* err) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_edges; e += stride)
+        if (src[e] >= n_local) atomicOr(err, kErrBounds);
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n_own; v += stride)
+        if (col_ptr[v] > col_ptr[v + 1]) atomicOr(err, kErrBounds);
+}
+
+// ------------------------------------------------------- initial values
+
+
+__global__ void k_init_values(int algo, uint32_t n, uint32_t source, uint32_t* own,
+                              float* rank, const uint32_t* outdeg, StepStats* st) {
+    unsigned long long dang = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (algo == (int)Algo::SSSP) {
+            own[v] = (v == source) ? 0u : kInf;
+        } else if (algo == (int)Algo::CC) {
+            own[v] = v;
+        } else {
+            const float r0 = (float)(1.0 / (double)n);
+            rank[v] = r0;
+            const uint32_t od = outdeg[v];
+            own[v] = __float_as_uint(od ? __fdiv_rn(r0, (float)od) : 0.0f);
+            if (od == 0u) dang += fx_of(r0);
+        }
+    }
+    if (algo == (int)Algo::PR) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dang += __shfl_xor_sync(kFull, dang, o);
+        if ((threadIdx.x & 31) == 0 && dang)
+            atomicAdd(&st->dangling_fx[(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) % kStatLanes], dang);
+    }
+}
+
+__global__ void k_init_ghosts(uint32_t n_ghost, const uint32_t* __restrict__ gid,
+                              const uint32_t* __restrict__ own, uint32_t* __restrict__ ghost) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_ghost; g += gridDim.x * blockDim.x)
+        ghost[g] = own[gid[g]];
+}
+
+// ----------------------------------------------------------------- sync
+
+__device__ __forceinline__ uint32_t range_mask(uint32_t w, uint32_t v_lo, uint32_t v_hi) {
+    const uint32_t base = w * 32u;
+    const uint32_t lo = v_lo > base ? v_lo - base : 0u;
+    const uint32_t hi = v_hi < base + 32u ? v_hi - base : 32u;
+    if (hi <= lo) return 0u;
+    const uint32_t upper = hi == 32u ? kFull : ((1u << hi) - 1u);
+    return upper & ~((1u << lo) - 1u);
+}
+
+constexpr int kSyncBlock = 256;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < kSyncBlock / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < kSyncBlock / 32) s_warp[lane] = v;
+    }
+    __syncthreads();
+    const uint32_t warp_off = warp ? s_warp[warp - 1] : 0u;
+    total = s_warp[kSyncBlock / 32 - 1];
+    __syncthreads();
+    return warp_off + incl - x;
+}
+
+// Count changed ∩ boundary per block; the last block to finish turns the
+// counts into per-block offsets and decides whether the exchange is skipped.
+__global__ void __launch_bounds__(kSyncBlock) k_sync_count(const SyncArgs a) {
+    __shared__ uint32_t s_warp[kSyncBlock / 32];
+    __shared__ bool s_last;
+    const uint32_t p = blockIdx.y;
+    const PartDev P = a.parts[p];
+    const uint32_t v_lo = P.v_begin, v_hi = P.v_begin + P.n_own;
+    const uint32_t w_lo = v_lo >> 5, w_hi = (v_hi + 31u) >> 5;
+    const uint32_t w = w_lo + blockIdx.x * kSyncBlock + threadIdx.x;
+    uint32_t c = 0;
+    if (P.n_own && w < w_hi) c = __popc(a.changed_bits[w] & a.boundary_bits[w] & range_mask(w, v_lo, v_hi));
+    uint32_t total;
+    block_excl_scan(c, s_warp, total);
+    if (threadIdx.x == 0) {
+        a.block_counts[p * a.blocks_x + blockIdx.x] = total;
+        __threadfence();
+        const uint32_t ticket = atomicAdd(a.done_ctr, 1u);
+        s_last = ticket == gridDim.x * gridDim.y - 1u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long grand = 0;
+    for (uint32_t q = 0; q < a.n_parts; ++q) {
+        uint32_t run = 0;
+        for (uint32_t b0 = 0; b0 < a.blocks_x; b0 += kSyncBlock) {
+            const uint32_t b = b0 + threadIdx.x;
+            const uint32_t x = b < a.blocks_x ? __ldcg(&a.block_counts[q * a.blocks_x + b]) : 0u;
+            uint32_t tot;
+            const uint32_t ex = block_excl_scan(x, s_warp, tot);
+            if (b < a.blocks_x) a.block_offsets[q * a.blocks_x + b] = run + ex;
+            run += tot;
+        }
+        if (threadIdx.x == 0) a.part_counts[q] = run;
+        grand += run;
+    }
+    if (threadIdx.x == 0) {
+        a.stats_out->boundary_changed = grand;
+        a.stats_out->skipped = grand == 0 ? 1ull : 0ull;
+        *a.done_ctr = 0u;
+    }
+}
+
+// Write each partition's global data queue (ascending ids) and update every
+// cached copy of the uploaded vertices.
+__global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
+    __shared__ uint32_t s_warp[kSyncBlock / 32];
+    if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
+    const uint32_t p = blockIdx.y;
+    const PartDev P = a.parts[p];
+    const uint32_t v_lo = P.v_begin, v_hi = P.v_begin + P.n_own;
+    const uint32_t w_lo = v_lo >> 5, w_hi = (v_hi + 31u) >> 5;
+    const uint32_t w = w_lo + blockIdx.x * kSyncBlock + threadIdx.x;
+    uint32_t bits = 0;
+    if (P.n_own && w < w_hi) bits = a.changed_bits[w] & a.boundary_bits[w] & range_mask(w, v_lo, v_hi);
+    uint32_t total;
+    uint32_t pos = block_excl_scan(__popc(bits), s_warp, total);
+    if (P.n_own == 0 || blockIdx.x * kSyncBlock >= w_hi - w_lo) return;
+    pos += a.block_offsets[p * a.blocks_x + blockIdx.x] + (uint32_t)a.gdq_base[p];
+    while (bits) {
+        const uint32_t b = __ffs(bits) - 1u;
+        bits &= bits - 1u;
+        const uint32_t gid = w * 32u + b;
+        const uint32_t val = a.own_val[gid];
+        a.gdq_ids[pos] = gid;
+        a.gdq_vals[pos] = val;
+        ++pos;
+        for (uint32_t m = a.mirror_ptr[gid]; m < a.mirror_ptr[gid + 1]; ++m) a.ghost[a.mirror_idx[m]] = val;
+    }
+}
+
+}  // namespace
+
+uint32_t tile_count(uint32_t n_own, uint64_t n_edges, uint32_t tile_items) {
+    const uint64_t items = (uint64_t)n_own + n_edges;
+    return (uint32_t)((items + tile_items - 1) / tile_items);
+}
+
+cudaError_t launch_build_tiles(const uint32_t* col_ptr, uint32_t n_own, uint32_t n_edges,
+                               uint32_t tile_items, uint32_t hub_items, uint32_t part,
+                               uint32_t tile_base, uint32_t nt, Tile* tiles, uint64_t* cuts,
+                               cudaStream_t s) {
+    if (nt == 0) return cudaSuccess;
+    k_cuts<<<(nt + 1 + 255) / 256, 256, 0, s>>>(col_ptr, n_own, n_edges, tile_items, hub_items, nt, cuts);
+    k_tiles<<<(nt + 255) / 256, 256, 0, s>>>(col_ptr, n_own, cuts, nt, part, tile_base, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outdeg(const PartDev& p, const uint32_t* src, const uint32_t* ghost_gid,
+                          uint32_t* outdeg, cudaStream_t s) {
+    if (p.n_edges == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((p.n_edges + 255) / 256, 152ull * 16);
+    k_outdeg<<<(unsigned)blocks, 256, 0, s>>>(src, p.n_edges, p.n_own, p.v_begin, ghost_gid, outdeg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_csc(const uint32_t* col_ptr, uint32_t n_own, const uint32_t* src,
+                                uint64_t n_edges, uint32_t n_local, uint32_t* err, cudaStream_t s) {
+    const uint64_t work = std::max<uint64_t>(n_edges, n_own);
+    if (work == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((work + 255) / 256, 152ull * 16);
+    k_validate<<<(unsigned)blocks, 256, 0, s>>>(col_ptr, n_own, src, n_edges, n_local, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_values(Algo a, uint32_t n, uint32_t source, uint32_t* own, float* rank,
+                               const uint32_t* outdeg, StepStats* st, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 152u * 8);
+    k_init_values<<<blocks, 256, 0, s>>>((int)a, n, source, own, rank, outdeg, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_ghosts(Algo, uint32_t n_ghost, const uint32_t* gid, const uint32_t* own,
+                               uint32_t* ghost, cudaStream_t s) {
+    if (n_ghost == 0) return cudaSuccess;
+    const uint32_t blocks = std::min<uint32_t>((n_ghost + 255) / 256, 152u * 8);
+    k_init_ghosts<<<blocks, 256, 0, s>>>(n_ghost, gid, own, ghost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sync(const SyncArgs& a, uint32_t, cudaStream_t s) {
+    if (a.n_parts == 0 || a.blocks_x == 0) return cudaSuccess;
+    dim3 grid(a.blocks_x, a.n_parts);
+    k_sync_count<<<grid, kSyncBlock, 0, s>>>(a);
+    k_sync_write<<<grid, kSyncBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gxp

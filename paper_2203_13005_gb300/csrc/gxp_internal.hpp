@@ -1,0 +1,164 @@
+// Internal declarations of libgxp: device data layout, kernel launchers and
+// the host-side context. Not part of the C-ABI (include/gxp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gxp.h"
+
+namespace gxp {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr int kBlock = 256;          // threads per superstep CTA
+constexpr int kMaxIpt = 12;          // merge items per thread (static register budget)
+constexpr int kMaxTileItems = kBlock * kMaxIpt;
+constexpr int kStatLanes = 64;       // stat accumulators are spread over lanes to
+                                     // avoid same-address atomic serialization
+constexpr int kStatRing = 64;        // superstep stat slots kept on the device
+
+// Device error word bits (ORed by kernels, read by the host at sync points).
+constexpr uint32_t kErrBounds = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+// Fixed-point scale of the exact global sums (dangling mass, L1 delta):
+// an fp32 value x in [0, 2] is held as round(x * 2^60) in a uint64.
+constexpr int kFxShift = 60;
+
+enum class Algo : int { SSSP = 0, CC = 1, PR = 2 };
+
+// One edge block ("tile") paired with its vertex block (Section II-B): the
+// in-edges [e0, e0+ne) of local destinations [v0, v0+nv) of one partition.
+// Blocks are cut at vertex boundaries except inside hub vertices whose
+// in-degree exceeds hub_items; such a vertex spans several blocks, and its
+// partial merges are combined by the last block to finish it.
+struct Tile {
+    uint32_t v0;       // first local destination vertex
+    uint32_t nv;       // destination vertices touched (incl. an open head/tail)
+    uint32_t e0;       // first edge (partition-local CSC index)
+    uint32_t ne;       // edge count
+    uint32_t part;     // partition index
+    uint32_t flags;    // kHeadOpen | kTailOpen
+    uint32_t hub_t0;   // kHeadOpen: global index of the tile where the head vertex starts
+    uint32_t nparts;   // tile that starts an open tail vertex: tiles that vertex spans
+};
+constexpr uint32_t kHeadOpen = 1u;
+constexpr uint32_t kTailOpen = 2u;
+
+// Per-partition device view (array in device memory, indexed by Tile::part).
+struct PartDev {
+    const uint32_t* col_ptr;   // [n_own + 1], padded to a multiple of 4 + 4
+    const uint32_t* src;       // [n_edges] local source index, padded likewise
+    const uint32_t* w;         // [n_edges] weights or nullptr
+    uint32_t n_own;            // owned vertices
+    uint32_t v_begin;          // global id of local vertex 0
+    uint32_t n_ghost;          // cached remote vertices (local ids n_own ..)
+    uint32_t ghost_base;       // offset of this partition's ghosts in the ghost array
+    uint64_t n_edges;
+};
+
+// Accumulators of one superstep (one ring slot).
+struct StepStats {
+    unsigned long long changed[kStatLanes];
+    unsigned long long dangling_fx[kStatLanes];   // sum of fx(r) over out-degree-0 vertices
+    unsigned long long l1_fx[kStatLanes];         // sum |fx(r_new) - fx(r_old)|
+    unsigned long long boundary_changed;          // pairs uploaded by the sync (all partitions)
+    unsigned long long skipped;                   // 1 if the exchange was skipped
+    unsigned long long pad[6];
+};
+
+// Everything the superstep kernel touches.
+struct SuperstepArgs {
+    const Tile* tiles;
+    const PartDev* parts;
+    uint32_t n_tiles;
+    const uint32_t* own_cur;     // [V] current values (u32 or f32 bits), global id order
+    uint32_t* own_nxt;           // [V] next values
+    const uint32_t* ghost;       // [sum of n_ghost] cached remote values
+    const float* rank_cur;       // PageRank ranks [V] (fp32)
+    float* rank_nxt;
+    const uint32_t* outdeg;      // [V] global out-degree (PageRank)
+    uint32_t* changed_bits;      // [ceil(V/32)] or nullptr
+    uint32_t* part_head;         // [n_tiles] hub partials (value bits)
+    uint32_t* part_tail;         // [n_tiles]
+    uint32_t* hub_cnt;           // [n_tiles] arrival counters (self-resetting)
+    StepStats* stats_in;         // slot of the current state (PageRank: its dangling mass)
+    StepStats* stats_out;        // slot the superstep accumulates into
+    StepStats* stats_clear;      // slot zeroed for the superstep after next
+    uint32_t* err;               // device error word
+    uint64_t timeout_ns;         // limit of any device-side wait
+    uint32_t check_bounds;
+    float damping;
+    double inv_n;                // 1 / N
+    uint32_t max_items;          // largest tile (merge items)
+};
+
+// Arguments of the two sync kernels (changed ∩ boundary -> gdq -> caches).
+struct SyncArgs {
+    const PartDev* parts;
+    uint32_t n_parts;
+    const uint32_t* changed_bits;
+    const uint32_t* boundary_bits;
+    const uint32_t* own_val;          // values after the superstep, [V]
+    const uint32_t* mirror_ptr;       // [V+1] CSR over owned vertices
+    const uint32_t* mirror_idx;       // flat ghost index of each cached copy
+    uint32_t* ghost;                  // [sum n_ghost] caches to update
+    uint32_t* gdq_ids;                // [sum of boundary counts]
+    uint32_t* gdq_vals;
+    const uint64_t* gdq_base;         // [n_parts] offset of each partition's gdq
+    uint32_t* block_counts;           // [n_parts * blocks_x]
+    uint32_t* block_offsets;          // [n_parts * blocks_x]
+    uint32_t* part_counts;            // [n_parts]
+    uint32_t* done_ctr;               // arrival counter of the count kernel
+    uint32_t blocks_x;
+    StepStats* stats_out;
+};
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_build_tiles(const uint32_t* d_col_ptr, uint32_t n_own, uint32_t n_edges,
+                               uint32_t tile_items, uint32_t hub_items, uint32_t part,
+                               uint32_t tile_base, uint32_t n_tiles, Tile* d_tiles,
+                               uint64_t* d_scratch_cuts, cudaStream_t s);
+uint32_t tile_count(uint32_t n_own, uint64_t n_edges, uint32_t tile_items);
+
+cudaError_t launch_outdeg(const PartDev& p, const uint32_t* d_src, const uint32_t* d_ghost_gid,
+                          uint32_t* d_outdeg, cudaStream_t s);
+cudaError_t launch_validate_csc(const uint32_t* d_col_ptr, uint32_t n_own, const uint32_t* d_src,
+                                uint64_t n_edges, uint32_t n_local, uint32_t* d_err, cudaStream_t s);
+
+cudaError_t launch_init_values(Algo a, uint32_t n_vertices, uint32_t source,
+                               uint32_t* own_cur, float* rank_cur, const uint32_t* outdeg,
+                               StepStats* stats0, cudaStream_t s);
+cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* ghost_gid_all,
+                               const uint32_t* own_cur, uint32_t* ghost, cudaStream_t s);
+
+cudaError_t launch_superstep(Algo a, const SuperstepArgs& args, size_t smem_bytes, cudaStream_t s);
+size_t superstep_smem_bytes(Algo a, uint32_t max_items);
+
+cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);
+
+// Fixed point -> double (exact for sums below 2^53 units, else rounded once).
+__host__ __device__ inline double fx_to_double(unsigned long long v) {
+    return (double)v * (1.0 / (double)(1ULL << kFxShift));
+}
+
+#ifdef __CUDACC__
+// x >= 0 (fp32) -> x * 2^60 truncated to an integer, exactly, with integer
+// operations only; values below 2^-126 count as 0. For x <= 2 the result is
+// below 2^62, so sums of up to 2 units of mass cannot overflow.
+__device__ __forceinline__ unsigned long long fx_of(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e == 0) return 0ull;
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 150 + kFxShift;
+    if (sh >= 0) return m << sh;
+    return (-sh) >= 64 ? 0ull : (m >> (-sh));
+}
+#endif
+
+}  // namespace gxp

@@ -1,0 +1,256 @@
+"""ctypes binding of libgxp.so (the C-ABI in ``include/gxp.h``).
+
+Argument marshalling only: every step of the superstep path runs in the
+library's CUDA kernels. The raw functions keep the C names (``gxp_init``,
+``gxp_load_partition``, ``gxp_superstep``, ``gxp_sync`` ...); ``Context`` is a
+thin convenience wrapper that turns status codes into exceptions and accepts
+numpy arrays (host) or CUDA tensors (device) through their data pointers.
+
+Loading fails loudly when the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# status codes
+GXP_OK, GXP_E_INVAL, GXP_E_NOMEM, GXP_E_CUDA, GXP_E_TIMEOUT = 0, 1, 2, 3, 4
+GXP_E_BOUNDS, GXP_E_STATE, GXP_E_UNSUPPORTED, GXP_E_BUSY = 5, 6, 7, 8
+# algorithms and template operators
+GXP_ALGO_SSSP, GXP_ALGO_CC, GXP_ALGO_PAGERANK, GXP_ALGO_PPR = 0, 1, 2, 3
+GXP_GEN_RELAX, GXP_GEN_LABEL, GXP_GEN_CONTRIB = 0, 1, 2
+GXP_MERGE_MIN, GXP_MERGE_SUM = 0, 1
+GXP_APPLY_MIN, GXP_APPLY_PAGERANK = 0, 1
+GXP_FMT_COO, GXP_FMT_CSC, GXP_FMT_CSR = 0, 1, 2
+ALL_PARTS = 0xFFFFFFFF
+INF = 0xFFFFFFFF
+
+TEMPLATES = {
+    GXP_ALGO_SSSP: (GXP_GEN_RELAX, GXP_MERGE_MIN, GXP_APPLY_MIN),
+    GXP_ALGO_CC: (GXP_GEN_LABEL, GXP_MERGE_MIN, GXP_APPLY_MIN),
+    GXP_ALGO_PAGERANK: (GXP_GEN_CONTRIB, GXP_MERGE_SUM, GXP_APPLY_PAGERANK),
+}
+
+
+class gxp_config(C.Structure):
+    _fields_ = [("mem_budget", C.c_uint64), ("tile_items", C.c_uint32), ("hub_items", C.c_uint32),
+                ("timeout_ns", C.c_uint64), ("check_bounds", C.c_uint32), ("max_slots", C.c_uint32),
+                ("pipeline_depth", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+
+
+class gxp_stats(C.Structure):
+    _fields_ = [("supersteps", C.c_uint64), ("edges_scanned", C.c_uint64), ("last_changed", C.c_uint64),
+                ("last_boundary_changed", C.c_uint64), ("syncs_done", C.c_uint64),
+                ("syncs_skipped", C.c_uint64), ("sync_pairs", C.c_uint64), ("last_l1_delta", C.c_double),
+                ("last_dangling", C.c_double), ("last_superstep_ms", C.c_double),
+                ("device_bytes", C.c_uint64), ("reserved", C.c_uint64 * 6)]
+
+
+# (name, restype, argtypes) of every exported symbol
+_P, _U32, _U64, _I, _F, _D = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int, C.c_float, C.c_double
+SIGNATURES = [
+    ("gxp_config_default", None, [_P]),
+    ("gxp_init", _I, [_I, _P, _P]),
+    ("gxp_destroy", None, [_P]),
+    ("gxp_status_string", C.c_char_p, [_I]),
+    ("gxp_last_error", C.c_char_p, [_P]),
+    ("gxp_set_stream", _I, [_P, _P]),
+    ("gxp_create_graph", _I, [_P, _U64, _U32, _P]),
+    ("gxp_load_partition", _I, [_P, _U32, _I, _U64, _P, _P, _P]),
+    ("gxp_begin", _I, [_P, _I, _U32, _F]),
+    ("gxp_get_values", _I, [_P, _U32, _P, _U64]),
+    ("gxp_set_values", _I, [_P, _U32, _P, _U64]),
+    ("gxp_superstep", _I, [_P, _I, _I, _I, _I, _P]),
+    ("gxp_sync", _I, [_P, _U32, _P, _P, _U64, _P, _P]),
+    ("gxp_run", _I, [_P, _I, _U32, _F, _U32, _P]),
+    ("gxp_stats_get", _I, [_P, _P]),
+    ("gxp_block_size_model", _I, [_D, _D, _D, _D, _U64, _P, _P, _P]),
+]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.GXP_LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgxp.so (building it first if asked); raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build_gxp()
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgxp.so not found at {path}: run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class GxpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_status_name(code)}: {msg}")
+        self.code = code
+
+
+def _status_name(code: int) -> str:
+    return load().gxp_status_string(code).decode()
+
+
+def _ptr(x):
+    """Data pointer of a numpy array, a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)!r}")
+
+
+def block_size_model(k1: float, k2: float, k3: float, a: float, d: int):
+    """Lemma 1 with the integer rounding step: returns (b, s, t_estimate)."""
+    b, s, t = C.c_uint64(), C.c_uint64(), C.c_double()
+    rc = load().gxp_block_size_model(k1, k2, k3, a, d, C.byref(b), C.byref(s), C.byref(t))
+    if rc:
+        raise GxpError(rc, load().gxp_last_error(None).decode())
+    return b.value, s.value, t.value
+
+
+class Context:
+    """One gxp_ctx: a device, a partitioned graph and a running algorithm."""
+
+    def __init__(self, device: int = 0, tile_items: int = 0, hub_items: int = 0,
+                 check_bounds: bool = False, timeout_ns: int = 0, mem_budget: int = 0):
+        self.lib = load()
+        cfg = gxp_config()
+        self.lib.gxp_config_default(C.byref(cfg))
+        cfg.tile_items, cfg.hub_items = tile_items, hub_items
+        cfg.check_bounds, cfg.timeout_ns, cfg.mem_budget = int(check_bounds), timeout_ns, mem_budget
+        h = C.c_void_p()
+        rc = self.lib.gxp_init(device, C.byref(cfg), C.byref(h))
+        if rc:
+            raise GxpError(rc, self.lib.gxp_last_error(None).decode())
+        self.h = h
+        self.n_vertices = 0
+        self.n_parts = 0
+        self.bounds = None
+        self.algo = None
+
+    def _ck(self, rc: int):
+        if rc:
+            raise GxpError(rc, self.lib.gxp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gxp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ----------------------------------------------------------------- graph
+    def set_stream(self, stream):
+        self._ck(self.lib.gxp_set_stream(self.h, stream))
+
+    def create_graph(self, n_vertices: int, n_parts: int = 1, part_begin=None):
+        pb = None
+        if part_begin is not None:
+            pb = np.ascontiguousarray(part_begin, dtype=np.uint64)
+        self._ck(self.lib.gxp_create_graph(self.h, n_vertices, n_parts, _ptr(pb)))
+        self.n_vertices, self.n_parts = n_vertices, n_parts
+        self.bounds = (pb.tolist() if pb is not None
+                       else [n_vertices * p // n_parts for p in range(n_parts + 1)])
+
+    def load_partition(self, part: int, fmt: int, n_edges: int, idx0, idx1, weights=None):
+        self._ck(self.lib.gxp_load_partition(self.h, part, fmt, n_edges, _ptr(idx0), _ptr(idx1),
+                                             _ptr(weights)))
+
+    def load_coo(self, src, dst, w=None):
+        """Split a whole-graph COO list by destination owner and load every partition."""
+        src = np.ascontiguousarray(src, dtype=np.uint32)
+        dst = np.ascontiguousarray(dst, dtype=np.uint32)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.uint32)
+        if self.n_parts == 1:
+            self.load_partition(0, GXP_FMT_COO, len(src), src, dst, w)
+            return
+        b = np.asarray(self.bounds, dtype=np.int64)
+        owner = np.searchsorted(b, dst, side="right") - 1
+        order = np.argsort(owner, kind="stable")
+        cuts = np.searchsorted(owner[order], np.arange(self.n_parts + 1))
+        for p in range(self.n_parts):
+            sel = order[cuts[p]:cuts[p + 1]]
+            ws = None if w is None else np.ascontiguousarray(w[sel])
+            self.load_partition(p, GXP_FMT_COO, len(sel), np.ascontiguousarray(src[sel]),
+                                np.ascontiguousarray(dst[sel]), ws)
+
+    # ------------------------------------------------------------- algorithm
+    def begin(self, algo: int, source: int = 0, damping: float = 0.85):
+        self._ck(self.lib.gxp_begin(self.h, algo, source, damping))
+        self.algo = algo
+
+    def superstep(self, algo=None, template=None, want_changed: bool = True):
+        algo = self.algo if algo is None else algo
+        g, m, a = template if template is not None else TEMPLATES[algo]
+        n = C.c_uint64()
+        self._ck(self.lib.gxp_superstep(self.h, algo, g, m, a, C.byref(n) if want_changed else None))
+        return n.value if want_changed else None
+
+    def run(self, algo: int, source: int = 0, damping: float = 0.85, max_steps: int = 1 << 30) -> int:
+        s = C.c_uint32()
+        self._ck(self.lib.gxp_run(self.h, algo, source, damping, max_steps, C.byref(s)))
+        self.algo = algo
+        return s.value
+
+    def values(self, part: int = ALL_PARTS, out=None):
+        n = self.n_vertices if part == ALL_PARTS else int(self.bounds[part + 1] - self.bounds[part])
+        if out is None:
+            out = np.empty(n, dtype=np.float32 if self.algo == GXP_ALGO_PAGERANK else np.uint32)
+        self._ck(self.lib.gxp_get_values(self.h, part, _ptr(out), n))
+        return out
+
+    def set_values(self, arr, part: int = ALL_PARTS):
+        arr = np.ascontiguousarray(arr)
+        self._ck(self.lib.gxp_set_values(self.h, part, _ptr(arr), len(arr)))
+
+    def sync(self, part: int):
+        """(ids, values, skipped) of partition `part`'s last upload (Algorithm 3)."""
+        n, sk = C.c_uint64(), C.c_int()
+        rc = self.lib.gxp_sync(self.h, part, None, None, 0, C.byref(n), C.byref(sk))
+        if rc not in (GXP_OK, GXP_E_INVAL):
+            self._ck(rc)
+        cnt = n.value
+        ids = np.empty(max(cnt, 1), dtype=np.uint32)
+        vals = np.empty(max(cnt, 1), dtype=np.float32 if self.algo == GXP_ALGO_PAGERANK else np.uint32)
+        self._ck(self.lib.gxp_sync(self.h, part, _ptr(ids), _ptr(vals), cnt, C.byref(n), C.byref(sk)))
+        return ids[:cnt], vals[:cnt], bool(sk.value)
+
+    def stats(self) -> dict:
+        s = gxp_stats()
+        self._ck(self.lib.gxp_stats_get(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in gxp_stats._fields_ if k != "reserved"}
