@@ -224,6 +224,46 @@ GXP_API gxp_status gxp_stats_get(gxp_ctx* ctx, gxp_stats* out);
 GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double a, uint64_t d,
                                         uint64_t* b, uint64_t* s, double* t);
 
+/* ------------------------------------------ allocation-free superstep -- */
+
+/* The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory themselves — for example
+ * code whose GPU memory is wholly owned by another allocator (a framework's
+ * caching pool), or latency-sensitive code that cannot accept cudaMalloc's
+ * implicit device synchronisation.
+ *
+ * One SSSP (RELAX, MIN, MIN) or CC (LABEL, MIN, MIN) superstep over a single
+ * partition's CSC that lives in the caller's device memory, computing d_next
+ * from d_cur exactly as gxp_superstep does. It calls no cudaMalloc, cudaFree
+ * or allocating library routine. Its scratch is a fixed file-scope device
+ * array of about 6.8 MB that every GPU loading libgxp.so holds until the
+ * process exits; it limits the input to n_vertices + n_edges <= 2^28
+ * (larger inputs return GXP_E_INVAL).
+ *
+ * Arguments (all device pointers, on the current CUDA device):
+ *   d_col_ptr  uint32[n_vertices + 1], CSC offsets from 0 to n_edges
+ *   d_src      uint32[n_edges] source ids (< n_vertices), dst-sorted
+ *   d_w        uint32[n_edges] weights (SSSP only; NULL for CC)
+ *   d_cur      uint32[n_vertices] current values (read only)
+ *   d_next     uint32[n_vertices] next values (written)
+ * d_col_ptr, d_src and d_w must be 16-byte aligned and readable up to
+ * round_up(n_vertices + 1, 4) and round_up(n_edges, 4) elements. n_changed
+ * (host pointer, nullable) receives the number of vertices whose value
+ * changed. The call is enqueued on `stream` (a cudaStream_t, NULL = default
+ * stream) and waits for it before returning.
+ *
+ * The first call on a device looks up the scratch's device address (once per
+ * device); make that first call before any stream capture. Every call clears
+ * the parts of the scratch that must start at zero, but all calls share the
+ * one array: calls that overlap on the GPU race and give wrong results.
+ * Errors: GXP_E_INVAL (sizes, null or misaligned pointers, input beyond the
+ * scratch limit), GXP_E_UNSUPPORTED (other algorithms), GXP_E_BOUNDS (a source
+ * id out of range), GXP_E_TIMEOUT, GXP_E_CUDA. */
+GXP_API gxp_status gxp_superstep_min_noalloc(gxp_algo algo, uint32_t n_vertices, uint64_t n_edges,
+                                             const uint32_t* d_col_ptr, const uint32_t* d_src,
+                                             const uint32_t* d_w, const uint32_t* d_cur,
+                                             uint32_t* d_next, uint64_t* n_changed, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

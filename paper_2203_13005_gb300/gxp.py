@@ -69,6 +69,7 @@ SIGNATURES = [
     ("gxp_run", _I, [_P, _I, _U32, _F, _U32, _P]),
     ("gxp_stats_get", _I, [_P, _P]),
     ("gxp_block_size_model", _I, [_D, _D, _D, _D, _U64, _P, _P, _P]),
+    ("gxp_superstep_min_noalloc", _I, [_I, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
 ]
 
 _lib = None
