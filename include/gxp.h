@@ -90,7 +90,8 @@ typedef enum gxp_dtype { GXP_U32 = 0, GXP_F32 = 1, GXP_F64 = 2 } gxp_dtype;
 
 typedef struct gxp_config {
     uint64_t mem_budget;        /* bytes of device memory the context may hold; 0 = no limit */
-    uint32_t tile_items;        /* merge items (vertices + edges) per edge block; 0 = 2048 */
+    uint32_t tile_items;        /* merge items (vertices + edges) per edge block; 0 = 512;
+                                   tile_items + hub_items <= 3072 */
     uint32_t hub_items;         /* vertices with more in-edges than this are split across
                                    blocks; 0 = tile_items / 2 */
     uint64_t timeout_ns;        /* limit for any device-side wait; 0 = 2e9 (2 s) */
@@ -237,7 +238,7 @@ GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double 
  * from d_cur exactly as gxp_superstep does. It calls no cudaMalloc, cudaFree
  * or allocating library routine. Its scratch is a fixed file-scope device
  * array of about 6.8 MB that every GPU loading libgxp.so holds until the
- * process exits; it limits the input to n_vertices + n_edges <= 2^28
+ * process exits; it limits the input to 4 * n_vertices + n_edges <= 2^28
  * (larger inputs return GXP_E_INVAL).
  *
  * Arguments (all device pointers, on the current CUDA device):
@@ -246,8 +247,9 @@ GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double 
  *   d_w        uint32[n_edges] weights (SSSP only; NULL for CC)
  *   d_cur      uint32[n_vertices] current values (read only)
  *   d_next     uint32[n_vertices] next values (written)
- * d_col_ptr, d_src and d_w must be 16-byte aligned and readable up to
- * round_up(n_vertices + 1, 4) and round_up(n_edges, 4) elements. n_changed
+ * d_col_ptr, d_src, d_w and d_cur must be 16-byte aligned and readable up to
+ * round_up(n_vertices + 1, 4), round_up(n_edges, 4) and round_up(n_vertices, 4)
+ * elements. n_changed
  * (host pointer, nullable) receives the number of vertices whose value
  * changed. The call is enqueued on `stream` (a cudaStream_t, NULL = default
  * stream) and waits for it before returning.

@@ -23,7 +23,7 @@ void cuda_check(cudaError_t e, const char* what) {
 
 namespace {
 
-constexpr uint32_t kDefaultTile = 2048;
+constexpr uint32_t kDefaultTile = 2048;   // edges per hub part; rows above tile/2 in-edges are hubs
 
 inline size_t pad4(size_t n) { return ((n + 3) & ~size_t(3)) + 4; }
 
@@ -45,13 +45,12 @@ Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
     gxp_config_default(&cfg_);
     if (cfg) cfg_ = *cfg;
     if (cfg_.tile_items == 0) cfg_.tile_items = kDefaultTile;
-    if (cfg_.hub_items == 0) cfg_.hub_items = cfg_.tile_items / 4;
-    if (cfg_.hub_items >= cfg_.tile_items) cfg_.hub_items = cfg_.tile_items - 1;
+    if (cfg_.hub_items == 0) cfg_.hub_items = cfg_.tile_items / 2;
     if (cfg_.timeout_ns == 0) cfg_.timeout_ns = 2000000000ull;
     if (cfg_.max_slots == 0) cfg_.max_slots = 64;
     if (cfg_.pipeline_depth == 0) cfg_.pipeline_depth = 3;
-    if ((uint64_t)cfg_.tile_items + cfg_.hub_items > (uint64_t)kMaxTileItems)
-        fail(GXP_E_INVAL, "tile_items + hub_items must not exceed " + std::to_string(kMaxTileItems));
+    if (cfg_.tile_items > (1u << 24) || cfg_.hub_items > (1u << 24))
+        fail(GXP_E_INVAL, "tile_items and hub_items must not exceed 2^24");
     int n_dev = 0;
     cuda_check(cudaGetDeviceCount(&n_dev), "cudaGetDeviceCount");
     if (device < 0 || device >= n_dev) fail(GXP_E_INVAL, "no such CUDA device");
@@ -247,44 +246,94 @@ void Engine::finalize() {
     free_graph_device();
     const uint32_t V = (uint32_t)n_vertices_;
     const uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
-    max_items_ = T + H;
 
-    n_tiles_ = 0;
+
     n_ghost_total_ = 0;
     total_edges_ = 0;
     weighted_ = true;
-    uint32_t max_nt = 0;
     for (auto& hp : parts_) {
-        hp.n_tiles = tile_count(hp.n_own, hp.src.size(), T);
-        hp.tile_base = n_tiles_;
-        n_tiles_ += hp.n_tiles;
-        max_nt = std::max(max_nt, hp.n_tiles);
         hp.ghost_base = n_ghost_total_;
         if ((uint64_t)n_ghost_total_ + hp.ghost_gid.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many cached vertices");
         n_ghost_total_ += (uint32_t)hp.ghost_gid.size();
         total_edges_ += hp.src.size();
         if (hp.w.empty() && !hp.src.empty()) weighted_ = false;
     }
+
+    // Sliced-ELL layout of rows with at most H in-edges (SELL-32-sigma: sorted
+    // by in-degree within windows of kSellWindow rows, 32-row slices stored
+    // column-major); rows with more are hubs, reduced in parts of T edges.
+    std::vector<SellSlice> slices;
+    std::vector<HubPart> hubs;
     std::vector<PartDev> pd(n_parts_);
+    auto upload = [&](const std::vector<uint32_t>& h, size_t n_pad) -> uint32_t* {
+        uint32_t* d = (uint32_t*)dalloc(4 * n_pad);
+        cuda_check(cudaMemsetAsync(d, 0, 4 * n_pad, stream_), "memset");
+        if (!h.empty()) cuda_check(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, stream_), "upload");
+        cuda_check(cudaStreamSynchronize(stream_), "upload");   // the staging vector dies after this
+        return d;
+    };
     for (uint32_t p = 0; p < n_parts_; ++p) {
         HostPart& hp = parts_[p];
-        const size_t ne = hp.src.size();
-        hp.d_col_ptr = (uint32_t*)dalloc(4 * pad4(hp.n_own + 1));
-        hp.d_src = (uint32_t*)dalloc(4 * pad4(ne));
-        cuda_check(cudaMemsetAsync(hp.d_col_ptr, 0, 4 * pad4(hp.n_own + 1), stream_), "memset");
-        cuda_check(cudaMemsetAsync(hp.d_src, 0, 4 * pad4(ne), stream_), "memset");
-        cuda_check(cudaMemcpyAsync(hp.d_col_ptr, hp.col_ptr.data(), 4 * (hp.n_own + 1), cudaMemcpyHostToDevice, stream_), "upload col_ptr");
-        if (ne) cuda_check(cudaMemcpyAsync(hp.d_src, hp.src.data(), 4 * ne, cudaMemcpyHostToDevice, stream_), "upload src");
-        if (!hp.w.empty()) {
-            hp.d_w = (uint32_t*)dalloc(4 * pad4(ne));
-            cuda_check(cudaMemsetAsync(hp.d_w, 0, 4 * pad4(ne), stream_), "memset");
-            cuda_check(cudaMemcpyAsync(hp.d_w, hp.w.data(), 4 * ne, cudaMemcpyHostToDevice, stream_), "upload w");
+        const bool weighted = !hp.w.empty();
+        std::vector<uint32_t> sell_src, sell_w, perm, hsrc, hw, rows;
+        for (uint32_t v = 0; v < hp.n_own; ++v) {
+            const uint32_t b = hp.col_ptr[v], d = hp.col_ptr[v + 1] - b;
+            if (d <= H) continue;
+            const uint32_t np = (d + T - 1) / T;
+            const uint32_t t0 = (uint32_t)hubs.size();
+            for (uint32_t k = 0; k < np; ++k)
+                hubs.push_back(HubPart{v, p, (uint32_t)hsrc.size() + k * T, std::min<uint32_t>(T, d - k * T), t0, np, {0, 0}});
+            hsrc.insert(hsrc.end(), hp.src.begin() + b, hp.src.begin() + b + d);
+            if (weighted) hw.insert(hw.end(), hp.w.begin() + b, hp.w.begin() + b + d);
         }
-        pd[p] = PartDev{hp.d_col_ptr, hp.d_src, hp.d_w, hp.n_own, hp.v_begin,
-                        (uint32_t)hp.ghost_gid.size(), hp.ghost_base, (uint64_t)ne};
+        if (hsrc.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub edges in one partition");
+        auto deg = [&](uint32_t v) { return hp.col_ptr[v + 1] - hp.col_ptr[v]; };
+        for (uint32_t w0 = 0; w0 < hp.n_own; w0 += kSellWindow) {
+            const uint32_t w1 = (uint32_t)std::min<uint64_t>((uint64_t)w0 + kSellWindow, hp.n_own);
+            rows.clear();
+            for (uint32_t v = w0; v < w1; ++v)
+                if (deg(v) <= H) rows.push_back(v);
+            std::stable_sort(rows.begin(), rows.end(), [&](uint32_t x, uint32_t y) { return deg(x) > deg(y); });
+            for (size_t i = 0; i < rows.size(); i += 32) {
+                const size_t n = std::min<size_t>(32, rows.size() - i);
+                const uint32_t width = deg(rows[i]);
+                slices.push_back(SellSlice{p, (uint32_t)perm.size(), width, 0u, (uint64_t)sell_src.size()});
+                for (size_t l = 0; l < 32; ++l) perm.push_back(l < n ? rows[i + l] : kSellPad);
+                for (uint32_t k = 0; k < width; ++k)
+                    for (size_t l = 0; l < 32; ++l) {
+                        const bool has = l < n && k < deg(rows[i + l]);
+                        const uint32_t e = has ? hp.col_ptr[rows[i + l]] + k : 0u;
+                        sell_src.push_back(has ? hp.src[e] : kSellPad);
+                        if (weighted) sell_w.push_back(has ? hp.w[e] : 0u);
+                    }
+            }
+        }
+        // plain CSC copies keep the out-degree pass and the bounds check simple
+        hp.d_col_ptr = upload(hp.col_ptr, pad4(hp.n_own + 1));
+        hp.d_src = upload(hp.src, pad4(hp.src.size()));
+        pd[p] = PartDev{hp.d_col_ptr, hp.d_src, nullptr, hp.n_own, hp.v_begin,
+                        (uint32_t)hp.ghost_gid.size(), hp.ghost_base, (uint64_t)hp.src.size(),
+                        upload(sell_src, pad4(sell_src.size())), weighted ? upload(sell_w, pad4(sell_w.size())) : nullptr,
+                        upload(perm, pad4(perm.size())), upload(hsrc, pad4(hsrc.size())),
+                        weighted ? upload(hw, pad4(hw.size())) : nullptr};
     }
+    // heavy slices first, so the hardware scheduler's tail is made of light ones
+    std::stable_sort(slices.begin(), slices.end(), [](const SellSlice& x, const SellSlice& y) { return x.width > y.width; });
+    if (slices.size() > 0xFFFFFFF0ull || hubs.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "graph too large");
+    n_slices_ = (uint32_t)slices.size();
+    n_hubs_ = (uint32_t)hubs.size();
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
     cuda_check(cudaMemcpyAsync(d_parts_, pd.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_), "upload parts");
+    d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(slices.size(), 1));
+    if (!slices.empty())
+        cuda_check(cudaMemcpyAsync(d_slices_, slices.data(), sizeof(SellSlice) * slices.size(), cudaMemcpyHostToDevice, stream_), "upload slices");
+    const size_t nh1 = std::max<size_t>(hubs.size(), 1);
+    d_hubs_ = (HubPart*)dalloc(sizeof(HubPart) * nh1);
+    if (!hubs.empty())
+        cuda_check(cudaMemcpyAsync(d_hubs_, hubs.data(), sizeof(HubPart) * hubs.size(), cudaMemcpyHostToDevice, stream_), "upload hubs");
+    d_hub_val_ = (uint32_t*)dalloc(4 * nh1);
+    d_hub_arrive_ = (uint32_t*)dalloc(4 * nh1);
+    cuda_check(cudaMemsetAsync(d_hub_arrive_, 0, 4 * nh1, stream_), "memset");
 
     d_ghost_gid_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
     d_ghost_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
@@ -292,38 +341,21 @@ void Engine::finalize() {
         if (!hp.ghost_gid.empty())
             cuda_check(cudaMemcpyAsync(d_ghost_gid_ + hp.ghost_base, hp.ghost_gid.data(), 4 * hp.ghost_gid.size(),
                                        cudaMemcpyHostToDevice, stream_), "upload ghost ids");
-
-    // edge blocks
-    d_tiles_ = (Tile*)dalloc(sizeof(Tile) * std::max<uint32_t>(n_tiles_, 1));
-    uint64_t* d_cuts = nullptr;
-    cuda_check(cudaMalloc(&d_cuts, 8 * ((size_t)max_nt + 2)), "cudaMalloc cuts");
-    for (uint32_t p = 0; p < n_parts_; ++p) {
-        HostPart& hp = parts_[p];
-        cudaError_t e = launch_build_tiles(hp.d_col_ptr, hp.n_own, (uint32_t)hp.src.size(), T, H, p,
-                                           hp.tile_base, hp.n_tiles, d_tiles_ + hp.tile_base, d_cuts, stream_);
-        if (e != cudaSuccess) {
-            cudaFree(d_cuts);
-            cuda_check(e, "build tiles");
-        }
-    }
-    cuda_check(cudaStreamSynchronize(stream_), "build tiles");
-    cudaFree(d_cuts);
-    const size_t nt1 = std::max<uint32_t>(n_tiles_, 1);
-    d_part_head_ = (uint32_t*)dalloc(4 * nt1);
-    d_part_tail_ = (uint32_t*)dalloc(4 * nt1);
-    d_hub_cnt_ = (uint32_t*)dalloc(4 * nt1);
-    cuda_check(cudaMemsetAsync(d_hub_cnt_, 0, 4 * nt1, stream_), "memset");
+    cuda_check(cudaStreamSynchronize(stream_), "upload");
 
     // out-degrees over all partitions' edges
-    d_outdeg_ = (uint32_t*)dalloc(4 * (size_t)V);
-    cuda_check(cudaMemsetAsync(d_outdeg_, 0, 4 * (size_t)V, stream_), "memset");
+    // vertex arrays are padded so 16-byte-aligned bulk copies of any slice stay inside
+    d_outdeg_ = (uint32_t*)dalloc(4 * pad4(V));
+    cuda_check(cudaMemsetAsync(d_outdeg_, 0, 4 * pad4(V), stream_), "memset");
     for (uint32_t p = 0; p < n_parts_; ++p)
         cuda_check(launch_outdeg(pd[p], parts_[p].d_src, d_ghost_gid_ + parts_[p].ghost_base, d_outdeg_, stream_),
                    "out-degrees");
 
     for (int b = 0; b < 2; ++b) {
-        d_own_[b] = (uint32_t*)dalloc(4 * (size_t)V);
-        d_rank_[b] = (float*)dalloc(4 * (size_t)V);
+        d_own_[b] = (uint32_t*)dalloc(4 * pad4(V));
+        d_rank_[b] = (float*)dalloc(4 * pad4(V));
+        cuda_check(cudaMemsetAsync(d_own_[b], 0, 4 * pad4(V), stream_), "memset");
+        cuda_check(cudaMemsetAsync(d_rank_[b], 0, 4 * pad4(V), stream_), "memset");
     }
     d_stats_ = (StepStats*)dalloc(sizeof(StepStats) * kStatRing);
     d_err_ = (uint32_t*)dalloc(4);
@@ -333,7 +365,7 @@ void Engine::finalize() {
             cuda_check(launch_validate_csc(parts_[p].d_col_ptr, parts_[p].n_own, parts_[p].d_src, pd[p].n_edges,
                                            parts_[p].n_own + pd[p].n_ghost, d_err_, stream_), "validate");
     if (n_parts_ > 1) build_caches();
-    cuda_check(cudaStreamSynchronize(stream_), "finalize");
+    cuda_check(cudaStreamSynchronize(stream_), "finalize");   // host staging vectors die after this
     check_device_error();
     finalized_ = true;
 }
@@ -433,10 +465,12 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
                     (algo_ == Algo::PR && g == GXP_GEN_CONTRIB && m == GXP_MERGE_SUM && ap == GXP_APPLY_PAGERANK);
     if (!ok) fail(GXP_E_UNSUPPORTED, "unsupported (msggen, merge, apply) template for this algorithm");
     const int nx = cur_ ^ 1;
-    SuperstepArgs a{};
-    a.tiles = d_tiles_;
+    SellArgs a{};
+    a.slices = d_slices_;
+    a.n_slices = n_slices_;
+    a.hubs = d_hubs_;
+    a.n_hubs = n_hubs_;
     a.parts = d_parts_;
-    a.n_tiles = n_tiles_;
     a.own_cur = d_own_[cur_];
     a.own_nxt = d_own_[nx];
     a.ghost = d_ghost_;
@@ -444,20 +478,17 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
     a.rank_nxt = d_rank_[nx];
     a.outdeg = d_outdeg_;
     a.changed_bits = n_parts_ > 1 ? d_changed_ : nullptr;
-    a.part_head = d_part_head_;
-    a.part_tail = d_part_tail_;
-    a.hub_cnt = d_hub_cnt_;
+    a.hub_val = d_hub_val_;
+    a.hub_arrive = d_hub_arrive_;
     a.stats_in = d_stats_ + (step_ % kStatRing);
     a.stats_out = d_stats_ + ((step_ + 1) % kStatRing);
     a.stats_clear = d_stats_ + ((step_ + 2) % kStatRing);
     a.err = d_err_;
-    a.timeout_ns = cfg_.timeout_ns;
     a.check_bounds = cfg_.check_bounds;
     a.damping = damping_;
     a.inv_n = 1.0 / (double)n_vertices_;
-    a.max_items = max_items_;
     cuda_check(cudaEventRecord(ev_a_, stream_), "event");
-    cuda_check(launch_superstep(algo_, a, superstep_smem_bytes(algo_, max_items_), stream_), "superstep kernel");
+    cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
     if (n_parts_ > 1) {
         SyncArgs s{};
         s.parts = d_parts_;

@@ -31,7 +31,6 @@ struct HostPart {
     uint32_t* d_col_ptr = nullptr;
     uint32_t* d_src = nullptr;
     uint32_t* d_w = nullptr;
-    uint32_t tile_base = 0, n_tiles = 0;
     uint32_t ghost_base = 0;
     uint64_t gdq_base = 0, n_boundary = 0;
 };
@@ -84,9 +83,10 @@ private:
     std::vector<void*> graph_allocs_;
     uint64_t graph_bytes_ = 0;
     PartDev* d_parts_ = nullptr;
-    Tile* d_tiles_ = nullptr;
-    uint32_t n_tiles_ = 0, max_items_ = 0;
-    uint32_t *d_part_head_ = nullptr, *d_part_tail_ = nullptr, *d_hub_cnt_ = nullptr;
+    SellSlice* d_slices_ = nullptr;
+    HubPart* d_hubs_ = nullptr;
+    uint32_t n_slices_ = 0, n_hubs_ = 0;
+    uint32_t *d_hub_val_ = nullptr, *d_hub_arrive_ = nullptr;
     uint32_t* d_outdeg_ = nullptr;
     uint32_t* d_own_[2] = {nullptr, nullptr};
     float* d_rank_[2] = {nullptr, nullptr};

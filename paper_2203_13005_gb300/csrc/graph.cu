@@ -18,29 +18,34 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // -------------------------------------------------------------- tiles
 
-__device__ __forceinline__ uint64_t cut_pos(uint64_t c) { return (c >> 32) + (c & 0xFFFFFFFFull); }
+// Merge-path position of a cut (vertex ends consumed i, edges consumed j): a
+// vertex end weighs kVertexCost items, an edge one.
+__device__ __forceinline__ uint64_t cut_pos(uint64_t c) {
+    return (c >> 32) * kVertexCost + (c & 0xFFFFFFFFull);
+}
 
-// Cut k of the merged sequence (vertex ends + edges) at diagonal k*T, snapped
-// back to the start of the vertex it falls in unless that vertex is a hub
-// (in-degree > H). Packed as (vertex << 32 | edge).
+// Cut k of the merged sequence (vertex ends + edges) at weighted position k*T,
+// clamped before the end of the vertex it falls in and snapped back to the
+// start of that vertex unless it is a hub (in-degree > H). Packed as
+// (vertex << 32 | edge).
 __global__ void k_cuts(const uint32_t* __restrict__ col_ptr, uint32_t n, uint32_t n_edges,
                        uint32_t T, uint32_t H, uint32_t nt, uint64_t* __restrict__ cuts) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k > nt) return;
-    const uint64_t total = (uint64_t)n + n_edges;
+    const uint64_t total = (uint64_t)n * kVertexCost + n_edges;
     const uint64_t D = min((uint64_t)k * T, total);
-    // largest i in [0, n] with i + col_ptr[i] <= D
+    // largest i in [0, n] with i*cost + col_ptr[i] <= D
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         const uint32_t mid = lo + (hi - lo + 1u) / 2u;
-        if ((uint64_t)mid + col_ptr[mid] <= D) lo = mid;
+        if ((uint64_t)mid * kVertexCost + col_ptr[mid] <= D) lo = mid;
         else hi = mid - 1u;
     }
     const uint32_t i = lo;
-    uint64_t j = D - i;
-    if (i < n && j > col_ptr[i]) {
-        const uint32_t deg = col_ptr[i + 1] - col_ptr[i];
-        if (deg <= H) j = col_ptr[i];
+    uint64_t j = D - (uint64_t)i * kVertexCost;
+    if (i < n) {
+        if (j > col_ptr[i + 1]) j = col_ptr[i + 1];   // inside vertex i's end item: cut before it
+        if (j > col_ptr[i] && col_ptr[i + 1] - col_ptr[i] <= H) j = col_ptr[i];
     }
     cuts[k] = ((uint64_t)i << 32) | j;
 }
@@ -75,11 +80,11 @@ __global__ void k_tiles(const uint32_t* __restrict__ col_ptr, uint32_t n, const 
     t.nparts = 0;
     if (t.nv == 0u && t.ne == 0u) t.flags = 0u;
     if (head) {
-        const uint64_t p_first = (uint64_t)i0 + col_ptr[i0];
+        const uint64_t p_first = (uint64_t)i0 * kVertexCost + col_ptr[i0];
         t.hub_t0 = tile_base + upper_bound_cut(cuts, nt, p_first) - 1u;
     }
     if (tail && !(head && t.nv == 1u)) {
-        const uint64_t p_end = (uint64_t)i1 + col_ptr[i1 + 1];
+        const uint64_t p_end = (uint64_t)i1 * kVertexCost + col_ptr[i1 + 1];
         const uint32_t t1 = upper_bound_cut(cuts, nt, p_end) - 1u;
         t.nparts = t1 - k + 1u;
     }
@@ -256,7 +261,7 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
 }  // namespace
 
 uint32_t tile_count(uint32_t n_own, uint64_t n_edges, uint32_t tile_items) {
-    const uint64_t items = (uint64_t)n_own + n_edges;
+    const uint64_t items = (uint64_t)n_own * kVertexCost + n_edges;
     return (uint32_t)((items + tile_items - 1) / tile_items);
 }
 

@@ -14,9 +14,9 @@
 namespace gxp {
 
 constexpr uint32_t kInf = 0xFFFFFFFFu;
-constexpr int kBlock = 256;          // threads per superstep CTA
-constexpr int kMaxIpt = 12;          // merge items per thread (static register budget)
-constexpr int kMaxTileItems = kBlock * kMaxIpt;
+constexpr int kBlock = 128;          // threads per superstep CTA (4 independent warps)
+constexpr uint32_t kVertexCost = 4;  // merge-path weight of a vertex end when cutting tiles
+constexpr int kMaxTileItems = 3072;  // tile_items + hub_items limit (shared-memory budget)
 constexpr int kStatLanes = 64;       // stat accumulators are spread over lanes to
                                      // avoid same-address atomic serialization
 constexpr int kStatRing = 64;        // superstep stat slots kept on the device
@@ -49,9 +49,35 @@ struct Tile {
 constexpr uint32_t kHeadOpen = 1u;
 constexpr uint32_t kTailOpen = 2u;
 
+// Sliced-ELL layout of the non-hub rows (SELL-32-sigma): rows are sorted by
+// in-degree inside windows of kSellWindow rows and grouped into slices of 32;
+// a slice stores its rows' in-edges column-major (edge k of all 32 rows, then
+// edge k+1, ...), padded to the slice's largest degree with kSellPad.
+struct SellSlice {
+    uint32_t part;     // partition index
+    uint32_t row0;     // first entry of the slice in the partition's perm array
+    uint32_t width;    // edges per row slot (the slice's largest in-degree)
+    uint32_t pad0;
+    uint64_t off;      // first element of the slice in the partition's sell arrays
+};
+constexpr uint32_t kSellPad = 0xFFFFFFFFu;   // empty edge slot / empty row slot
+constexpr uint32_t kSellWindow = 65536;      // rows sorted by degree within windows of this size
+
+// A slice of the in-edges of one hub row (in-degree above the SELL limit),
+// reduced by one warp; the last part of a row to arrive combines all parts.
+struct HubPart {
+    uint32_t v;        // partition-local destination vertex
+    uint32_t part;     // partition index
+    uint32_t e0;       // first edge in the partition's hub edge arrays
+    uint32_t ne;       // edges in this part
+    uint32_t t0;       // global index of the row's first part
+    uint32_t nparts;   // parts of this row
+    uint32_t pad[2];
+};
+
 // Per-partition device view (array in device memory, indexed by Tile::part).
 struct PartDev {
-    const uint32_t* col_ptr;   // [n_own + 1], padded to a multiple of 4 + 4
+    const uint32_t* col_ptr;   // [n_own + 1] CSC offsets, padded to a multiple of 4 + 4
     const uint32_t* src;       // [n_edges] local source index, padded likewise
     const uint32_t* w;         // [n_edges] weights or nullptr
     uint32_t n_own;            // owned vertices
@@ -59,6 +85,12 @@ struct PartDev {
     uint32_t n_ghost;          // cached remote vertices (local ids n_own ..)
     uint32_t ghost_base;       // offset of this partition's ghosts in the ghost array
     uint64_t n_edges;
+    // sliced-ELL layout (engine path)
+    const uint32_t* sell_src;  // column-major slices, kSellPad in empty slots
+    const uint32_t* sell_w;    // weights in the same layout, or nullptr
+    const uint32_t* perm;      // slice row slot -> local vertex (kSellPad = empty)
+    const uint32_t* hsrc;      // hub rows' in-edges, row after row
+    const uint32_t* hw;        // and weights, or nullptr
 };
 
 // Accumulators of one superstep (one ring slot).
@@ -76,14 +108,15 @@ struct SuperstepArgs {
     const Tile* tiles;
     const PartDev* parts;
     uint32_t n_tiles;
-    const uint32_t* own_cur;     // [V] current values (u32 or f32 bits), global id order
+    const uint32_t* own_cur;     // [V] current values (u32 or f32 bits), global id order;
+                                 // own_cur, rank_cur and outdeg are padded to a multiple of 4
     uint32_t* own_nxt;           // [V] next values
     const uint32_t* ghost;       // [sum of n_ghost] cached remote values
     const float* rank_cur;       // PageRank ranks [V] (fp32)
     float* rank_nxt;
     const uint32_t* outdeg;      // [V] global out-degree (PageRank)
     uint32_t* changed_bits;      // [ceil(V/32)] or nullptr
-    uint32_t* part_head;         // [n_tiles] hub partials (value bits)
+    uint32_t* part_head;         // [n_tiles] partials of rows split across tiles (value bits)
     uint32_t* part_tail;         // [n_tiles]
     uint32_t* hub_cnt;           // [n_tiles] arrival counters (self-resetting)
     StepStats* stats_in;         // slot of the current state (PageRank: its dangling mass)
@@ -95,6 +128,31 @@ struct SuperstepArgs {
     float damping;
     double inv_n;                // 1 / N
     uint32_t max_items;          // largest tile (merge items)
+};
+
+// Everything the sliced-ELL superstep kernel touches.
+struct SellArgs {
+    const SellSlice* slices;
+    uint32_t n_slices;
+    const HubPart* hubs;
+    uint32_t n_hubs;
+    const PartDev* parts;
+    const uint32_t* own_cur;
+    uint32_t* own_nxt;
+    const uint32_t* ghost;
+    const float* rank_cur;
+    float* rank_nxt;
+    const uint32_t* outdeg;
+    uint32_t* changed_bits;
+    uint32_t* hub_val;           // [n_hubs] published partials (value bits)
+    uint32_t* hub_arrive;        // [n_hubs] arrival counters, indexed by a row's first part
+    StepStats* stats_in;
+    StepStats* stats_out;
+    StepStats* stats_clear;
+    uint32_t* err;
+    uint32_t check_bounds;
+    float damping;
+    double inv_n;
 };
 
 // Arguments of the two sync kernels (changed ∩ boundary -> gdq -> caches).
@@ -137,6 +195,7 @@ cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* g
                                const uint32_t* own_cur, uint32_t* ghost, cudaStream_t s);
 
 cudaError_t launch_superstep(Algo a, const SuperstepArgs& args, size_t smem_bytes, cudaStream_t s);
+cudaError_t launch_superstep_sell(Algo a, const SellArgs& args, cudaStream_t s);
 size_t superstep_smem_bytes(Algo a, uint32_t max_items);
 
 cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);

@@ -26,7 +26,7 @@ namespace {
 
 constexpr uint32_t kNoAllocTileItems = 2048;
 constexpr uint32_t kNoAllocHubItems = 512;
-constexpr uint64_t kNoAllocMaxTiles = 131072;   // n_vertices + n_edges <= 2^28
+constexpr uint64_t kNoAllocMaxTiles = 131072;   // 4 * n_vertices + n_edges <= 2^28
 constexpr uint64_t kHeaderBytes = 4096;          // stats slot, error word, partition view
 constexpr uint64_t kNoAllocScratchBytes =
     kHeaderBytes + kNoAllocMaxTiles * (4 + 4 + 4 + sizeof(Tile)) + 8 * (kNoAllocMaxTiles + 2);
@@ -102,7 +102,8 @@ extern "C" GXP_API gxp_status gxp_superstep_min_noalloc(gxp_algo algo, uint32_t 
     if (n_vertices == 0 || n_vertices >= 0xFFFFFFFFu || n_edges > 0xFFFFFFFFull) return GXP_E_INVAL;
     if (!d_col_ptr || !d_cur || !d_next || (n_edges && !d_src) || (algo == GXP_ALGO_SSSP && n_edges && !d_w))
         return GXP_E_INVAL;
-    if (!aligned16(d_col_ptr) || (d_src && !aligned16(d_src)) || (d_w && !aligned16(d_w))) return GXP_E_INVAL;
+    if (!aligned16(d_col_ptr) || !aligned16(d_cur) || (d_src && !aligned16(d_src)) || (d_w && !aligned16(d_w)))
+        return GXP_E_INVAL;
     const uint32_t n_tiles = tile_count(n_vertices, n_edges, kNoAllocTileItems);
     if ((uint64_t)n_tiles > kNoAllocMaxTiles) return GXP_E_INVAL;   // beyond the scratch's fixed size
     unsigned char* base = nullptr;

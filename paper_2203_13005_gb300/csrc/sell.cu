@@ -1,0 +1,286 @@
+// Superstep kernel over the sliced-ELL layout: MSGGen + MSGMerge + MSGApply
+// (Section IV-A1's algorithm template) in pull form, one warp per work item.
+//
+//  * slice of 32 non-hub rows (the edge block of Section II-B, laid out
+//    column-major): lane i owns row i. For each of the slice's `width` edge
+//    slots the warp reads 32 consecutive source ids (one coalesced 128-byte
+//    load), gathers the sources' values with up to kUnroll independent loads
+//    in flight per lane, and folds the messages into a per-lane register in
+//    the row's edge order (MSGMerge without shuffles or shared memory). Then
+//    each lane applies its row (MSGApply); the changed bits of a warp are
+//    grouped per bitmap word with __match_any_sync and ORed in with one
+//    atomic per word.
+//  * hub part: up to kHubPartEdges in-edges of one high-in-degree row,
+//    reduced lane-strided in registers and by a fixed warp tree; the last part
+//    of a row to arrive combines all parts in part order and applies.
+//
+// Sums run in a fixed order, so fp32 PageRank is deterministic; PageRank's
+// global sums (dangling mass, L1 delta) are exact 64-bit fixed point.
+#include "gxp_internal.hpp"
+
+namespace gxp {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSellBlock = 256;
+constexpr int kSellWarps = kSellBlock / 32;
+
+template <Algo A> struct Ops;
+
+template <> struct Ops<Algo::SSSP> {
+    using T = uint32_t;
+    static constexpr bool kWeighted = true;
+    static constexpr int kUnroll = 8;
+    __device__ static T ident() { return kInf; }
+    __device__ static T combine(T a, T b) { return min(a, b); }
+    __device__ static T from_bits(uint32_t x) { return x; }
+    __device__ static uint32_t to_bits(T x) { return x; }
+    // MSGGen: relax; unreachable sources send nothing.
+    __device__ static T gen(uint32_t du, uint32_t w) {
+        if (du == kInf) return kInf;
+        uint32_t s = du + w;
+        if (s < du || s == kInf) s = kInf - 1u;   // saturate below INF
+        return s;
+    }
+};
+
+template <> struct Ops<Algo::CC> {
+    using T = uint32_t;
+    static constexpr bool kWeighted = false;
+    static constexpr int kUnroll = 8;
+    __device__ static T ident() { return kInf; }
+    __device__ static T combine(T a, T b) { return min(a, b); }
+    __device__ static T from_bits(uint32_t x) { return x; }
+    __device__ static uint32_t to_bits(T x) { return x; }
+    __device__ static T gen(uint32_t lu, uint32_t) { return lu; }
+};
+
+template <> struct Ops<Algo::PR> {
+    using T = float;
+    static constexpr bool kWeighted = false;
+    static constexpr int kUnroll = 8;
+    __device__ static T ident() { return 0.0f; }
+    __device__ static T combine(T a, T b) { return a + b; }
+    __device__ static T from_bits(uint32_t x) { return __uint_as_float(x); }
+    __device__ static uint32_t to_bits(T x) { return __float_as_uint(x); }
+    // The message array already holds r[u] / outdeg(u) (written by Apply).
+    __device__ static T gen(uint32_t cu, uint32_t) { return __uint_as_float(cu); }
+};
+
+__device__ __forceinline__ uint32_t arrive_acq_rel(uint32_t* ctr) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+    return old;
+}
+
+template <class Op>
+__device__ __forceinline__ typename Op::T warp_all(typename Op::T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = Op::combine(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+template <Algo A>
+__global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
+    using Op = Ops<A>;
+    using T = typename Op::T;
+    constexpr int kU = Op::kUnroll;
+    __shared__ unsigned long long s_acc[3];
+    __shared__ uint32_t s_done;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x == 0 && a.stats_clear != nullptr) {
+        // zero the ring slot two supersteps ahead (never read or written by this one)
+        unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats_clear);
+        for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
+    }
+    if (tid == 0) {
+        s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
+        s_done = 0u;
+    }
+    float base = 0.0f;
+    if constexpr (A == Algo::PR) {
+        // (1-d)/N + d*D/N from the exact dangling-mass sum of the current ranks
+        unsigned long long sd = a.stats_in->dangling_fx[lane] + a.stats_in->dangling_fx[lane + 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
+        const double d = (double)a.damping;
+        base = (float)((1.0 - d) * a.inv_n + d * fx_to_double(sd) * a.inv_n);
+    }
+    __syncthreads();
+    const float damping = a.damping;
+
+    uint32_t n_changed = 0;
+    unsigned long long l1 = 0ull, dang = 0ull;
+
+    // MSGApply of local vertex v of partition P with merged message m
+    auto apply = [&](const PartDev& P, uint32_t v, T m) -> bool {
+        const uint32_t gid = P.v_begin + v;
+        if constexpr (A == Algo::PR) {
+            const float rn = fmaf(damping, m, base);
+            const float ro = a.rank_cur[gid];
+            const uint32_t od = a.outdeg[gid];
+            a.rank_nxt[gid] = rn;
+            const float c = od ? __fdiv_rn(rn, (float)od) : 0.0f;
+            const uint32_t cb = __float_as_uint(c);
+            a.own_nxt[gid] = cb;
+            const unsigned long long fn = fx_of(rn), fo = fx_of(ro);
+            l1 += fn > fo ? fn - fo : fo - fn;
+            if (od == 0u) dang += fn;
+            // message changes are tracked only when a bitmap is wanted (partitions)
+            return a.changed_bits != nullptr && cb != a.own_cur[gid];
+        } else {
+            const uint32_t old = a.own_cur[gid];
+            const uint32_t nw = min(old, (uint32_t)m);
+            a.own_nxt[gid] = nw;
+            return nw != old;
+        }
+    };
+    // gather the value of local source u of partition P
+    auto gather = [&](const PartDev& P, uint32_t u, bool& ok) -> uint32_t {
+        ok = true;
+        if (a.check_bounds && u >= P.n_own + P.n_ghost) {
+            atomicOr(a.err, kErrBounds);
+            ok = false;
+            return 0u;
+        }
+        return __ldg(u < P.n_own ? a.own_cur + P.v_begin + u : a.ghost + P.ghost_base + (u - P.n_own));
+    };
+
+    const uint32_t gw = blockIdx.x * kSellWarps + (uint32_t)warp;
+    if (gw < a.n_hubs) {
+        // ============================================================ hub part
+        const HubPart hp = a.hubs[gw];
+        const PartDev P = a.parts[hp.part];
+        const uint32_t* src = P.hsrc + hp.e0;
+        const uint32_t* wts = P.hw + hp.e0;
+        T acc = Op::ident();
+        for (uint32_t jb = 0; jb < hp.ne; jb += 32u * kU) {
+            uint32_t u[kU], x[kU], wv[kU];
+            bool ok[kU];
+#pragma unroll
+            for (int q = 0; q < kU; ++q) {
+                const uint32_t j = jb + (uint32_t)q * 32u + (uint32_t)lane;
+                u[q] = kSellPad;
+                wv[q] = 0u;
+                if (j < hp.ne) {
+                    u[q] = __ldcs(src + j);
+                    if (Op::kWeighted) wv[q] = __ldcs(wts + j);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kU; ++q) x[q] = u[q] != kSellPad ? gather(P, u[q], ok[q]) : (ok[q] = false, 0u);
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+                if (ok[q]) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+        }
+        T total = warp_all<Op>(acc);
+        bool do_apply = hp.nparts == 1u;
+        if (!do_apply) {
+            uint32_t last = 0;
+            if (lane == 0) {
+                __stcg(&a.hub_val[gw], Op::to_bits(total));
+                last = arrive_acq_rel(&a.hub_arrive[hp.t0]) == hp.nparts - 1u ? 1u : 0u;
+            }
+            last = __shfl_sync(kFull, last, 0);
+            if (last) {
+                __threadfence();
+                T tot = Op::ident();   // parts in a fixed order: lane-strided, then a fixed tree
+                for (uint32_t q = (uint32_t)lane; q < hp.nparts; q += 32u)
+                    tot = Op::combine(tot, Op::from_bits(__ldcg(&a.hub_val[hp.t0 + q])));
+                total = warp_all<Op>(tot);
+                if (lane == 0) a.hub_arrive[hp.t0] = 0u;   // ready for the next superstep
+                do_apply = true;
+            }
+        }
+        if (do_apply && lane == 0 && apply(P, hp.v, total)) {
+            ++n_changed;
+            if (a.changed_bits) {
+                const uint32_t g = P.v_begin + hp.v;
+                atomicOr(&a.changed_bits[g >> 5], 1u << (g & 31u));
+            }
+        }
+    } else if (gw - a.n_hubs < a.n_slices) {
+        // =============================================================== slice
+        const SellSlice sl = a.slices[gw - a.n_hubs];
+        const PartDev P = a.parts[sl.part];
+        const uint32_t row = P.perm[sl.row0 + lane];
+        const uint32_t* col = P.sell_src + sl.off + lane;
+        const uint32_t* wcol = P.sell_w + sl.off + lane;
+        T acc = Op::ident();
+        for (uint32_t kb = 0; kb < sl.width; kb += kU) {
+            uint32_t u[kU], x[kU], wv[kU];
+            bool ok[kU];
+#pragma unroll
+            for (int q = 0; q < kU; ++q) {
+                u[q] = kSellPad;
+                wv[q] = 0u;
+                if (kb + q < sl.width) {
+                    u[q] = __ldcs(col + 32u * (kb + q));
+                    if (Op::kWeighted) wv[q] = __ldcs(wcol + 32u * (kb + q));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kU; ++q) x[q] = u[q] != kSellPad ? gather(P, u[q], ok[q]) : (ok[q] = false, 0u);
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+                if (ok[q]) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+        }
+        const bool ch = row != kSellPad && apply(P, row, acc);
+        const unsigned chm = __ballot_sync(kFull, ch);
+        if (lane == 0) n_changed += __popc(chm);
+        if (ch && a.changed_bits) {
+            // one atomic per bitmap word touched by this warp
+            const uint32_t g = P.v_begin + row;
+            const unsigned grp = __match_any_sync(chm, g >> 5);
+            const unsigned bits = __reduce_or_sync(grp, 1u << (g & 31u));
+            if ((uint32_t)lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(&a.changed_bits[g >> 5], bits);
+        }
+    }
+
+    // warp totals -> CTA totals in shared memory; the last warp flushes them
+    unsigned long long c64 = n_changed;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c64 += __shfl_xor_sync(kFull, c64, o);
+        if constexpr (A == Algo::PR) {
+            l1 += __shfl_xor_sync(kFull, l1, o);
+            dang += __shfl_xor_sync(kFull, dang, o);
+        }
+    }
+    if (lane == 0) {
+        if (c64) atomicAdd(&s_acc[0], c64);
+        if (l1) atomicAdd(&s_acc[1], l1);
+        if (dang) atomicAdd(&s_acc[2], dang);
+        __threadfence_block();
+        if (atomicAdd(&s_done, 1u) == (uint32_t)kSellWarps - 1u) {
+            __threadfence_block();
+            const unsigned long long x0 = atomicAdd(&s_acc[0], 0ull), x1 = atomicAdd(&s_acc[1], 0ull),
+                                     x2 = atomicAdd(&s_acc[2], 0ull);
+            const uint32_t ln = blockIdx.x % kStatLanes;
+            if (x0) atomicAdd(&a.stats_out->changed[ln], x0);
+            if (x1) atomicAdd(&a.stats_out->l1_fx[ln], x1);
+            if (x2) atomicAdd(&a.stats_out->dangling_fx[ln], x2);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_superstep_sell(Algo alg, const SellArgs& args, cudaStream_t s) {
+    const uint64_t work = (uint64_t)args.n_hubs + args.n_slices;
+    if (work == 0) {
+        // nothing to compute, but the stat slot two supersteps ahead must still be cleared
+        if (args.stats_clear) return cudaMemsetAsync(args.stats_clear, 0, sizeof(StepStats), s);
+        return cudaSuccess;
+    }
+    const uint32_t grid = (uint32_t)((work + kSellWarps - 1) / kSellWarps);
+    switch (alg) {
+        case Algo::SSSP: k_sell<Algo::SSSP><<<grid, kSellBlock, 0, s>>>(args); break;
+        case Algo::CC: k_sell<Algo::CC><<<grid, kSellBlock, 0, s>>>(args); break;
+        case Algo::PR: k_sell<Algo::PR><<<grid, kSellBlock, 0, s>>>(args); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gxp
