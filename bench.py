@@ -35,7 +35,7 @@ ITERS = 20
 DAMPING = 0.85
 WL = synth.PAGERANK_RMAT22
 PROFILE = os.path.join(REPO, "profiles", "superstep_pagerank_rmat22.txt")
-KERNEL_SRC = os.path.join(REPO, "paper_2203_13005_gb300", "csrc", "superstep.cu")
+KERNEL_SRC = os.path.join(REPO, "paper_2203_13005_gb300", "csrc", "sell.cu")
 
 
 def algorithmic_bytes(n_vertices: int, n_edges: int) -> int:
@@ -296,7 +296,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_launch,
-                         "kernel": "k_superstep<PR>", "avg_launch_us": avg_kernel_s * 1e6},
+                         "kernel": "k_sell<PR>", "avg_launch_us": avg_kernel_s * 1e6},
             "e2e": {"value": ITERS * m / e2e_s / 1e9, "unit": "GTEPS",
                     "h2d_bytes_per_step": 8 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n,
                     "ms_per_step": e2e_s * 1e3},

@@ -276,6 +276,20 @@ void Engine::finalize() {
         HostPart& hp = parts_[p];
         const bool weighted = !hp.w.empty();
         std::vector<uint32_t> sell_src, sell_w, perm, hsrc, hw, rows;
+        // Each row's in-edges in ascending source order: the k-th sources of the
+        // 32 rows of a slice then fall in similar id ranges, so a warp's gathers
+        // share more cache sectors (and hub parts gather near-consecutive ids).
+        std::vector<uint32_t> ssrc(hp.src.size()), sw(weighted ? hp.w.size() : 0), idx;
+        for (uint32_t v = 0; v < hp.n_own; ++v) {
+            const uint32_t b = hp.col_ptr[v], d = hp.col_ptr[v + 1] - b;
+            idx.resize(d);
+            for (uint32_t k = 0; k < d; ++k) idx[k] = b + k;
+            std::stable_sort(idx.begin(), idx.end(), [&](uint32_t x, uint32_t y) { return hp.src[x] < hp.src[y]; });
+            for (uint32_t k = 0; k < d; ++k) {
+                ssrc[b + k] = hp.src[idx[k]];
+                if (weighted) sw[b + k] = hp.w[idx[k]];
+            }
+        }
         for (uint32_t v = 0; v < hp.n_own; ++v) {
             const uint32_t b = hp.col_ptr[v], d = hp.col_ptr[v + 1] - b;
             if (d <= H) continue;
@@ -283,8 +297,8 @@ void Engine::finalize() {
             const uint32_t t0 = (uint32_t)hubs.size();
             for (uint32_t k = 0; k < np; ++k)
                 hubs.push_back(HubPart{v, p, (uint32_t)hsrc.size() + k * T, std::min<uint32_t>(T, d - k * T), t0, np, {0, 0}});
-            hsrc.insert(hsrc.end(), hp.src.begin() + b, hp.src.begin() + b + d);
-            if (weighted) hw.insert(hw.end(), hp.w.begin() + b, hp.w.begin() + b + d);
+            hsrc.insert(hsrc.end(), ssrc.begin() + b, ssrc.begin() + b + d);
+            if (weighted) hw.insert(hw.end(), sw.begin() + b, sw.begin() + b + d);
         }
         if (hsrc.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub edges in one partition");
         auto deg = [&](uint32_t v) { return hp.col_ptr[v + 1] - hp.col_ptr[v]; };
@@ -303,8 +317,8 @@ void Engine::finalize() {
                     for (size_t l = 0; l < 32; ++l) {
                         const bool has = l < n && k < deg(rows[i + l]);
                         const uint32_t e = has ? hp.col_ptr[rows[i + l]] + k : 0u;
-                        sell_src.push_back(has ? hp.src[e] : kSellPad);
-                        if (weighted) sell_w.push_back(has ? hp.w[e] : 0u);
+                        sell_src.push_back(has ? ssrc[e] : kSellPad);
+                        if (weighted) sell_w.push_back(has ? sw[e] : 0u);
                     }
             }
         }
