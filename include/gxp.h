@@ -215,6 +215,45 @@ GXP_API gxp_status gxp_run(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float d
 
 GXP_API gxp_status gxp_stats_get(gxp_ctx* ctx, gxp_stats* out);
 
+/* ------------------------------------------- batched multi-source SSSP -- */
+
+typedef struct gxp_batch_opts {
+    uint32_t streamed;       /* 1: edges stay in pinned host memory and every superstep
+                                streams them through a ring of device buffers (the pipeline
+                                shuffle of Section III-A, Algorithms 1-2); 0: edges resident */
+    uint32_t pipelined;      /* streamed only: 1 = copy of block i+1 overlaps compute of block
+                                i (3-slot ring); 0 = copy, then compute, block by block */
+    uint64_t block_edges;    /* streamed only: edges per block; 0 = choose by the Lemma 1 model
+                                from measured coefficients, then a local sweep (autotuner) */
+    uint32_t use_graph;      /* 1: replay each superstep from a captured CUDA graph */
+    uint32_t max_steps;      /* 0 = run to convergence */
+    uint32_t reserved[6];
+} gxp_batch_opts;
+
+typedef struct gxp_batch_report {
+    uint32_t supersteps;     /* supersteps run, including the final one that changed nothing */
+    uint32_t blocks;         /* edge blocks per superstep (streamed) */
+    uint64_t block_edges;    /* edges per block used */
+    double   ms_total;       /* wall time of the run on the device stream, excluding set-up */
+    double   k1, k2, k3, a;  /* autotuner: per-edge download/compute/upload and per-block cost (ms) */
+    double   model_block_edges;  /* Lemma 1's continuous optimum b_opt (edges) */
+    double   model_ms;       /* the pipeline-time equation's estimate at the chosen block size */
+    double   sweep_best_ms;  /* measured superstep time at the chosen block size (autotuner) */
+    uint64_t edges_per_superstep;
+    uint64_t reserved[6];
+} gxp_batch_report;
+
+/* Multi-source Bellman-Ford (Section V-A runs several SSSP sources at once):
+ * n_sources <= 64 sources advance together, every edge serving all of them.
+ * Requires a single-partition weighted graph. dist_out (host or device,
+ * nullable) receives uint32[n_vertices][n_sources]: dist_out[v*n_sources+s]
+ * is the distance from sources[s] to v (0xFFFFFFFF if unreachable) — equal,
+ * source by source, to gxp_run(GXP_ALGO_SSSP). opts may be NULL (resident
+ * edges, run to convergence); report may be NULL. */
+GXP_API gxp_status gxp_sssp_batch(gxp_ctx* ctx, const uint32_t* sources, uint32_t n_sources,
+                                  uint32_t* dist_out, const gxp_batch_opts* opts,
+                                  gxp_batch_report* report);
+
 /* ----------------------------------------------- block-size model (a8) -- */
 
 /* Lemma 1 (Section III-A, "Block Size Selection"): with per-entity download,

@@ -139,6 +139,11 @@ GXP_API gxp_status gxp_stats_get(gxp_ctx* ctx, gxp_stats* out) {
     return guarded(ctx, [&](gxp::Engine& e) { e.stats(out); });
 }
 
+GXP_API gxp_status gxp_sssp_batch(gxp_ctx* ctx, const uint32_t* sources, uint32_t n_sources, uint32_t* dist_out,
+                                  const gxp_batch_opts* opts, gxp_batch_report* report) {
+    return guarded(ctx, [&](gxp::Engine& e) { e.sssp_batch(sources, n_sources, dist_out, opts, report); });
+}
+
 GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double a, uint64_t d, uint64_t* b,
                                         uint64_t* s, double* t) {
     try {

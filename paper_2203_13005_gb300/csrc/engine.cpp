@@ -82,6 +82,7 @@ void* Engine::dalloc(size_t bytes) {
 }
 
 void Engine::free_graph_device() {
+    free_batch();   // graphs and pinned buffers that refer to the device buffers below
     for (void* p : graph_allocs_) cudaFree(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
@@ -89,6 +90,7 @@ void Engine::free_graph_device() {
         hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
     }
     finalized_ = false;
+    sell_ready_ = false;
     begun_ = false;
 }
 
@@ -238,15 +240,142 @@ void Engine::load_partition(uint32_t part, gxp_format fmt, uint64_t n_edges, con
     build_local(hp, V, n_parts_ > 1, std::move(col_ptr), std::move(gsrc), std::move(w));
 }
 
-// Upload every partition, cut edge blocks, count out-degrees, build caches.
+uint32_t* Engine::upload_u32(const std::vector<uint32_t>& h, size_t n_pad) {
+    uint32_t* d = (uint32_t*)dalloc(4 * std::max<size_t>(n_pad, 1));
+    cuda_check(cudaMemsetAsync(d, 0, 4 * std::max<size_t>(n_pad, 1), stream_), "memset");
+    if (!h.empty()) cuda_check(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, stream_), "upload");
+    cuda_check(cudaStreamSynchronize(stream_), "upload");   // the staging vector may die after this
+    return d;
+}
+
+// Sliced-ELL layout of the rows with at most H in-edges (SELL-32-sigma: rows
+// sorted by in-degree within windows of kSellWindow rows, grouped in 32-row
+// slices stored column-major, each row's in-edges in ascending source order)
+// and hub parts of T edges for the rows with more. Built on first use by a
+// superstep (the batched path does not need it).
+void Engine::build_sell() {
+    const uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
+    std::vector<SellSlice> slices;
+    std::vector<HubPart> hubs;
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        HostPart& hp = parts_[p];
+        const bool weighted = !hp.w.empty();
+        const uint32_t n = hp.n_own;
+        const uint64_t E = hp.src.size();
+        auto deg = [&](uint32_t v) { return hp.col_ptr[v + 1] - hp.col_ptr[v]; };
+        // Each row's in-edges in ascending source order: the k-th sources of the
+        // 32 rows of a slice then fall in similar id ranges, so a warp's gathers
+        // share more cache sectors (and hub parts gather near-consecutive ids).
+        std::vector<uint32_t> ssrc(E), sw(weighted ? E : 0);
+#pragma omp parallel
+        {
+            std::vector<std::pair<uint32_t, uint32_t>> buf;
+#pragma omp for schedule(dynamic, 2048)
+            for (int64_t vi = 0; vi < (int64_t)n; ++vi) {
+                const uint32_t v = (uint32_t)vi, b = hp.col_ptr[v], d = deg(v);
+                buf.resize(d);
+                for (uint32_t k = 0; k < d; ++k) buf[k] = {hp.src[b + k], weighted ? hp.w[b + k] : 0u};
+                std::sort(buf.begin(), buf.end());
+                for (uint32_t k = 0; k < d; ++k) {
+                    ssrc[b + k] = buf[k].first;
+                    if (weighted) sw[b + k] = buf[k].second;
+                }
+            }
+        }
+        // hub rows: parts of T edges
+        std::vector<uint32_t> hsrc, hw;
+        for (uint32_t v = 0; v < n; ++v) {
+            const uint32_t b = hp.col_ptr[v], d = deg(v);
+            if (d <= H) continue;
+            const uint32_t np = (d + T - 1) / T;
+            const uint32_t t0 = (uint32_t)hubs.size();
+            for (uint32_t k = 0; k < np; ++k)
+                hubs.push_back(HubPart{v, p, (uint32_t)hsrc.size() + k * T, std::min<uint32_t>(T, d - k * T), t0, np, {0, 0}});
+            hsrc.insert(hsrc.end(), ssrc.begin() + b, ssrc.begin() + b + d);
+            if (weighted) hw.insert(hw.end(), sw.begin() + b, sw.begin() + b + d);
+        }
+        if (hsrc.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub edges in one partition");
+        // windows: non-hub rows by in-degree, descending (ties by id)
+        const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
+        std::vector<std::vector<uint32_t>> wrows(nw);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t wi = 0; wi < (int64_t)nw; ++wi) {
+            const uint32_t w0 = (uint32_t)wi * kSellWindow;
+            const uint32_t w1 = (uint32_t)std::min<uint64_t>((uint64_t)w0 + kSellWindow, n);
+            auto& rows = wrows[wi];
+            for (uint32_t v = w0; v < w1; ++v)
+                if (deg(v) <= H) rows.push_back(v);
+            std::stable_sort(rows.begin(), rows.end(), [&](uint32_t x, uint32_t y) { return deg(x) > deg(y); });
+        }
+        // slice descriptors and offsets
+        const size_t first_slice = slices.size();
+        std::vector<const uint32_t*> slice_rows;
+        std::vector<uint32_t> slice_n;
+        uint64_t perm_size = 0, sell_size = 0;
+        for (uint32_t wi = 0; wi < nw; ++wi) {
+            const auto& rows = wrows[wi];
+            for (size_t i = 0; i < rows.size(); i += 32) {
+                const uint32_t width = deg(rows[i]);
+                slices.push_back(SellSlice{p, (uint32_t)perm_size, width, 0u, sell_size});
+                slice_rows.push_back(rows.data() + i);
+                slice_n.push_back((uint32_t)std::min<size_t>(32, rows.size() - i));
+                perm_size += 32;
+                sell_size += 32ull * width;
+            }
+        }
+        if (perm_size > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many rows in one partition");
+        std::vector<uint32_t> perm(perm_size), sell_src(sell_size), sell_w(weighted ? sell_size : 0);
+        const int64_t ns = (int64_t)(slices.size() - first_slice);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t si = 0; si < ns; ++si) {
+            const SellSlice& sl = slices[first_slice + si];
+            const uint32_t* rows = slice_rows[si];
+            const uint32_t cnt = slice_n[si];
+            for (uint32_t l = 0; l < 32; ++l) perm[sl.row0 + l] = l < cnt ? rows[l] : kSellPad;
+            for (uint32_t k = 0; k < sl.width; ++k)
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const bool has = l < cnt && k < deg(rows[l]);
+                    const uint32_t e = has ? hp.col_ptr[rows[l]] + k : 0u;
+                    sell_src[sl.off + 32ull * k + l] = has ? ssrc[e] : kSellPad;
+                    if (weighted) sell_w[sl.off + 32ull * k + l] = has ? sw[e] : 0u;
+                }
+        }
+        pd_[p].sell_src = upload_u32(sell_src, pad4(sell_src.size()));
+        pd_[p].sell_w = weighted ? upload_u32(sell_w, pad4(sell_w.size())) : nullptr;
+        pd_[p].perm = upload_u32(perm, pad4(perm.size()));
+        pd_[p].hsrc = upload_u32(hsrc, pad4(hsrc.size()));
+        pd_[p].hw = weighted ? upload_u32(hw, pad4(hw.size())) : nullptr;
+    }
+    // heavy slices first, so the hardware scheduler's tail is made of light ones
+    std::stable_sort(slices.begin(), slices.end(), [](const SellSlice& x, const SellSlice& y) { return x.width > y.width; });
+    if (slices.size() > 0xFFFFFFF0ull || hubs.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "graph too large");
+    n_slices_ = (uint32_t)slices.size();
+    n_hubs_ = (uint32_t)hubs.size();
+    cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
+               "upload parts");
+    d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(slices.size(), 1));
+    if (!slices.empty())
+        cuda_check(cudaMemcpyAsync(d_slices_, slices.data(), sizeof(SellSlice) * slices.size(), cudaMemcpyHostToDevice,
+                                   stream_), "upload slices");
+    const size_t nh1 = std::max<size_t>(hubs.size(), 1);
+    d_hubs_ = (HubPart*)dalloc(sizeof(HubPart) * nh1);
+    if (!hubs.empty())
+        cuda_check(cudaMemcpyAsync(d_hubs_, hubs.data(), sizeof(HubPart) * hubs.size(), cudaMemcpyHostToDevice, stream_),
+                   "upload hubs");
+    d_hub_val_ = (uint32_t*)dalloc(4 * nh1);
+    d_hub_arrive_ = (uint32_t*)dalloc(4 * nh1);
+    cuda_check(cudaMemsetAsync(d_hub_arrive_, 0, 4 * nh1, stream_), "memset");
+    cuda_check(cudaStreamSynchronize(stream_), "upload");   // host vectors die here
+    sell_ready_ = true;
+}
+
+// Upload every partition, count out-degrees, build caches.
 void Engine::finalize() {
     for (uint32_t p = 0; p < n_parts_; ++p)
         if (!parts_[p].loaded) fail(GXP_E_STATE, "partition " + std::to_string(p) + " not loaded");
     cuda_check(cudaStreamSynchronize(stream_), "sync");
     free_graph_device();
     const uint32_t V = (uint32_t)n_vertices_;
-    const uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
-
 
     n_ghost_total_ = 0;
     total_edges_ = 0;
@@ -259,95 +388,21 @@ void Engine::finalize() {
         if (hp.w.empty() && !hp.src.empty()) weighted_ = false;
     }
 
-    // Sliced-ELL layout of rows with at most H in-edges (SELL-32-sigma: sorted
-    // by in-degree within windows of kSellWindow rows, 32-row slices stored
-    // column-major); rows with more are hubs, reduced in parts of T edges.
-    std::vector<SellSlice> slices;
-    std::vector<HubPart> hubs;
-    std::vector<PartDev> pd(n_parts_);
-    auto upload = [&](const std::vector<uint32_t>& h, size_t n_pad) -> uint32_t* {
-        uint32_t* d = (uint32_t*)dalloc(4 * n_pad);
-        cuda_check(cudaMemsetAsync(d, 0, 4 * n_pad, stream_), "memset");
-        if (!h.empty()) cuda_check(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, stream_), "upload");
-        cuda_check(cudaStreamSynchronize(stream_), "upload");   // the staging vector dies after this
-        return d;
-    };
+    pd_.assign(n_parts_, PartDev{});
     for (uint32_t p = 0; p < n_parts_; ++p) {
         HostPart& hp = parts_[p];
-        const bool weighted = !hp.w.empty();
-        std::vector<uint32_t> sell_src, sell_w, perm, hsrc, hw, rows;
-        // Each row's in-edges in ascending source order: the k-th sources of the
-        // 32 rows of a slice then fall in similar id ranges, so a warp's gathers
-        // share more cache sectors (and hub parts gather near-consecutive ids).
-        std::vector<uint32_t> ssrc(hp.src.size()), sw(weighted ? hp.w.size() : 0), idx;
-        for (uint32_t v = 0; v < hp.n_own; ++v) {
-            const uint32_t b = hp.col_ptr[v], d = hp.col_ptr[v + 1] - b;
-            idx.resize(d);
-            for (uint32_t k = 0; k < d; ++k) idx[k] = b + k;
-            std::stable_sort(idx.begin(), idx.end(), [&](uint32_t x, uint32_t y) { return hp.src[x] < hp.src[y]; });
-            for (uint32_t k = 0; k < d; ++k) {
-                ssrc[b + k] = hp.src[idx[k]];
-                if (weighted) sw[b + k] = hp.w[idx[k]];
-            }
-        }
-        for (uint32_t v = 0; v < hp.n_own; ++v) {
-            const uint32_t b = hp.col_ptr[v], d = hp.col_ptr[v + 1] - b;
-            if (d <= H) continue;
-            const uint32_t np = (d + T - 1) / T;
-            const uint32_t t0 = (uint32_t)hubs.size();
-            for (uint32_t k = 0; k < np; ++k)
-                hubs.push_back(HubPart{v, p, (uint32_t)hsrc.size() + k * T, std::min<uint32_t>(T, d - k * T), t0, np, {0, 0}});
-            hsrc.insert(hsrc.end(), ssrc.begin() + b, ssrc.begin() + b + d);
-            if (weighted) hw.insert(hw.end(), sw.begin() + b, sw.begin() + b + d);
-        }
-        if (hsrc.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub edges in one partition");
-        auto deg = [&](uint32_t v) { return hp.col_ptr[v + 1] - hp.col_ptr[v]; };
-        for (uint32_t w0 = 0; w0 < hp.n_own; w0 += kSellWindow) {
-            const uint32_t w1 = (uint32_t)std::min<uint64_t>((uint64_t)w0 + kSellWindow, hp.n_own);
-            rows.clear();
-            for (uint32_t v = w0; v < w1; ++v)
-                if (deg(v) <= H) rows.push_back(v);
-            std::stable_sort(rows.begin(), rows.end(), [&](uint32_t x, uint32_t y) { return deg(x) > deg(y); });
-            for (size_t i = 0; i < rows.size(); i += 32) {
-                const size_t n = std::min<size_t>(32, rows.size() - i);
-                const uint32_t width = deg(rows[i]);
-                slices.push_back(SellSlice{p, (uint32_t)perm.size(), width, 0u, (uint64_t)sell_src.size()});
-                for (size_t l = 0; l < 32; ++l) perm.push_back(l < n ? rows[i + l] : kSellPad);
-                for (uint32_t k = 0; k < width; ++k)
-                    for (size_t l = 0; l < 32; ++l) {
-                        const bool has = l < n && k < deg(rows[i + l]);
-                        const uint32_t e = has ? hp.col_ptr[rows[i + l]] + k : 0u;
-                        sell_src.push_back(has ? ssrc[e] : kSellPad);
-                        if (weighted) sell_w.push_back(has ? sw[e] : 0u);
-                    }
-            }
-        }
-        // plain CSC copies keep the out-degree pass and the bounds check simple
-        hp.d_col_ptr = upload(hp.col_ptr, pad4(hp.n_own + 1));
-        hp.d_src = upload(hp.src, pad4(hp.src.size()));
-        pd[p] = PartDev{hp.d_col_ptr, hp.d_src, nullptr, hp.n_own, hp.v_begin,
-                        (uint32_t)hp.ghost_gid.size(), hp.ghost_base, (uint64_t)hp.src.size(),
-                        upload(sell_src, pad4(sell_src.size())), weighted ? upload(sell_w, pad4(sell_w.size())) : nullptr,
-                        upload(perm, pad4(perm.size())), upload(hsrc, pad4(hsrc.size())),
-                        weighted ? upload(hw, pad4(hw.size())) : nullptr};
+        // plain CSC copies: the out-degree pass and the bounds check read them
+        hp.d_col_ptr = upload_u32(hp.col_ptr, pad4(hp.n_own + 1));
+        hp.d_src = upload_u32(hp.src, pad4(hp.src.size()));
+        pd_[p] = PartDev{hp.d_col_ptr, hp.d_src, nullptr, hp.n_own, hp.v_begin,
+                         (uint32_t)hp.ghost_gid.size(), hp.ghost_base, (uint64_t)hp.src.size(),
+                         nullptr, nullptr, nullptr, nullptr, nullptr};
     }
-    // heavy slices first, so the hardware scheduler's tail is made of light ones
-    std::stable_sort(slices.begin(), slices.end(), [](const SellSlice& x, const SellSlice& y) { return x.width > y.width; });
-    if (slices.size() > 0xFFFFFFF0ull || hubs.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "graph too large");
-    n_slices_ = (uint32_t)slices.size();
-    n_hubs_ = (uint32_t)hubs.size();
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
-    cuda_check(cudaMemcpyAsync(d_parts_, pd.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_), "upload parts");
-    d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(slices.size(), 1));
-    if (!slices.empty())
-        cuda_check(cudaMemcpyAsync(d_slices_, slices.data(), sizeof(SellSlice) * slices.size(), cudaMemcpyHostToDevice, stream_), "upload slices");
-    const size_t nh1 = std::max<size_t>(hubs.size(), 1);
-    d_hubs_ = (HubPart*)dalloc(sizeof(HubPart) * nh1);
-    if (!hubs.empty())
-        cuda_check(cudaMemcpyAsync(d_hubs_, hubs.data(), sizeof(HubPart) * hubs.size(), cudaMemcpyHostToDevice, stream_), "upload hubs");
-    d_hub_val_ = (uint32_t*)dalloc(4 * nh1);
-    d_hub_arrive_ = (uint32_t*)dalloc(4 * nh1);
-    cuda_check(cudaMemsetAsync(d_hub_arrive_, 0, 4 * nh1, stream_), "memset");
+    cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
+               "upload parts");
+    sell_ready_ = false;
+    const std::vector<PartDev>& pd = pd_;
 
     d_ghost_gid_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
     d_ghost_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
@@ -457,6 +512,7 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     if (a == Algo::PR && !(damping >= 0.0f && damping < 1.0f)) fail(GXP_E_INVAL, "damping must be in [0, 1)");
     if (!finalized_) finalize();
     if (a == Algo::SSSP && !weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights on every partition");
+    if (!sell_ready_) build_sell();
     const uint32_t V = (uint32_t)n_vertices_;
     cuda_check(cudaMemsetAsync(d_stats_, 0, sizeof(StepStats) * kStatRing, stream_), "memset");
     cuda_check(launch_init_values(a, V, source, d_own_[0], d_rank_[0], d_outdeg_, d_stats_, stream_), "init values");

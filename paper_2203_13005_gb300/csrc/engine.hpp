@@ -53,6 +53,8 @@ public:
     void get_values(uint32_t part, void* out, uint64_t n);
     void set_values(uint32_t part, const void* in, uint64_t n);
     void stats(gxp_stats* out);
+    void sssp_batch(const uint32_t* sources, uint32_t n_sources, uint32_t* dist_out, const gxp_batch_opts* opts,
+                    gxp_batch_report* rep);
 
     std::string last_error;
     bool poisoned = false;
@@ -63,10 +65,17 @@ private:
     void* dalloc(size_t bytes);
     void free_graph_device();
     void finalize();
+    void build_sell();
     void build_caches();
+    uint32_t* upload_u32(const std::vector<uint32_t>& h, size_t n_pad);
     void account(bool force);
     void check_device_error();
     void copy_in(void* dst, const void* src, size_t bytes);   // host or device src -> host dst
+    void prepare_batch(bool streamed);
+    void free_batch();
+    double time_pipeline(uint64_t block_edges, bool pipelined, bool dry, int reps);
+    void superstep_batch(const std::vector<uint64_t>& cuts, bool streamed, bool pipelined, bool dry, int parity);
+    std::vector<uint64_t> block_cuts(uint64_t block_edges) const;
 
     int device_;
     gxp_config cfg_;
@@ -77,7 +86,8 @@ private:
     uint64_t n_vertices_ = 0;
     uint32_t n_parts_ = 0;
     std::vector<HostPart> parts_;
-    bool have_graph_ = false, finalized_ = false;
+    bool have_graph_ = false, finalized_ = false, sell_ready_ = false;
+    std::vector<PartDev> pd_;   // host copy of the per-partition device views
 
     // device graph-level buffers
     std::vector<void*> graph_allocs_;
@@ -104,6 +114,28 @@ private:
     uint32_t* d_err_ = nullptr;
     bool weighted_ = false;
 
+    // batched multi-source SSSP (single partition)
+    struct Batch {
+        bool ready = false, resident = false, pinned_ready = false;
+        std::vector<uint4> units;          // {dst, first edge, edges, split}
+        std::vector<uint64_t> unit_edge;   // first edge of each unit, + total at the end
+        uint4* d_units = nullptr;
+        uint2* h_edges = nullptr;          // pinned (source, weight) in destination order
+        uint2* d_edges = nullptr;          // resident copy
+        uint2* d_ring[3] = {nullptr, nullptr, nullptr};
+        uint64_t ring_edges = 0;
+        uint32_t* d_dist = nullptr;        // [V][64]
+        uint32_t* d_frontier[2] = {nullptr, nullptr};
+        unsigned long long* d_changed = nullptr;   // per-block counters
+        unsigned long long* h_changed = nullptr;   // pinned mirror (upload stage)
+        uint32_t* d_sources = nullptr;
+        size_t max_blocks = 0;
+        cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+        cudaEvent_t ev_loaded[3] = {}, ev_free[3] = {}, ev_t0 = nullptr, ev_t1 = nullptr;
+        cudaGraphExec_t graph[2] = {nullptr, nullptr};
+        uint64_t graph_block_edges = 0;
+        bool graph_streamed = false, graph_pipelined = false;
+    } batch_;
     // algorithm state
     bool begun_ = false;
     Algo algo_ = Algo::SSSP;

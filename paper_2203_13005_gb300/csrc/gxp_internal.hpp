@@ -155,6 +155,19 @@ struct SellArgs {
     double inv_n;
 };
 
+// Arguments of the batched multi-source SSSP superstep kernel (one edge block).
+constexpr uint32_t kUnitEdges = 256;   // in-edges of one destination per warp work unit
+struct MsArgs {
+    const uint4* units;          // {dst, first edge (global), edges, split-row flag}
+    uint64_t u_begin, u_end;     // this block's units
+    const uint2* edges;          // (source, weight); edges[i] is global edge edge_base + i
+    uint64_t edge_base;
+    uint32_t* dist;              // [V][64]
+    const uint32_t* frontier_cur;
+    uint32_t* frontier_next;
+    unsigned long long* changed; // units that improved a slot (this block's counter)
+};
+
 // Arguments of the two sync kernels (changed ∩ boundary -> gdq -> caches).
 struct SyncArgs {
     const PartDev* parts;
@@ -199,6 +212,12 @@ cudaError_t launch_superstep_sell(Algo a, const SellArgs& args, cudaStream_t s);
 size_t superstep_smem_bytes(Algo a, uint32_t max_items);
 
 cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);
+
+cudaError_t launch_msssp(const MsArgs& a, bool dry, uint32_t grid, cudaStream_t s);
+cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_t* sources, uint32_t n_sources,
+                              uint32_t* frontier, cudaStream_t s);
+cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long* out, cudaStream_t s);
+uint32_t msssp_grid(uint64_t units);
 
 // Fixed point -> double (exact for sums below 2^53 units, else rounded once).
 __host__ __device__ inline double fx_to_double(unsigned long long v) {

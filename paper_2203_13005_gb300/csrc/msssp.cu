@@ -1,0 +1,141 @@
+// Batched multi-source SSSP superstep: up to 64 Bellman-Ford instances (one
+// per source, Section V-A's multi-source SSSP-BF) advance together in one
+// pass over the edges, so every edge block read from memory (or streamed by
+// the pipeline shuffle of Section III-A) serves all sources.
+//
+// Layout: dist[v][64] uint32 (one 256-byte row per vertex); an edge is a
+// (source, weight) uint2 in destination order. Work unit = up to
+// kUnitEdges in-edges of one destination; a warp owns a unit and each lane
+// two source slots:
+//   MSGGen   for each in-edge (u, w) whose source changed in the previous
+//            superstep (frontier bit), the warp reads u's 256-byte row
+//            (coalesced) and adds w, saturating below INF;
+//   MSGMerge per-slot minimum in registers;
+//   MSGApply new = min(old, merged) is stored in place (rows split over
+//            several units use atomicMin), and a destination with any
+//            improved slot sets its frontier bit for the next superstep.
+// In-place updates only ever lower distances, so the fixed point equals the
+// per-source Bellman-Ford result; superstep counts may be below Jacobi's.
+#include <algorithm>
+
+#include "gxp_internal.hpp"
+
+namespace gxp {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kMsBlock = 256;
+constexpr int kEdgeUnroll = 4;
+
+__device__ __forceinline__ uint32_t sat_add(uint32_t d, uint32_t w) {
+    if (d == kInf) return kInf;
+    uint32_t s = d + w;
+    if (s < d || s == kInf) s = kInf - 1u;
+    return s;
+}
+
+template <bool kDry>
+__global__ void __launch_bounds__(kMsBlock) k_msssp(const MsArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp0 = (blockIdx.x * kMsBlock + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * kMsBlock) >> 5;
+    uint32_t changed_units = 0;
+    for (uint64_t k = a.u_begin + warp0; k < a.u_end; k += n_warps) {
+        const uint4 un = a.units[k];   // v, first edge (global), edges, split flag
+        const uint32_t v = un.x, len = un.z;
+        const uint2* e = a.edges + (un.y - a.edge_base);
+        uint2 acc = make_uint2(kInf, kInf);
+        for (uint32_t i = 0; i < len; i += kEdgeUnroll) {
+            uint2 ed[kEdgeUnroll];
+            bool act[kEdgeUnroll];
+#pragma unroll
+            for (int q = 0; q < kEdgeUnroll; ++q) {
+                ed[q] = i + q < len ? __ldg(e + i + q) : make_uint2(0u, 0u);
+                act[q] = false;
+            }
+#pragma unroll
+            for (int q = 0; q < kEdgeUnroll; ++q)
+                if (i + q < len) act[q] = (__ldg(a.frontier_cur + (ed[q].x >> 5)) >> (ed[q].x & 31u)) & 1u;
+            uint2 row[kEdgeUnroll];
+#pragma unroll
+            for (int q = 0; q < kEdgeUnroll; ++q)
+                row[q] = act[q] ? reinterpret_cast<const uint2*>(a.dist)[(uint64_t)ed[q].x * 32u + lane]
+                                : make_uint2(kInf, kInf);
+#pragma unroll
+            for (int q = 0; q < kEdgeUnroll; ++q) {
+                acc.x = min(acc.x, sat_add(row[q].x, ed[q].y));
+                acc.y = min(acc.y, sat_add(row[q].y, ed[q].y));
+            }
+        }
+        if (kDry) {
+            changed_units += (acc.x == 0u && acc.y == 0u);   // keeps the loads live
+            continue;
+        }
+        uint2* mine = reinterpret_cast<uint2*>(a.dist) + (uint64_t)v * 32u + lane;
+        const uint2 old = *mine;
+        const bool better_x = acc.x < old.x, better_y = acc.y < old.y;
+        if (un.w) {   // row split across units: combine with atomics
+            if (better_x) atomicMin(&a.dist[(uint64_t)v * 64u + 2u * lane], acc.x);
+            if (better_y) atomicMin(&a.dist[(uint64_t)v * 64u + 2u * lane + 1u], acc.y);
+        } else if (better_x || better_y) {
+            *mine = make_uint2(min(old.x, acc.x), min(old.y, acc.y));
+        }
+        if (__any_sync(kFull, better_x || better_y)) {
+            if (lane == 0) atomicOr(&a.frontier_next[v >> 5], 1u << (v & 31u));
+            ++changed_units;
+        }
+    }
+    if (lane == 0 && changed_units) atomicAdd(a.changed, (unsigned long long)changed_units);
+}
+
+__global__ void k_msssp_init(uint32_t* dist, uint64_t n_vertices) {
+    const uint64_t total = n_vertices * 64u;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x)
+        dist[i] = kInf;
+}
+
+// slot s of vertex sources[s] starts at 0 and the source is on the frontier
+__global__ void k_msssp_sources(uint32_t* dist, const uint32_t* sources, uint32_t n_sources, uint32_t* frontier) {
+    for (uint32_t s = threadIdx.x; s < n_sources; s += blockDim.x) {
+        dist[(uint64_t)sources[s] * 64u + s] = 0u;
+        atomicOr(&frontier[sources[s] >> 5], 1u << (sources[s] & 31u));
+    }
+}
+
+__global__ void k_popc(const uint32_t* bits, uint64_t words, unsigned long long* out) {
+    unsigned long long c = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+        c += __popc(bits[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+}  // namespace
+
+cudaError_t launch_msssp(const MsArgs& a, bool dry, uint32_t grid, cudaStream_t s) {
+    if (a.u_end <= a.u_begin) return cudaSuccess;
+    if (dry) k_msssp<true><<<grid, kMsBlock, 0, s>>>(a);
+    else k_msssp<false><<<grid, kMsBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_t* sources, uint32_t n_sources,
+                              uint32_t* frontier, cudaStream_t s) {
+    k_msssp_init<<<1216, 256, 0, s>>>(dist, n_vertices);
+    k_msssp_sources<<<1, 64, 0, s>>>(dist, sources, n_sources, frontier);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long* out, cudaStream_t s) {
+    k_popc<<<608, 256, 0, s>>>(bits, words, out);
+    return cudaGetLastError();
+}
+
+uint32_t msssp_grid(uint64_t units) {
+    const uint64_t warps = std::max<uint64_t>(1, units);
+    const uint64_t blocks = (warps + (kMsBlock / 32) - 1) / (kMsBlock / 32);
+    return (uint32_t)std::min<uint64_t>(blocks, 152ull * 8);
+}
+
+}  // namespace gxp

@@ -70,6 +70,7 @@ SIGNATURES = [
     ("gxp_stats_get", _I, [_P, _P]),
     ("gxp_block_size_model", _I, [_D, _D, _D, _D, _U64, _P, _P, _P]),
     ("gxp_superstep_min_noalloc", _I, [_I, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
+    ("gxp_sssp_batch", _I, [_P, _P, _U32, _P, _P, _P]),
 ]
 
 _lib = None
@@ -132,6 +133,19 @@ def block_size_model(k1: float, k2: float, k3: float, a: float, d: int):
     if rc:
         raise GxpError(rc, load().gxp_last_error(None).decode())
     return b.value, s.value, t.value
+
+
+class gxp_batch_opts(C.Structure):
+    _fields_ = [("streamed", C.c_uint32), ("pipelined", C.c_uint32), ("block_edges", C.c_uint64),
+                ("use_graph", C.c_uint32), ("max_steps", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+
+
+class gxp_batch_report(C.Structure):
+    _fields_ = [("supersteps", C.c_uint32), ("blocks", C.c_uint32), ("block_edges", C.c_uint64),
+                ("ms_total", C.c_double), ("k1", C.c_double), ("k2", C.c_double), ("k3", C.c_double),
+                ("a", C.c_double), ("model_block_edges", C.c_double), ("model_ms", C.c_double),
+                ("sweep_best_ms", C.c_double), ("edges_per_superstep", C.c_uint64),
+                ("reserved", C.c_uint64 * 6)]
 
 
 class Context:
@@ -250,6 +264,19 @@ class Context:
         vals = np.empty(max(cnt, 1), dtype=np.float32 if self.algo == GXP_ALGO_PAGERANK else np.uint32)
         self._ck(self.lib.gxp_sync(self.h, part, _ptr(ids), _ptr(vals), cnt, C.byref(n), C.byref(sk)))
         return ids[:cnt], vals[:cnt], bool(sk.value)
+
+    def sssp_batch(self, sources, out=None, streamed=False, pipelined=True, block_edges=0,
+                   use_graph=False, max_steps=0):
+        """Multi-source SSSP: returns (dist uint32[V][n_sources] (or `out`), report dict)."""
+        srcs = np.ascontiguousarray(sources, dtype=np.uint32)
+        if out is None:
+            out = np.empty((self.n_vertices, len(srcs)), dtype=np.uint32)
+        o = gxp_batch_opts()
+        o.streamed, o.pipelined, o.block_edges = int(streamed), int(pipelined), block_edges
+        o.use_graph, o.max_steps = int(use_graph), max_steps
+        r = gxp_batch_report()
+        self._ck(self.lib.gxp_sssp_batch(self.h, _ptr(srcs), len(srcs), _ptr(out), C.byref(o), C.byref(r)))
+        return out, {k: getattr(r, k) for k, _ in gxp_batch_report._fields_ if k != "reserved"}
 
     def stats(self) -> dict:
         s = gxp_stats()
