@@ -251,6 +251,193 @@ def run_cc(args):
     ctx.close()
 
 
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def serve_cpu_baseline(stream, graphs_host, budget_s=20.0):
+    """The oracle answering the served stream in order on this host, one query
+    at a time (single-threaded fp64 C), until about budget_s seconds pass."""
+    import oracle
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(len(stream["t"])):
+        g, kind = int(stream["graph"][i]), int(stream["kind"][i])
+        n, src, dst, w, elig = graphs_host[g]
+        s = int(elig[stream["pick"][i]])
+        if kind == 0:
+            oracle.sssp(n, src, dst, w, s)
+        else:
+            oracle.ppr(n, src, dst, s, synth.SERVE_DAMPING, synth.SERVE_ITERS)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {done} queries of the served stream, in order, one at a time"}
+
+
+def run_serve(args):
+    """Serving: an open-loop Poisson stream of SSSP and personalized-PageRank
+    queries over four resident R-MAT graphs (scales 18/20/22/24), answered by
+    the continuous-batching server; latency = scheduled arrival -> result in
+    pinned host memory. Beside it, the same queries answered one at a time by
+    the single-query engine, and by the server with all of them queued at once."""
+    import threading
+    import torch
+    from paper_2203_13005_gb300 import gxp
+    rate, dur = args.serve_rate, args.serve_seconds
+    ctx = gxp.Context(0)
+    srv = gxp.Server(ctx)
+    engines, elig, host = [], [], []
+    t_load = time.perf_counter()
+    scales = [int(x) for x in args.serve_scales.split(",")]
+    served = [wl for wl in synth.SERVE_GRAPHS if wl.scale in scales]
+    for wl in served:
+        src, dst, w = wl.edges()
+        n = wl.n_vertices
+        srv.add_graph(n, src, dst, w)
+        e = gxp.Context(0)
+        e.create_graph(n, 1)
+        e.load_coo(src, dst, w)
+        engines.append(e)
+        el = np.flatnonzero(np.bincount(src, minlength=n) > 0).astype(np.uint32)
+        elig.append(el)
+        host.append((n, src, dst, w, el) if wl.scale <= 20 and not args.no_cpu_baseline else None)
+        del src, dst, w
+    load_s = time.perf_counter() - t_load
+    srv.start(priorities=args.serve_priorities)
+    stream = synth.serve_stream(rate, dur, [len(e) for e in elig], synth.SERVE_SEED)
+    N = len(stream["t"])
+    srcs = np.array([elig[g][p] for g, p in zip(stream["graph"], stream["pick"])], dtype=np.uint32)
+    nmax = max(wl.n_vertices for wl in served)
+    buf = torch.empty(nmax, dtype=torch.int32, pin_memory=True)
+
+    def submit(i):
+        return srv.submit(int(stream["graph"][i]), int(stream["kind"][i]), int(srcs[i]),
+                          synth.SERVE_DAMPING, synth.SERVE_ITERS)
+
+    # warm-up: every (graph, kind) lane and every single-query engine once
+    for _ in range(args.warmup):
+        for g in range(len(engines)):
+            for kind in (gxp.GXP_QUERY_SSSP, gxp.GXP_QUERY_PPR):
+                srv.poll(srv.submit(g, kind, int(elig[g][0]), synth.SERVE_DAMPING, synth.SERVE_ITERS), buf)
+    for g, e in enumerate(engines):
+        e.run(gxp.GXP_ALGO_SSSP, int(elig[g][0]))
+        e.run(gxp.GXP_ALGO_PPR, int(elig[g][0]), synth.SERVE_DAMPING, synth.SERVE_ITERS)
+
+    # open-loop replay of the stream
+    lock = threading.Lock()
+    qidx = {}
+    lat = np.full(N, np.nan)
+    info = [None] * N
+    finish = [0.0]
+    drain_limit = args.serve_drain
+    t_base = [0.0]
+
+    def collector():
+        got = 0
+        while got < N:
+            q = srv.next_done(1000)
+            if q == 0:
+                if time.perf_counter() - t_base[0] > dur + drain_limit:
+                    break
+                continue
+            with lock:
+                i = qidx.get(q)
+            while i is None:   # submit() returned but the id is not recorded yet
+                time.sleep(1e-5)
+                with lock:
+                    i = qidx.get(q)
+            info[i] = srv.info(q)
+            srv.poll(q, buf)
+            t = time.perf_counter()
+            lat[i] = t - (t_base[0] + stream["t"][i])
+            finish[0] = t
+            got += 1
+
+    col = threading.Thread(target=collector)
+    with ClockSampler(0) as clk:
+        t_base[0] = time.perf_counter() + 0.05
+        col.start()
+        for i in range(N):
+            target = t_base[0] + stream["t"][i]
+            while True:
+                d = target - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(d - 2e-4 if d > 5e-4 else 0)
+            with lock:
+                qidx[submit(i)] = i
+        col.join()
+    rep = srv.report()
+    done = ~np.isnan(lat)
+    lat_ms = lat[done] * 1e3
+    span = finish[0] - t_base[0]
+    by = {}
+    for g, wl in enumerate(served):
+        for kind, kn in ((0, "sssp"), (1, "ppr")):
+            sel = done & (stream["graph"] == g) & (stream["kind"] == kind)
+            by[f"{kn}_rmat{wl.scale}"] = {"n": int(sel.sum()), "p50_ms": _pct(lat[sel] * 1e3, 50),
+                                          "p99_ms": _pct(lat[sel] * 1e3, 99)}
+    qms = [x["queue_ms"] for x in info if x]
+    rms = [x["run_ms"] for x in info if x]
+
+    # closed loop on the first K queries: one at a time vs all queued at once
+    K = min(N, args.serve_closed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(K):
+        e = engines[int(stream["graph"][i])]
+        if stream["kind"][i] == 0:
+            e.run(gxp.GXP_ALGO_SSSP, int(srcs[i]))
+        else:
+            e.run(gxp.GXP_ALGO_PPR, int(srcs[i]), synth.SERVE_DAMPING, synth.SERVE_ITERS)
+        e.values(out=buf[:e.n_vertices].numpy().view(
+            np.float32 if stream["kind"][i] else np.uint32))
+    single_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mine = {submit(i) for i in range(K)}
+    while mine:   # collect in order of completion
+        q = srv.next_done(-1)
+        srv.poll(q, buf)
+        mine.discard(q)
+    batched_s = time.perf_counter() - t0
+
+    base = None
+    if not args.no_cpu_baseline and any(h is not None for h in host):
+        # bounded sample: the stream's queries on the scale-18 and scale-20 graphs
+        keep = np.isin(stream["graph"], [i for i, h in enumerate(host) if h is not None])
+        base = serve_cpu_baseline({k: v[keep] for k, v in stream.items()}, host)
+        base["sample"] += " (its queries on the scale-18 and scale-20 graphs)"
+    line = {
+        "metric": "served-query p50/p99 latency", "value": float(done.sum() / span) if span > 0 else 0.0,
+        "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32+f32", "data": "synthetic",
+        "config": {"workload": "serve_rmat" + "_".join(str(wl.scale) for wl in served), "offered_qps": rate,
+                   "duration_s": dur,
+                   "mix": f"graph uniform over {len(served)}, SSSP/PPR 1:1, sources uniform over out-degree >= 1",
+                   "ppr": {"damping": synth.SERVE_DAMPING, "iters": synth.SERVE_ITERS},
+                   "max_slots": 64, "results_per_graph": 128, "priorities": bool(args.serve_priorities)},
+        "latency": {"p50_ms": _pct(lat_ms, 50), "p90_ms": _pct(lat_ms, 90), "p99_ms": _pct(lat_ms, 99),
+                    "max_ms": float(lat_ms.max()) if len(lat_ms) else None,
+                    "queue_p50_ms": _pct(qms, 50), "queue_p99_ms": _pct(qms, 99),
+                    "run_p50_ms": _pct(rms, 50), "run_p99_ms": _pct(rms, 99), "by_lane": by},
+        "submitted": int(N), "completed": int(done.sum()), "backlog_at_end": int(N - done.sum()),
+        "lane_supersteps": {"sssp": rep["sssp_supersteps"], "ppr": rep["ppr_supersteps"]},
+        "closed_loop": {"queries": int(K), "one_at_a_time_qps": K / single_s, "batched_qps": K / batched_s,
+                        "speedup": single_s / batched_s},
+        "server_device_bytes": rep["device_bytes"], "graph_load_s": load_s,
+        "cpu_baseline": base, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    srv.stop()
+    for e in engines:
+        e.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -260,8 +447,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default=WL.name,
-                    choices=[WL.name, synth.MSSSP_RMAT24.name, synth.CC_ER24_P8.name],
+                    choices=[WL.name, synth.MSSSP_RMAT24.name, synth.CC_ER24_P8.name, "serve"],
                     help="extra workloads print their own line; the default is the headline")
+    ap.add_argument("--serve-rate", type=float, default=synth.SERVE_RATE, help="serve: offered queries/s")
+    ap.add_argument("--serve-seconds", type=float, default=synth.SERVE_SECONDS, help="serve: arrival window")
+    ap.add_argument("--serve-drain", type=float, default=60.0, help="serve: seconds allowed after the window")
+    ap.add_argument("--serve-closed", type=int, default=1000, help="serve: queries of the closed-loop comparison")
+    ap.add_argument("--serve-scales", default="18,20,22,24", help="serve: R-MAT scales of the served graphs")
+    ap.add_argument("--serve-priorities", action="store_true", help="serve: smaller graphs' lanes first")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.warmup < 3:
@@ -275,6 +468,9 @@ def main():
         return
     if args.workload == synth.CC_ER24_P8.name:
         run_cc(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import torch

@@ -58,7 +58,8 @@ typedef enum gxp_algo {
     GXP_ALGO_SSSP = 0,      /* Bellman-Ford shortest paths (Section V-A) */
     GXP_ALGO_CC = 1,        /* min-label propagation = weakly connected components */
     GXP_ALGO_PAGERANK = 2,  /* PageRank with dangling-mass redistribution */
-    GXP_ALGO_PPR = 3        /* personalized PageRank (serving and batches only) */
+    GXP_ALGO_PPR = 3        /* personalized PageRank from `source`: PageRank whose teleport and
+                               dangling mass return to the source (r_0 = e_source) */
 } gxp_algo;
 
 /* The three template functions of Section IV-A1, as built-in operators. */
@@ -75,7 +76,8 @@ typedef enum gxp_merge {
 
 typedef enum gxp_apply {
     GXP_APPLY_MIN = 0,      /* x' = min(x, m); changed if x' != x */
-    GXP_APPLY_PAGERANK = 1  /* r' = (1-d)/N + d (m + D/N), D = dangling mass */
+    GXP_APPLY_PAGERANK = 1  /* r' = (1-d)/N + d (m + D/N), D = dangling mass; personalized
+                               PageRank: r' = d m, plus (1-d) + d D at the source */
 } gxp_apply;
 
 typedef enum gxp_format {
@@ -90,13 +92,14 @@ typedef enum gxp_dtype { GXP_U32 = 0, GXP_F32 = 1, GXP_F64 = 2 } gxp_dtype;
 
 typedef struct gxp_config {
     uint64_t mem_budget;        /* bytes of device memory the context may hold; 0 = no limit */
-    uint32_t tile_items;        /* merge items (vertices + edges) per edge block; 0 = 512;
-                                   tile_items + hub_items <= 3072 */
-    uint32_t hub_items;         /* vertices with more in-edges than this are split across
-                                   blocks; 0 = tile_items / 2 */
+    uint32_t tile_items;        /* in-edges per hub part (a part of a high-in-degree vertex's
+                                   in-edges reduced by one warp); 0 = 2048; <= 2^24 */
+    uint32_t hub_items;         /* vertices with more in-edges than this are hubs, split into
+                                   parts of tile_items edges; the rest are packed into
+                                   32-row sliced-ELL slices; 0 = tile_items / 2; <= 2^24 */
     uint64_t timeout_ns;        /* limit for any device-side wait; 0 = 2e9 (2 s) */
     uint32_t check_bounds;      /* 1: kernels range-check every gathered index */
-    uint32_t max_slots;         /* query slots for serving / batches; 0 = 64 */
+    uint32_t max_slots;         /* unused (serving takes gxp_serve_opts.max_slots); 0 */
     uint32_t pipeline_depth;    /* ring slots of the pipeline shuffle; 0 = 3 */
     uint32_t reserved[7];
 } gxp_config;
@@ -164,8 +167,10 @@ GXP_API gxp_status gxp_load_partition(gxp_ctx* ctx, uint32_t part, gxp_format fm
 
 /* Start an algorithm: set every partition's vertex values to its initial
  * state — SSSP: d[source] = 0, else 0xFFFFFFFF; CC: l[v] = v; PageRank:
- * r[v] = 1/N — and reset the superstep counters. `source` is ignored for CC
- * and PageRank. damping is used by PageRank/PPR (e.g. 0.85). Builds the
+ * r[v] = 1/N; personalized PageRank: r = e_source — and reset the superstep
+ * counters. `source` is ignored for CC and PageRank. damping is used by
+ * PageRank/PPR (e.g. 0.85). PPR runs the PageRank template (CONTRIB, SUM,
+ * PAGERANK) with gxp_superstep(GXP_ALGO_PPR, ...). Builds the
  * partition caches (ghost/mirror tables) on first use. */
 GXP_API gxp_status gxp_begin(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping);
 
@@ -253,6 +258,119 @@ typedef struct gxp_batch_report {
 GXP_API gxp_status gxp_sssp_batch(gxp_ctx* ctx, const uint32_t* sources, uint32_t n_sources,
                                   uint32_t* dist_out, const gxp_batch_opts* opts,
                                   gxp_batch_report* report);
+
+/* -------------------------------------------------------------- serving -- */
+
+/* Continuous batching of queries over graphs resident on the device (the
+ * paper has no serving layer; this follows its multi-query use of one pass
+ * over the edges, Section V-A). Each served graph has one lane per query
+ * kind; a lane runs up to 64 queries as the columns of one [V][64] state
+ * matrix, so every superstep's pass over the edges serves all of them.
+ * Queries that arrive while others run are admitted at the next superstep
+ * boundary once a slot and a result buffer are free (admission by memory: a
+ * query holds one device result buffer of n_vertices x 4 bytes from
+ * admission until its result is collected). A query's result does not
+ * depend on which other queries share its supersteps: every slot computes
+ * from its own column in an order fixed by the edge order, so results are
+ * bit-identical alone and in any mix.
+ *
+ * Threading: gxp_query_submit, gxp_query_poll, gxp_query_next_done,
+ * gxp_query_info_get and gxp_serve_report_get may be called from any number
+ * of threads at once; gxp_serve_add_graph, gxp_serve_start and
+ * gxp_serve_stop from one thread while no other call on the server runs.
+ * These calls report error details through gxp_last_error(NULL) on the
+ * calling thread; they do not touch the context's superstep engine. */
+
+typedef enum gxp_query_kind {
+    GXP_QUERY_SSSP = 0,     /* Bellman-Ford distances from `source` (weighted graphs) */
+    GXP_QUERY_PPR = 1       /* personalized PageRank from `source`: r_0 = e_s,
+                               r_{t+1} = d A^T D^-1 r_t + ((1-d) + d D_t) e_s, where D_t is the
+                               mass of r_t on vertices without out-edges; fp32 ranks, exact
+                               fixed-point D_t; `iters` supersteps */
+} gxp_query_kind;
+
+typedef enum gxp_query_state {
+    GXP_QUERY_QUEUED = 0, GXP_QUERY_RUNNING = 1, GXP_QUERY_DONE = 2, GXP_QUERY_FAILED = 3
+} gxp_query_state;
+
+typedef struct gxp_serve_opts {
+    uint32_t max_slots;          /* queries run at once per (graph, kind), 1..64; 0 = 64 */
+    uint32_t results_per_graph;  /* device result buffers per graph; 0 = 2 * max_slots */
+    uint32_t queue_cap;          /* queries waiting for admission, all graphs; 0 = 2^20 */
+    uint32_t priorities;         /* 1: lanes of graphs with fewer edges get higher CUDA stream
+                                    priority (their short supersteps overtake long ones at block
+                                    boundaries); 0: equal priority */
+    uint32_t reserved[8];
+} gxp_serve_opts;
+
+typedef struct gxp_query_info {
+    uint32_t state;              /* gxp_query_state */
+    uint32_t supersteps;         /* supersteps the query took part in */
+    uint32_t graph;
+    uint32_t kind;               /* gxp_query_kind */
+    uint64_t n_values;           /* result length: n_vertices of the graph */
+    double   queue_ms;           /* submission -> admission */
+    double   run_ms;             /* admission -> result ready on the device */
+    uint64_t reserved[4];
+} gxp_query_info;
+
+typedef struct gxp_serve_report {
+    uint64_t submitted, completed, failed;
+    uint64_t queued, running;    /* now */
+    uint64_t sssp_supersteps;    /* over all graphs since gxp_serve_start */
+    uint64_t ppr_supersteps;
+    uint64_t device_bytes;       /* held by the server */
+    uint64_t reserved[8];
+} gxp_serve_report;
+
+/* Make a graph resident for serving: n_edges directed edges src[i] -> dst[i]
+ * (uint32 ids < n_vertices), weights uint32 (NULL: the graph serves PPR
+ * only). Arrays may be host or device pointers and are copied. *graph
+ * receives the graph's index (0, 1, ... in order of addition). Only before
+ * gxp_serve_start. Errors: GXP_E_INVAL (ids, sizes, more than 2^32 - 1
+ * edges), GXP_E_NOMEM (over the context's mem_budget, which bounds the
+ * server's device memory), GXP_E_STATE (server running). */
+GXP_API gxp_status gxp_serve_add_graph(gxp_ctx* ctx, uint64_t n_vertices, uint64_t n_edges,
+                                       const uint32_t* src, const uint32_t* dst,
+                                       const uint32_t* weights, uint32_t* graph);
+
+/* Allocate the lanes and result pools and start one host thread per lane.
+ * opts may be NULL. Errors: GXP_E_NOMEM, GXP_E_STATE (no graph / running). */
+GXP_API gxp_status gxp_serve_start(gxp_ctx* ctx, const gxp_serve_opts* opts);
+
+/* Stop the lanes: queued and running queries fail with GXP_E_STATE; results
+ * already done stay collectable. The server can be started again. */
+GXP_API gxp_status gxp_serve_stop(gxp_ctx* ctx);
+
+/* Queue a query. damping in [0, 1) (PPR only), iters = PPR supersteps
+ * (0 = 20); both are ignored for SSSP, which runs until no distance of the
+ * query improves. *qid receives its id (never 0). Errors: GXP_E_INVAL
+ * (graph, kind, source, damping), GXP_E_UNSUPPORTED (SSSP on an unweighted
+ * graph), GXP_E_BUSY (queue_cap queries already waiting), GXP_E_STATE (not
+ * started, or a lane failed). */
+GXP_API gxp_status gxp_query_submit(gxp_ctx* ctx, uint32_t graph, gxp_query_kind kind,
+                                    uint32_t source, float damping, uint32_t iters, uint64_t* qid);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: without limit) for query qid.
+ * *done = 1 once its result is ready. Then, if out is non-NULL, the result
+ * (uint32 distances, 0xFFFFFFFF = unreachable, or fp32 ranks; n_vertices
+ * values, cap must be at least that) is copied to out (host or device
+ * memory) and the query is released: its id becomes invalid and its result
+ * buffer returns to the pool. With out = NULL the query stays. A failed
+ * query returns its error (and is released when out is non-NULL).
+ * Errors: GXP_E_INVAL (unknown qid, cap too small). */
+GXP_API gxp_status gxp_query_poll(gxp_ctx* ctx, uint64_t qid, void* out, uint64_t cap,
+                                  int timeout_ms, int* done);
+
+/* Wait up to timeout_ms (< 0: without limit) for a finished (done or failed)
+ * query not yet handed out by this call, in order of completion. *qid
+ * receives its id, or 0 on timeout. */
+GXP_API gxp_status gxp_query_next_done(gxp_ctx* ctx, int timeout_ms, uint64_t* qid);
+
+/* State and timing of a query not yet released. */
+GXP_API gxp_status gxp_query_info_get(gxp_ctx* ctx, uint64_t qid, gxp_query_info* out);
+
+GXP_API gxp_status gxp_serve_report_get(gxp_ctx* ctx, gxp_serve_report* out);
 
 /* ----------------------------------------------- block-size model (a8) -- */
 

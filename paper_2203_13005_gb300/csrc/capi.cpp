@@ -3,11 +3,17 @@
 #include <new>
 #include <string>
 
+#include <memory>
+
 #include "engine.hpp"
+#include "server.hpp"
 
 struct gxp_ctx {
     gxp::Engine eng;
-    gxp_ctx(int device, const gxp_config* cfg) : eng(device, cfg) {}
+    int device;
+    uint64_t mem_budget;
+    std::unique_ptr<gxp::Server> server;   // created by the first gxp_serve_add_graph
+    gxp_ctx(int dev, const gxp_config* cfg) : eng(dev, cfg), device(dev), mem_budget(cfg ? cfg->mem_budget : 0) {}
 };
 
 namespace {
@@ -35,6 +41,33 @@ gxp_status guarded(gxp_ctx* ctx, F&& f) {
         return GXP_E_NOMEM;
     } catch (...) {
         ctx->eng.last_error = "unexpected internal error";
+        return GXP_E_STATE;
+    }
+}
+
+// Serving calls: thread-safe, so errors go to the calling thread's message
+// (gxp_last_error(NULL)) and never poison the superstep engine.
+template <class F>
+gxp_status served(gxp_ctx* ctx, bool create, F&& f) {
+    if (!ctx) {
+        g_init_error = "null context";
+        return GXP_E_INVAL;
+    }
+    try {
+        if (!ctx->server) {
+            if (!create) gxp::fail(GXP_E_STATE, "no graph added for serving");
+            ctx->server = std::make_unique<gxp::Server>(ctx->device, ctx->mem_budget);
+        }
+        f(*ctx->server);
+        return GXP_OK;
+    } catch (const gxp::Error& e) {
+        g_init_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_init_error = "host allocation failed";
+        return GXP_E_NOMEM;
+    } catch (...) {
+        g_init_error = "unexpected internal error";
         return GXP_E_STATE;
     }
 }
@@ -142,6 +175,52 @@ GXP_API gxp_status gxp_stats_get(gxp_ctx* ctx, gxp_stats* out) {
 GXP_API gxp_status gxp_sssp_batch(gxp_ctx* ctx, const uint32_t* sources, uint32_t n_sources, uint32_t* dist_out,
                                   const gxp_batch_opts* opts, gxp_batch_report* report) {
     return guarded(ctx, [&](gxp::Engine& e) { e.sssp_batch(sources, n_sources, dist_out, opts, report); });
+}
+
+GXP_API gxp_status gxp_serve_add_graph(gxp_ctx* ctx, uint64_t n_vertices, uint64_t n_edges, const uint32_t* src,
+                                       const uint32_t* dst, const uint32_t* weights, uint32_t* graph) {
+    return served(ctx, true, [&](gxp::Server& s) {
+        const uint32_t g = s.add_graph(n_vertices, n_edges, src, dst, weights);
+        if (graph) *graph = g;
+    });
+}
+
+GXP_API gxp_status gxp_serve_start(gxp_ctx* ctx, const gxp_serve_opts* opts) {
+    return served(ctx, false, [&](gxp::Server& s) { s.start(opts); });
+}
+
+GXP_API gxp_status gxp_serve_stop(gxp_ctx* ctx) {
+    return served(ctx, false, [&](gxp::Server& s) { s.stop(); });
+}
+
+GXP_API gxp_status gxp_query_submit(gxp_ctx* ctx, uint32_t graph, gxp_query_kind kind, uint32_t source,
+                                    float damping, uint32_t iters, uint64_t* qid) {
+    if (!qid) return GXP_E_INVAL;
+    return served(ctx, false, [&](gxp::Server& s) { *qid = s.submit(graph, kind, source, damping, iters); });
+}
+
+GXP_API gxp_status gxp_query_poll(gxp_ctx* ctx, uint64_t qid, void* out, uint64_t cap, int timeout_ms, int* done) {
+    if (done) *done = 0;
+    return served(ctx, false, [&](gxp::Server& s) {
+        const bool d = s.poll(qid, out, cap, timeout_ms);
+        if (done) *done = d ? 1 : 0;
+    });
+}
+
+GXP_API gxp_status gxp_query_next_done(gxp_ctx* ctx, int timeout_ms, uint64_t* qid) {
+    if (!qid) return GXP_E_INVAL;
+    *qid = 0;
+    return served(ctx, false, [&](gxp::Server& s) { *qid = s.next_done(timeout_ms); });
+}
+
+GXP_API gxp_status gxp_query_info_get(gxp_ctx* ctx, uint64_t qid, gxp_query_info* out) {
+    if (!out) return GXP_E_INVAL;
+    return served(ctx, false, [&](gxp::Server& s) { s.info(qid, out); });
+}
+
+GXP_API gxp_status gxp_serve_report_get(gxp_ctx* ctx, gxp_serve_report* out) {
+    if (!out) return GXP_E_INVAL;
+    return served(ctx, false, [&](gxp::Server& s) { s.report(out); });
 }
 
 GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double a, uint64_t d, uint64_t* b,

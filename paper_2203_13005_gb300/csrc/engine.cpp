@@ -500,7 +500,7 @@ static Algo to_algo(gxp_algo a) {
         case GXP_ALGO_SSSP: return Algo::SSSP;
         case GXP_ALGO_CC: return Algo::CC;
         case GXP_ALGO_PAGERANK: return Algo::PR;
-        case GXP_ALGO_PPR: fail(GXP_E_UNSUPPORTED, "personalized PageRank runs through the query API");
+        case GXP_ALGO_PPR: return Algo::PR;   // PageRank with the teleport returning to one source
         default: fail(GXP_E_INVAL, "unknown algorithm");
     }
 }
@@ -508,17 +508,21 @@ static Algo to_algo(gxp_algo a) {
 void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     if (!have_graph_) fail(GXP_E_STATE, "no graph");
     const Algo a = to_algo(algo);
-    if (a == Algo::SSSP && source >= n_vertices_) fail(GXP_E_INVAL, "source out of range");
+    const bool personalized = algo == GXP_ALGO_PPR;
+    if ((a == Algo::SSSP || personalized) && source >= n_vertices_) fail(GXP_E_INVAL, "source out of range");
     if (a == Algo::PR && !(damping >= 0.0f && damping < 1.0f)) fail(GXP_E_INVAL, "damping must be in [0, 1)");
     if (!finalized_) finalize();
     if (a == Algo::SSSP && !weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights on every partition");
     if (!sell_ready_) build_sell();
     const uint32_t V = (uint32_t)n_vertices_;
     cuda_check(cudaMemsetAsync(d_stats_, 0, sizeof(StepStats) * kStatRing, stream_), "memset");
-    cuda_check(launch_init_values(a, V, source, d_own_[0], d_rank_[0], d_outdeg_, d_stats_, stream_), "init values");
+    const uint32_t ppr_source = personalized ? source : kInf;
+    cuda_check(launch_init_values(a, ppr_source, V, source, d_own_[0], d_rank_[0], d_outdeg_, d_stats_, stream_),
+               "init values");
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
     algo_ = a;
+    ppr_source_ = ppr_source;
     source_ = source;
     damping_ = damping;
     cur_ = 0;
@@ -529,7 +533,8 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
 
 uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply ap, bool want) {
     if (!begun_) fail(GXP_E_STATE, "gxp_begin must come first");
-    if (to_algo(algo) != algo_) fail(GXP_E_INVAL, "algorithm differs from the one begun");
+    if (to_algo(algo) != algo_ || (algo == GXP_ALGO_PPR) != (ppr_source_ != kInf))
+        fail(GXP_E_INVAL, "algorithm differs from the one begun");
     const bool ok = (algo_ == Algo::SSSP && g == GXP_GEN_RELAX && m == GXP_MERGE_MIN && ap == GXP_APPLY_MIN) ||
                     (algo_ == Algo::CC && g == GXP_GEN_LABEL && m == GXP_MERGE_MIN && ap == GXP_APPLY_MIN) ||
                     (algo_ == Algo::PR && g == GXP_GEN_CONTRIB && m == GXP_MERGE_SUM && ap == GXP_APPLY_PAGERANK);
@@ -557,6 +562,7 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
     a.check_bounds = cfg_.check_bounds;
     a.damping = damping_;
     a.inv_n = 1.0 / (double)n_vertices_;
+    a.ppr_source = ppr_source_;
     cuda_check(cudaEventRecord(ev_a_, stream_), "event");
     cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
     if (n_parts_ > 1) {

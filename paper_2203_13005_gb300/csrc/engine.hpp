@@ -140,6 +140,7 @@ private:
     bool begun_ = false;
     Algo algo_ = Algo::SSSP;
     uint32_t source_ = 0;
+    uint32_t ppr_source_ = kInf;   // personalized PageRank: its source; else kInf
     float damping_ = 0.85f;
     int cur_ = 0;
     uint64_t step_ = 0, accounted_ = 0;

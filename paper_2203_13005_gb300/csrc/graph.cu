@@ -117,7 +117,7 @@ __global__ void k_validate(const uint32_t* __restrict__ col_ptr, uint32_t n_own,
 // ------------------------------------------------------- initial values
 
 
-__global__ void k_init_values(int algo, uint32_t n, uint32_t source, uint32_t* own,
+__global__ void k_init_values(int algo, uint32_t ppr_source, uint32_t n, uint32_t source, uint32_t* own,
                               float* rank, const uint32_t* outdeg, StepStats* st) {
     unsigned long long dang = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
@@ -126,7 +126,8 @@ __global__ void k_init_values(int algo, uint32_t n, uint32_t source, uint32_t* o
         } else if (algo == (int)Algo::CC) {
             own[v] = v;
         } else {
-            const float r0 = (float)(1.0 / (double)n);
+            // PageRank: r_0 = 1/N everywhere; personalized PageRank: r_0 = e_source
+            const float r0 = ppr_source == kInf ? (float)(1.0 / (double)n) : (v == ppr_source ? 1.0f : 0.0f);
             rank[v] = r0;
             const uint32_t od = outdeg[v];
             own[v] = __float_as_uint(od ? __fdiv_rn(r0, (float)od) : 0.0f);
@@ -292,11 +293,11 @@ cudaError_t launch_validate_csc(const uint32_t* col_ptr, uint32_t n_own, const u
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_values(Algo a, uint32_t n, uint32_t source, uint32_t* own, float* rank,
+cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n, uint32_t source, uint32_t* own, float* rank,
                                const uint32_t* outdeg, StepStats* st, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 152u * 8);
-    k_init_values<<<blocks, 256, 0, s>>>((int)a, n, source, own, rank, outdeg, st);
+    k_init_values<<<blocks, 256, 0, s>>>((int)a, ppr_source, n, source, own, rank, outdeg, st);
     return cudaGetLastError();
 }
 

@@ -153,6 +153,7 @@ struct SellArgs {
     uint32_t check_bounds;
     float damping;
     double inv_n;
+    uint32_t ppr_source;         // PageRank: kInf; personalized PageRank: the source vertex
 };
 
 // Arguments of the batched multi-source SSSP superstep kernel (one edge block).
@@ -166,6 +167,36 @@ struct MsArgs {
     const uint32_t* frontier_cur;
     uint32_t* frontier_next;
     unsigned long long* changed; // units that improved a slot (this block's counter)
+    uint32_t* slot_improved;     // nullable: [2] bit s of word 0 / s - 32 of word 1 = slot s improved
+    uint64_t idle_mask;          // slots to skip (no query in them); 0 = compute all 64
+};
+
+// Finished query slots whose columns are copied out as result vectors.
+struct GatherList {
+    uint32_t n;
+    uint32_t slot[64];
+    uint32_t* out[64];
+};
+
+// Arguments of the personalized-PageRank superstep over 64 query slots
+// (serving). Matrices are [V][64] fp32, one 256-byte row per vertex.
+struct PprArgs {
+    const uint4* units;              // {dst, first edge, edges, partial index + 1 | 0}
+    uint64_t n_units;                // covers every vertex (empty rows too)
+    const uint32_t* src;             // source id of each edge, destination order
+    const uint2* split_rows;         // [n_split_rows + 1] {row, first partial}; last .y = n_partials
+    uint32_t n_split_rows;
+    const float* inv_outdeg;         // [V] 1 / outdeg, 0 for vertices without out-edges
+    const float* msg_cur;            // [V][64] r_t / outdeg
+    float* msg_nxt;                  // [V][64]
+    float* rank;                     // [V][64] r_{t+1}, written for slots in finish_mask
+    float* partial;                  // [n_partials][64]
+    const unsigned long long* dang_cur;   // [64] exact dangling mass of r_t per slot
+    unsigned long long* dang_next;        // [64] (zeroed before the superstep)
+    const float* slot_damping;       // [64]
+    const uint32_t* slot_source;     // [64]
+    uint64_t active_mask;            // slots holding a query
+    uint64_t finish_mask;            // slots whose last superstep this is
 };
 
 // Arguments of the two sync kernels (changed ∩ boundary -> gdq -> caches).
@@ -201,7 +232,7 @@ cudaError_t launch_outdeg(const PartDev& p, const uint32_t* d_src, const uint32_
 cudaError_t launch_validate_csc(const uint32_t* d_col_ptr, uint32_t n_own, const uint32_t* d_src,
                                 uint64_t n_edges, uint32_t n_local, uint32_t* d_err, cudaStream_t s);
 
-cudaError_t launch_init_values(Algo a, uint32_t n_vertices, uint32_t source,
+cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n_vertices, uint32_t source,
                                uint32_t* own_cur, float* rank_cur, const uint32_t* outdeg,
                                StepStats* stats0, cudaStream_t s);
 cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* ghost_gid_all,
@@ -218,6 +249,19 @@ cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_
                               uint32_t* frontier, cudaStream_t s);
 cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long* out, cudaStream_t s);
 uint32_t msssp_grid(uint64_t units);
+
+// serving (serve.cu): 64-slot personalized PageRank and slot management
+cudaError_t launch_ppr_superstep(const PprArgs& a, cudaStream_t s);
+uint32_t serve_grid(uint64_t warp_items);   // short-lived blocks for lanes sharing the GPU
+// slots in `mask` start a new query: PPR columns get the messages of
+// r_0 = e_src and its exact dangling mass; slot_source holds the sources
+cudaError_t launch_ppr_slots_init(float* msg_cur, const float* inv_outdeg, uint64_t n_vertices, uint64_t mask,
+                                  const uint32_t* slot_source, unsigned long long* dang_cur, cudaStream_t s);
+// SSSP columns in `mask` get d = INF except d[src] = 0; sources join the frontier
+cudaError_t launch_sssp_slots_init(uint32_t* dist, uint64_t n_vertices, uint64_t mask, const uint32_t* slot_source,
+                                   uint32_t* frontier, cudaStream_t s);
+// column slot[j] of mat[V][64] -> out[j][0..V) for j < n (row-tile transpose)
+cudaError_t launch_gather_columns(const uint32_t* mat, uint64_t n_vertices, const GatherList& list, cudaStream_t s);
 
 // Fixed point -> double (exact for sums below 2^53 units, else rounded once).
 __host__ __device__ inline double fx_to_double(unsigned long long v) {

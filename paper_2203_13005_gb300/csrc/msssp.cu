@@ -7,15 +7,19 @@
 // (source, weight) uint2 in destination order. Work unit = up to
 // kUnitEdges in-edges of one destination; a warp owns a unit and each lane
 // two source slots:
-//   MSGGen   for each in-edge (u, w) whose source changed in the previous
-//            superstep (frontier bit), the warp reads u's 256-byte row
-//            (coalesced) and adds w, saturating below INF;
+//   MSGGen   the warp reads 32 in-edges at once (one per lane, coalesced)
+//            and tests each source against the frontier (changed in the
+//            previous superstep); for the active ones only, taken from the
+//            ballot mask and broadcast by shuffle, it reads u's 256-byte row
+//            (coalesced, 8 rows in flight) and adds w, saturating below INF.
+//            A unit with no active in-edge ends there (no row traffic);
 //   MSGMerge per-slot minimum in registers;
 //   MSGApply new = min(old, merged) is stored in place (rows split over
 //            several units use atomicMin), and a destination with any
 //            improved slot sets its frontier bit for the next superstep.
-// In-place updates only ever lower distances, so the fixed point equals the
-// per-source Bellman-Ford result; superstep counts may be below Jacobi's.
+// Slots in idle_mask (no query) are skipped. In-place updates only ever
+// lower distances, so the fixed point equals the per-source Bellman-Ford
+// result; superstep counts may be below Jacobi's.
 #include <algorithm>
 
 #include "gxp_internal.hpp"
@@ -25,7 +29,7 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMsBlock = 256;
-constexpr int kEdgeUnroll = 4;
+constexpr int kRowsInFlight = 8;   // source rows gathered at once per warp
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t d, uint32_t w) {
     if (d == kInf) return kInf;
@@ -35,8 +39,15 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t d, uint32_t w) {
 }
 
 template <bool kDry>
-__global__ void __launch_bounds__(kMsBlock) k_msssp(const MsArgs a) {
+__global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
+    __shared__ uint32_t s_imp[2];
+    __shared__ unsigned long long s_changed;
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 2) s_imp[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_changed = 0ull;
+    __syncthreads();
+    const bool live = ((~a.idle_mask >> (2 * lane)) & 3ull) != 0ull;   // either of my 2 slots busy
+    uint32_t imp_lo = 0u, imp_hi = 0u;   // improved slots 0..31 / 32..63 (bit = slot)
     const uint32_t warp0 = (blockIdx.x * kMsBlock + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * kMsBlock) >> 5;
     uint32_t changed_units = 0;
@@ -45,47 +56,77 @@ __global__ void __launch_bounds__(kMsBlock) k_msssp(const MsArgs a) {
         const uint32_t v = un.x, len = un.z;
         const uint2* e = a.edges + (un.y - a.edge_base);
         uint2 acc = make_uint2(kInf, kInf);
-        for (uint32_t i = 0; i < len; i += kEdgeUnroll) {
-            uint2 ed[kEdgeUnroll];
-            bool act[kEdgeUnroll];
-#pragma unroll
-            for (int q = 0; q < kEdgeUnroll; ++q) {
-                ed[q] = i + q < len ? __ldg(e + i + q) : make_uint2(0u, 0u);
-                act[q] = false;
+        bool any = false;
+        for (uint32_t base = 0; base < len; base += 32u) {
+            // 32 edges at once, one per lane (coalesced), each tested against the frontier
+            uint2 my = make_uint2(0u, 0u);
+            bool act = false;
+            if (base + lane < len) {
+                my = __ldg(e + base + lane);
+                act = (__ldg(a.frontier_cur + (my.x >> 5)) >> (my.x & 31u)) & 1u;
             }
+            uint32_t mask = __ballot_sync(kFull, act);
+            any |= mask != 0u;
+            while (mask) {
+                // the active edges, kRowsInFlight source rows loaded at a time
+                int idx[kRowsInFlight];
 #pragma unroll
-            for (int q = 0; q < kEdgeUnroll; ++q)
-                if (i + q < len) act[q] = (__ldg(a.frontier_cur + (ed[q].x >> 5)) >> (ed[q].x & 31u)) & 1u;
-            uint2 row[kEdgeUnroll];
+                for (int q = 0; q < kRowsInFlight; ++q) {
+                    idx[q] = mask ? __ffs(mask) - 1 : -1;
+                    mask &= mask - 1u;
+                }
+                uint2 ed[kRowsInFlight], row[kRowsInFlight];
 #pragma unroll
-            for (int q = 0; q < kEdgeUnroll; ++q)
-                row[q] = act[q] ? reinterpret_cast<const uint2*>(a.dist)[(uint64_t)ed[q].x * 32u + lane]
-                                : make_uint2(kInf, kInf);
+                for (int q = 0; q < kRowsInFlight; ++q) {
+                    ed[q].x = __shfl_sync(kFull, my.x, idx[q] & 31);
+                    ed[q].y = __shfl_sync(kFull, my.y, idx[q] & 31);
+                }
 #pragma unroll
-            for (int q = 0; q < kEdgeUnroll; ++q) {
-                acc.x = min(acc.x, sat_add(row[q].x, ed[q].y));
-                acc.y = min(acc.y, sat_add(row[q].y, ed[q].y));
+                for (int q = 0; q < kRowsInFlight; ++q)
+                    row[q] = (idx[q] >= 0 && live)
+                                 ? reinterpret_cast<const uint2*>(a.dist)[(uint64_t)ed[q].x * 32u + lane]
+                                 : make_uint2(kInf, kInf);
+#pragma unroll
+                for (int q = 0; q < kRowsInFlight; ++q) {
+                    acc.x = min(acc.x, sat_add(row[q].x, ed[q].y));
+                    acc.y = min(acc.y, sat_add(row[q].y, ed[q].y));
+                }
             }
         }
+        if (!any) continue;   // no in-edge from the frontier: nothing to merge or apply
         if (kDry) {
             changed_units += (acc.x == 0u && acc.y == 0u);   // keeps the loads live
             continue;
         }
-        uint2* mine = reinterpret_cast<uint2*>(a.dist) + (uint64_t)v * 32u + lane;
-        const uint2 old = *mine;
-        const bool better_x = acc.x < old.x, better_y = acc.y < old.y;
-        if (un.w) {   // row split across units: combine with atomics
-            if (better_x) atomicMin(&a.dist[(uint64_t)v * 64u + 2u * lane], acc.x);
-            if (better_y) atomicMin(&a.dist[(uint64_t)v * 64u + 2u * lane + 1u], acc.y);
-        } else if (better_x || better_y) {
-            *mine = make_uint2(min(old.x, acc.x), min(old.y, acc.y));
+        uint32_t pair = 0u;   // my 2 slots that improved
+        if (live) {
+            uint2* mine = reinterpret_cast<uint2*>(a.dist) + (uint64_t)v * 32u + lane;
+            const uint2 old = *mine;
+            pair = (acc.x < old.x ? 1u : 0u) | (acc.y < old.y ? 2u : 0u);
+            if (un.w) {   // row split across units: combine with atomics
+                if (pair & 1u) atomicMin(&a.dist[(uint64_t)v * 64u + 2u * lane], acc.x);
+                if (pair & 2u) atomicMin(&a.dist[(uint64_t)v * 64u + 2u * lane + 1u], acc.y);
+            } else if (pair) {
+                *mine = make_uint2(min(old.x, acc.x), min(old.y, acc.y));
+            }
         }
-        if (__any_sync(kFull, better_x || better_y)) {
+        const uint32_t lo = __reduce_or_sync(kFull, lane < 16 ? pair << (2 * lane) : 0u);
+        const uint32_t hi = __reduce_or_sync(kFull, lane >= 16 ? pair << (2 * lane - 32) : 0u);
+        if (lo | hi) {
             if (lane == 0) atomicOr(&a.frontier_next[v >> 5], 1u << (v & 31u));
             ++changed_units;
+            imp_lo |= lo;
+            imp_hi |= hi;
         }
     }
-    if (lane == 0 && changed_units) atomicAdd(a.changed, (unsigned long long)changed_units);
+    // block totals in shared memory, then one global atomic per word and block
+    if (lane == 0 && changed_units) atomicAdd(&s_changed, (unsigned long long)changed_units);
+    if (lane == 0 && imp_lo) atomicOr(&s_imp[0], imp_lo);
+    if (lane == 0 && imp_hi) atomicOr(&s_imp[1], imp_hi);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_changed) atomicAdd(a.changed, s_changed);
+    if (!kDry && a.slot_improved != nullptr && threadIdx.x < 2 && s_imp[threadIdx.x])
+        atomicOr(&a.slot_improved[threadIdx.x], s_imp[threadIdx.x]);
 }
 
 __global__ void k_msssp_init(uint32_t* dist, uint64_t n_vertices) {

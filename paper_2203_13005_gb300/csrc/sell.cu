@@ -98,14 +98,20 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
         s_done = 0u;
     }
-    float base = 0.0f;
+    float base = 0.0f, base_src = 0.0f;
     if constexpr (A == Algo::PR) {
-        // (1-d)/N + d*D/N from the exact dangling-mass sum of the current ranks
+        // from the exact dangling-mass sum D of the current ranks: PageRank
+        // spreads (1-d) + d*D evenly, (1-d)/N + d*D/N to every vertex;
+        // personalized PageRank returns all of it to the source vertex
         unsigned long long sd = a.stats_in->dangling_fx[lane] + a.stats_in->dangling_fx[lane + 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
         const double d = (double)a.damping;
-        base = (float)((1.0 - d) * a.inv_n + d * fx_to_double(sd) * a.inv_n);
+        if (a.ppr_source == kInf) {
+            base = base_src = (float)((1.0 - d) * a.inv_n + d * fx_to_double(sd) * a.inv_n);
+        } else {
+            base_src = (float)((1.0 - d) + d * fx_to_double(sd));
+        }
     }
     __syncthreads();
     const float damping = a.damping;
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
     auto apply = [&](const PartDev& P, uint32_t v, T m) -> bool {
         const uint32_t gid = P.v_begin + v;
         if constexpr (A == Algo::PR) {
-            const float rn = fmaf(damping, m, base);
+            const float rn = fmaf(damping, m, gid == a.ppr_source ? base_src : base);
             const float ro = a.rank_cur[gid];
             const uint32_t od = a.outdeg[gid];
             a.rank_nxt[gid] = rn;

@@ -33,7 +33,11 @@ TEMPLATES = {
     GXP_ALGO_SSSP: (GXP_GEN_RELAX, GXP_MERGE_MIN, GXP_APPLY_MIN),
     GXP_ALGO_CC: (GXP_GEN_LABEL, GXP_MERGE_MIN, GXP_APPLY_MIN),
     GXP_ALGO_PAGERANK: (GXP_GEN_CONTRIB, GXP_MERGE_SUM, GXP_APPLY_PAGERANK),
+    GXP_ALGO_PPR: (GXP_GEN_CONTRIB, GXP_MERGE_SUM, GXP_APPLY_PAGERANK),
 }
+# serving
+GXP_QUERY_SSSP, GXP_QUERY_PPR = 0, 1
+GXP_QUERY_QUEUED, GXP_QUERY_RUNNING, GXP_QUERY_DONE, GXP_QUERY_FAILED = 0, 1, 2, 3
 
 
 class gxp_config(C.Structure):
@@ -71,6 +75,14 @@ SIGNATURES = [
     ("gxp_block_size_model", _I, [_D, _D, _D, _D, _U64, _P, _P, _P]),
     ("gxp_superstep_min_noalloc", _I, [_I, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
     ("gxp_sssp_batch", _I, [_P, _P, _U32, _P, _P, _P]),
+    ("gxp_serve_add_graph", _I, [_P, _U64, _U64, _P, _P, _P, _P]),
+    ("gxp_serve_start", _I, [_P, _P]),
+    ("gxp_serve_stop", _I, [_P]),
+    ("gxp_query_submit", _I, [_P, _U32, _I, _U32, _F, _U32, _P]),
+    ("gxp_query_poll", _I, [_P, _U64, _P, _U64, _I, _P]),
+    ("gxp_query_next_done", _I, [_P, _I, _P]),
+    ("gxp_query_info_get", _I, [_P, _U64, _P]),
+    ("gxp_serve_report_get", _I, [_P, _P]),
 ]
 
 _lib = None
@@ -245,7 +257,7 @@ class Context:
     def values(self, part: int = ALL_PARTS, out=None):
         n = self.n_vertices if part == ALL_PARTS else int(self.bounds[part + 1] - self.bounds[part])
         if out is None:
-            out = np.empty(n, dtype=np.float32 if self.algo == GXP_ALGO_PAGERANK else np.uint32)
+            out = np.empty(n, dtype=np.float32 if self.algo in (GXP_ALGO_PAGERANK, GXP_ALGO_PPR) else np.uint32)
         self._ck(self.lib.gxp_get_values(self.h, part, _ptr(out), n))
         return out
 
@@ -261,7 +273,8 @@ class Context:
             self._ck(rc)
         cnt = n.value
         ids = np.empty(max(cnt, 1), dtype=np.uint32)
-        vals = np.empty(max(cnt, 1), dtype=np.float32 if self.algo == GXP_ALGO_PAGERANK else np.uint32)
+        vals = np.empty(max(cnt, 1), dtype=np.float32 if self.algo in (GXP_ALGO_PAGERANK, GXP_ALGO_PPR)
+                        else np.uint32)
         self._ck(self.lib.gxp_sync(self.h, part, _ptr(ids), _ptr(vals), cnt, C.byref(n), C.byref(sk)))
         return ids[:cnt], vals[:cnt], bool(sk.value)
 
@@ -282,3 +295,89 @@ class Context:
         s = gxp_stats()
         self._ck(self.lib.gxp_stats_get(self.h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in gxp_stats._fields_ if k != "reserved"}
+
+
+class gxp_serve_opts(C.Structure):
+    _fields_ = [("max_slots", C.c_uint32), ("results_per_graph", C.c_uint32), ("queue_cap", C.c_uint32),
+                ("priorities", C.c_uint32), ("reserved", C.c_uint32 * 8)]
+
+
+class gxp_query_info(C.Structure):
+    _fields_ = [("state", C.c_uint32), ("supersteps", C.c_uint32), ("graph", C.c_uint32), ("kind", C.c_uint32),
+                ("n_values", C.c_uint64), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("reserved", C.c_uint64 * 4)]
+
+
+class gxp_serve_report(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("queued", C.c_uint64), ("running", C.c_uint64), ("sssp_supersteps", C.c_uint64),
+                ("ppr_supersteps", C.c_uint64), ("device_bytes", C.c_uint64), ("reserved", C.c_uint64 * 8)]
+
+
+class Server:
+    """Query server of one context (gxp_serve_* / gxp_query_*): graphs made
+    resident, then SSSP / personalized-PageRank queries served by continuous
+    batching. The query methods may be called from several threads."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.n = []   # vertices per graph
+
+    def _ck(self, rc: int):
+        if rc:
+            raise GxpError(rc, self.lib.gxp_last_error(None).decode())
+
+    def add_graph(self, n_vertices: int, src, dst, w=None) -> int:
+        src = src if hasattr(src, "data_ptr") else np.ascontiguousarray(src, dtype=np.uint32)
+        dst = dst if hasattr(dst, "data_ptr") else np.ascontiguousarray(dst, dtype=np.uint32)
+        if w is not None and not hasattr(w, "data_ptr"):
+            w = np.ascontiguousarray(w, dtype=np.uint32)
+        g = C.c_uint32()
+        self._ck(self.lib.gxp_serve_add_graph(self.ctx.h, n_vertices, len(src), _ptr(src), _ptr(dst), _ptr(w),
+                                              C.byref(g)))
+        self.n.append(n_vertices)
+        return g.value
+
+    def start(self, max_slots: int = 0, results_per_graph: int = 0, queue_cap: int = 0, priorities: bool = False):
+        o = gxp_serve_opts()
+        o.max_slots, o.results_per_graph, o.queue_cap = max_slots, results_per_graph, queue_cap
+        o.priorities = int(priorities)
+        self._ck(self.lib.gxp_serve_start(self.ctx.h, C.byref(o)))
+
+    def stop(self):
+        self._ck(self.lib.gxp_serve_stop(self.ctx.h))
+
+    def submit(self, graph: int, kind: int, source: int, damping: float = 0.85, iters: int = 0) -> int:
+        q = C.c_uint64()
+        self._ck(self.lib.gxp_query_submit(self.ctx.h, graph, kind, source, damping, iters, C.byref(q)))
+        return q.value
+
+    def poll(self, qid: int, out=None, timeout_ms: int = -1) -> bool:
+        """Wait for qid; with `out` (numpy or tensor of >= n_vertices 4-byte
+        values) copy the result there and release the query. Returns done."""
+        d = C.c_int()
+        cap = 0 if out is None else (out.numel() if hasattr(out, "numel") else out.size)
+        self._ck(self.lib.gxp_query_poll(self.ctx.h, qid, _ptr(out), cap, timeout_ms, C.byref(d)))
+        return bool(d.value)
+
+    def result(self, qid: int, kind: int, graph: int):
+        """Blocking: the result of qid as a new numpy array (uint32 or float32)."""
+        out = np.empty(self.n[graph], dtype=np.uint32 if kind == GXP_QUERY_SSSP else np.float32)
+        self.poll(qid, out, -1)
+        return out
+
+    def next_done(self, timeout_ms: int = -1) -> int:
+        q = C.c_uint64()
+        self._ck(self.lib.gxp_query_next_done(self.ctx.h, timeout_ms, C.byref(q)))
+        return q.value
+
+    def info(self, qid: int) -> dict:
+        i = gxp_query_info()
+        self._ck(self.lib.gxp_query_info_get(self.ctx.h, qid, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in gxp_query_info._fields_ if k != "reserved"}
+
+    def report(self) -> dict:
+        r = gxp_serve_report()
+        self._ck(self.lib.gxp_serve_report_get(self.ctx.h, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in gxp_serve_report._fields_ if k != "reserved"}

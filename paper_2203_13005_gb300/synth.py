@@ -120,6 +120,24 @@ def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int) -> np.ndar
     return t[t < duration_s]
 
 
+def serve_stream(rate_per_s: float, duration_s: float, n_eligible, seed: int) -> dict:
+    """The served query stream: Poisson arrival times; per query a graph
+    uniform over len(n_eligible) graphs, a kind (0 = SSSP, 1 = PPR) with
+    probability 1/2 each, and the index of its source among graph g's
+    n_eligible[g] eligible sources (uniform). Each attribute has its own
+    counter range of the seeded stream."""
+    t = poisson_arrivals(rate_per_s, duration_s, seed)
+    k = len(t)
+    u_g = stream_unit(seed ^ SOURCE_TAG, 0, k)
+    u_k = stream_unit(seed ^ SOURCE_TAG, 1 << 40, k)
+    u_s = stream_unit(seed ^ SOURCE_TAG, 2 << 40, k)
+    n_g = len(n_eligible)
+    g = np.minimum((u_g * n_g).astype(np.int64), n_g - 1)
+    cnt = np.asarray(n_eligible, dtype=np.int64)[g]
+    pick = np.minimum((u_s * cnt).astype(np.int64), cnt - 1)
+    return {"t": t, "graph": g, "kind": (u_k >= 0.5).astype(np.int64), "pick": pick}
+
+
 def omp_threads() -> int:
     return int(_load().gxs_omp_threads())
 
@@ -163,7 +181,13 @@ PAGERANK_RMAT22 = Workload("pagerank_rmat22", "rmat", 22, 1 << 26, 0x67700002)
 CC_ER24_P8 = Workload("cc_er24_8parts", "er", 24, 1 << 28, 0x67700003, parts=8)
 MSSSP_RMAT24 = Workload("msssp64_rmat24", "rmat", 24, 1 << 28, 0x67700004, 1, 255)
 SERVE_SEED = 0x67700005
-SERVE_GRAPHS = tuple(Workload(f"serve_rmat{s}", "rmat", s, 16 << s, 0x67700000 + s, 1, 255)
+# served graphs: R-MAT scales 18/20/22/24, edge factor 16, w ~ U{1..255};
+# seeds 0x67700018, 0x67700020, 0x67700022, 0x67700024 (the scale in hex digits)
+SERVE_GRAPHS = tuple(Workload(f"serve_rmat{s}", "rmat", s, 16 << s, 0x67700000 + int(str(s), 16), 1, 255)
                      for s in (18, 20, 22, 24))
+SERVE_RATE = 2000.0     # queries per second, open-loop Poisson
+SERVE_SECONDS = 60.0
+SERVE_DAMPING = 0.85
+SERVE_ITERS = 20
 
 WORKLOADS = {w.name: w for w in (SSSP_RMAT16, PAGERANK_RMAT22, CC_ER24_P8, MSSSP_RMAT24)}
