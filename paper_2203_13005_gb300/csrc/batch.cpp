@@ -53,6 +53,7 @@ void Engine::prepare_batch(bool streamed) {
     if (!weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights");
     Batch& b = batch_;
     HostPart& hp = parts_[0];
+    ensure_host(hp);
     const uint64_t V = n_vertices_, E = hp.src.size();
     if (!b.ready) {
         b.units.clear();

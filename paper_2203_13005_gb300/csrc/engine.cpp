@@ -65,6 +65,7 @@ Engine::~Engine() {
     cudaSetDevice(device_);
     if (stream_) cudaStreamSynchronize(stream_);
     free_graph_device();
+    for (auto& hp : parts_) release_part(hp);
     if (ev_a_) cudaEventDestroy(ev_a_);
     if (ev_b_) cudaEventDestroy(ev_b_);
     if (own_stream_) cudaStreamDestroy(own_stream_);
@@ -86,9 +87,8 @@ void Engine::free_graph_device() {
     for (void* p : graph_allocs_) cudaFree(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
-    for (auto& hp : parts_) {
-        hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
-    }
+    for (auto& hp : parts_)
+        if (!hp.on_device) hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
     finalized_ = false;
     sell_ready_ = false;
     begun_ = false;
@@ -125,6 +125,7 @@ void Engine::create_graph(uint64_t n, uint32_t n_parts, const uint64_t* part_beg
     }
     if (stream_) cudaStreamSynchronize(stream_);
     free_graph_device();
+    for (auto& hp : parts_) release_part(hp);
     parts_.assign(n_parts, HostPart{});
     for (uint32_t p = 0; p < n_parts; ++p) {
         parts_[p].v_begin = (uint32_t)b[p];
@@ -182,6 +183,10 @@ void Engine::load_partition(uint32_t part, gxp_format fmt, uint64_t n_edges, con
     if (n_edges > 0xFFFFFFFFull) fail(GXP_E_INVAL, "more than 2^32-1 edges in one partition");
     if (n_edges && (!idx0 || !idx1)) fail(GXP_E_INVAL, "null edge array");
     HostPart& hp = parts_[part];
+    if (fmt == GXP_FMT_CSC && n_parts_ == 1) {   // straight to the device
+        load_csc_device(hp, n_edges, idx0, idx1, weights);
+        return;
+    }
     const uint32_t lo = hp.v_begin, n_own = hp.n_own;
     const uint64_t V = n_vertices_;
     std::vector<uint32_t> col_ptr(n_own + 1, 0), gsrc(n_edges), w;
@@ -237,7 +242,90 @@ void Engine::load_partition(uint32_t part, gxp_format fmt, uint64_t n_edges, con
     }
     if (stream_) cudaStreamSynchronize(stream_);
     if (finalized_) free_graph_device();
+    release_part(hp);
     build_local(hp, V, n_parts_ > 1, std::move(col_ptr), std::move(gsrc), std::move(w));
+}
+
+// Single-partition CSC: the arrays are copied into device memory as given
+// (from host or device memory) and checked there; no host copy is made.
+void Engine::load_csc_device(HostPart& hp, uint64_t E, const void* cp_in, const uint32_t* src_in,
+                             const uint32_t* w_in) {
+    if (!cp_in || (E && !src_in)) fail(GXP_E_INVAL, "null CSC array");
+    if (stream_) cuda_check(cudaStreamSynchronize(stream_), "sync");
+    if (finalized_) free_graph_device();
+    release_part(hp);
+    const uint32_t n = hp.n_own;
+    auto own = [&](size_t bytes) {
+        void* q = nullptr;
+        if (cfg_.mem_budget && graph_bytes_ + bytes > cfg_.mem_budget)
+            fail(GXP_E_NOMEM, "allocation exceeds the context's mem_budget");
+        cuda_check(cudaMalloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
+        return q;
+    };
+    uint64_t* cp64 = nullptr;
+    uint32_t* flag = nullptr;
+    try {
+        hp.d_col_ptr = (uint32_t*)own(4 * pad4(n + 1));
+        hp.d_src = (uint32_t*)own(4 * pad4(E));
+        if (w_in) hp.d_w = (uint32_t*)own(4 * pad4(E));
+        hp.on_device = true;
+        cp64 = (uint64_t*)own(8 * ((size_t)n + 1));
+        flag = (uint32_t*)own(4);
+        cuda_check(cudaMemsetAsync(flag, 0, 4, stream_), "memset");
+        cuda_check(cudaMemsetAsync(hp.d_col_ptr, 0, 4 * pad4(n + 1), stream_), "memset");
+        cuda_check(cudaMemsetAsync(hp.d_src + E, 0, 4 * (pad4(E) - E), stream_), "memset");
+        cuda_check(cudaMemcpyAsync(cp64, cp_in, 8 * ((size_t)n + 1), cudaMemcpyDefault, stream_), "copy col_ptr");
+        if (E) cuda_check(cudaMemcpyAsync(hp.d_src, src_in, 4 * E, cudaMemcpyDefault, stream_), "copy sources");
+        if (w_in) {
+            cuda_check(cudaMemsetAsync(hp.d_w + E, 0, 4 * (pad4(E) - E), stream_), "memset");
+            if (E) cuda_check(cudaMemcpyAsync(hp.d_w, w_in, 4 * E, cudaMemcpyDefault, stream_), "copy weights");
+        }
+        cuda_check(launch_csc_import(cp64, n, E, hp.d_col_ptr, hp.d_src, n, flag, stream_), "check CSC");
+        uint32_t bad = 0;
+        cuda_check(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, stream_), "read check");
+        cuda_check(cudaStreamSynchronize(stream_), "check CSC");
+        cudaFree(cp64);
+        cudaFree(flag);
+        cp64 = nullptr;
+        flag = nullptr;
+        if (bad & 1u) fail(GXP_E_INVAL, "CSC col_ptr must run from 0 to n_edges, non-decreasing");
+        if (bad & 2u) fail(GXP_E_INVAL, "source id out of range");
+    } catch (...) {
+        if (cp64) cudaFree(cp64);
+        if (flag) cudaFree(flag);
+        release_part(hp);
+        throw;
+    }
+    hp.dev_edges = E;
+    hp.dev_weighted = w_in != nullptr;
+    hp.loaded = true;
+}
+
+void Engine::release_part(HostPart& hp) {
+    if (hp.on_device) {
+        if (stream_) cudaStreamSynchronize(stream_);
+        cudaFree(hp.d_col_ptr);
+        cudaFree(hp.d_src);
+        if (hp.d_w) cudaFree(hp.d_w);
+        hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
+        hp.on_device = false;
+        hp.dev_edges = 0;
+        hp.dev_weighted = false;
+        hp.loaded = false;
+    }
+}
+
+// Host copies of a device-loaded partition, for the paths that work on the host.
+void Engine::ensure_host(HostPart& hp) {
+    if (!hp.on_device || hp.col_ptr.size() == (size_t)hp.n_own + 1) return;
+    const uint64_t E = hp.dev_edges;
+    std::vector<uint32_t> cp(hp.n_own + 1), src(E), w(hp.dev_weighted ? E : 0);
+    cuda_check(cudaMemcpy(cp.data(), hp.d_col_ptr, 4 * cp.size(), cudaMemcpyDeviceToHost), "download CSC");
+    if (E) cuda_check(cudaMemcpy(src.data(), hp.d_src, 4 * E, cudaMemcpyDeviceToHost), "download CSC");
+    if (hp.dev_weighted && E) cuda_check(cudaMemcpy(w.data(), hp.d_w, 4 * E, cudaMemcpyDeviceToHost), "download CSC");
+    hp.col_ptr = std::move(cp);
+    hp.src = std::move(src);
+    hp.w = std::move(w);
 }
 
 uint32_t* Engine::upload_u32(const std::vector<uint32_t>& h, size_t n_pad) {
@@ -253,119 +341,140 @@ uint32_t* Engine::upload_u32(const std::vector<uint32_t>& h, size_t n_pad) {
 // slices stored column-major, each row's in-edges in ascending source order)
 // and hub parts of T edges for the rows with more. Built on first use by a
 // superstep (the batched path does not need it).
+// Sliced-ELL layout of every partition, built on the device (sell_build.cu):
+// rows sorted by source, windows sorted by in-degree, slices filled, hub rows
+// split into parts; then all slices ordered heavy-first. A few small counts
+// come back to the host to size the arrays.
 void Engine::build_sell() {
     const uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
-    std::vector<SellSlice> slices;
-    std::vector<HubPart> hubs;
+    std::vector<void*> tmp;   // freed when the build ends
+    auto talloc = [&](size_t bytes) {
+        void* q = nullptr;
+        cuda_check(cudaMalloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
+        tmp.push_back(q);
+        return q;
+    };
+    struct FreeTmp {
+        std::vector<void*>& v;
+        cudaStream_t s;
+        ~FreeTmp() {
+            cudaStreamSynchronize(s);
+            for (void* q : v) cudaFree(q);
+        }
+    } free_tmp{tmp, stream_};
+    auto d2h = [&](void* h, const void* d, size_t bytes) {
+        cuda_check(cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, stream_), "read counts");
+        cuda_check(cudaStreamSynchronize(stream_), "read counts");
+    };
+    std::vector<SellSlice*> part_desc(n_parts_);
+    std::vector<uint32_t> part_ns(n_parts_);
+    std::vector<HubPart*> part_hubs(n_parts_);
+    std::vector<uint32_t> part_nh(n_parts_);
+    uint64_t total_slices = 0;
+    uint32_t total_hubs = 0;
     for (uint32_t p = 0; p < n_parts_; ++p) {
         HostPart& hp = parts_[p];
-        const bool weighted = !hp.w.empty();
+        const bool weighted = hp.weighted();
         const uint32_t n = hp.n_own;
-        const uint64_t E = hp.src.size();
-        auto deg = [&](uint32_t v) { return hp.col_ptr[v + 1] - hp.col_ptr[v]; };
-        // Each row's in-edges in ascending source order: the k-th sources of the
-        // 32 rows of a slice then fall in similar id ranges, so a warp's gathers
-        // share more cache sectors (and hub parts gather near-consecutive ids).
-        std::vector<uint32_t> ssrc(E), sw(weighted ? E : 0);
-#pragma omp parallel
-        {
-            std::vector<std::pair<uint32_t, uint32_t>> buf;
-#pragma omp for schedule(dynamic, 2048)
-            for (int64_t vi = 0; vi < (int64_t)n; ++vi) {
-                const uint32_t v = (uint32_t)vi, b = hp.col_ptr[v], d = deg(v);
-                buf.resize(d);
-                for (uint32_t k = 0; k < d; ++k) buf[k] = {hp.src[b + k], weighted ? hp.w[b + k] : 0u};
-                std::sort(buf.begin(), buf.end());
-                for (uint32_t k = 0; k < d; ++k) {
-                    ssrc[b + k] = buf[k].first;
-                    if (weighted) sw[b + k] = buf[k].second;
-                }
-            }
+        const uint64_t E = hp.n_edges();
+        // 1. rows sorted by (source, weight); the sorted copy also serves the hub parts
+        uint32_t* d_w = hp.d_w;
+        if (weighted && !d_w) {
+            d_w = (uint32_t*)talloc(4 * E);
+            cuda_check(cudaMemcpyAsync(d_w, hp.w.data(), 4 * E, cudaMemcpyHostToDevice, stream_), "upload weights");
         }
-        // hub rows: parts of T edges
-        std::vector<uint32_t> hsrc, hw;
-        for (uint32_t v = 0; v < n; ++v) {
-            const uint32_t b = hp.col_ptr[v], d = deg(v);
-            if (d <= H) continue;
-            const uint32_t np = (d + T - 1) / T;
-            const uint32_t t0 = (uint32_t)hubs.size();
-            for (uint32_t k = 0; k < np; ++k)
-                hubs.push_back(HubPart{v, p, (uint32_t)hsrc.size() + k * T, std::min<uint32_t>(T, d - k * T), t0, np, {0, 0}});
-            hsrc.insert(hsrc.end(), ssrc.begin() + b, ssrc.begin() + b + d);
-            if (weighted) hw.insert(hw.end(), sw.begin() + b, sw.begin() + b + d);
-        }
-        if (hsrc.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub edges in one partition");
-        // windows: non-hub rows by in-degree, descending (ties by id)
+        uint32_t* ssrc = (uint32_t*)dalloc(4 * pad4(E));
+        uint32_t* sw = weighted ? (uint32_t*)dalloc(4 * pad4(E)) : nullptr;
+        uint2* big = (uint2*)talloc(8 * ((size_t)n + E / 2048 + 1));
+        uint32_t* cnt = (uint32_t*)talloc(4);
+        cuda_check(launch_sort_rows(hp.d_col_ptr, n, hp.d_src, d_w, ssrc, sw, big, cnt, stream_), "sort rows");
+        // 2. windows
         const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
-        std::vector<std::vector<uint32_t>> wrows(nw);
-#pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t wi = 0; wi < (int64_t)nw; ++wi) {
-            const uint32_t w0 = (uint32_t)wi * kSellWindow;
-            const uint32_t w1 = (uint32_t)std::min<uint64_t>((uint64_t)w0 + kSellWindow, n);
-            auto& rows = wrows[wi];
-            for (uint32_t v = w0; v < w1; ++v)
-                if (deg(v) <= H) rows.push_back(v);
-            std::stable_sort(rows.begin(), rows.end(), [&](uint32_t x, uint32_t y) { return deg(x) > deg(y); });
+        uint32_t* rows_out = (uint32_t*)talloc(4 * (size_t)n);
+        uint32_t* hub_out = (uint32_t*)talloc(4 * (size_t)n);
+        uint32_t* counts = (uint32_t*)talloc(8 * (size_t)nw + 8);   // non-hub counts, then hub counts
+        cuda_check(launch_sell_windows(hp.d_col_ptr, n, H, rows_out, hub_out, counts, counts + nw, stream_),
+                   "sort windows");
+        std::vector<uint32_t> hc(2 * (size_t)nw + 2, 0);
+        if (nw) d2h(hc.data(), counts, 8 * (size_t)nw);
+        std::vector<uint32_t> bases(2 * (size_t)nw + 2, 0);   // slice bases, then hub bases
+        uint64_t ns = 0, nh_rows = 0;
+        for (uint32_t w = 0; w < nw; ++w) {
+            bases[w] = (uint32_t)ns;
+            bases[nw + w] = (uint32_t)nh_rows;
+            ns += (hc[w] + 31) / 32;
+            nh_rows += hc[nw + w];
         }
-        // slice descriptors and offsets
-        const size_t first_slice = slices.size();
-        std::vector<const uint32_t*> slice_rows;
-        std::vector<uint32_t> slice_n;
-        uint64_t perm_size = 0, sell_size = 0;
-        for (uint32_t wi = 0; wi < nw; ++wi) {
-            const auto& rows = wrows[wi];
-            for (size_t i = 0; i < rows.size(); i += 32) {
-                const uint32_t width = deg(rows[i]);
-                slices.push_back(SellSlice{p, (uint32_t)perm_size, width, 0u, sell_size});
-                slice_rows.push_back(rows.data() + i);
-                slice_n.push_back((uint32_t)std::min<size_t>(32, rows.size() - i));
-                perm_size += 32;
-                sell_size += 32ull * width;
-            }
-        }
-        if (perm_size > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many rows in one partition");
-        std::vector<uint32_t> perm(perm_size), sell_src(sell_size), sell_w(weighted ? sell_size : 0);
-        const int64_t ns = (int64_t)(slices.size() - first_slice);
-#pragma omp parallel for schedule(dynamic, 64)
-        for (int64_t si = 0; si < ns; ++si) {
-            const SellSlice& sl = slices[first_slice + si];
-            const uint32_t* rows = slice_rows[si];
-            const uint32_t cnt = slice_n[si];
-            for (uint32_t l = 0; l < 32; ++l) perm[sl.row0 + l] = l < cnt ? rows[l] : kSellPad;
-            for (uint32_t k = 0; k < sl.width; ++k)
-                for (uint32_t l = 0; l < 32; ++l) {
-                    const bool has = l < cnt && k < deg(rows[l]);
-                    const uint32_t e = has ? hp.col_ptr[rows[l]] + k : 0u;
-                    sell_src[sl.off + 32ull * k + l] = has ? ssrc[e] : kSellPad;
-                    if (weighted) sell_w[sl.off + 32ull * k + l] = has ? sw[e] : 0u;
-                }
-        }
-        pd_[p].sell_src = upload_u32(sell_src, pad4(sell_src.size()));
-        pd_[p].sell_w = weighted ? upload_u32(sell_w, pad4(sell_w.size())) : nullptr;
-        pd_[p].perm = upload_u32(perm, pad4(perm.size()));
-        pd_[p].hsrc = upload_u32(hsrc, pad4(hsrc.size()));
-        pd_[p].hw = weighted ? upload_u32(hw, pad4(hw.size())) : nullptr;
+        if (ns * 32 > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many rows in one partition");
+        uint32_t* d_bases = (uint32_t*)talloc(8 * (size_t)nw + 8);
+        if (nw)
+            cuda_check(cudaMemcpyAsync(d_bases, bases.data(), 8 * (size_t)nw, cudaMemcpyHostToDevice, stream_),
+                       "upload bases");
+        // 3. slices and their offsets
+        uint32_t* perm = (uint32_t*)dalloc(4 * pad4(ns * 32));
+        uint32_t* width = (uint32_t*)talloc(4 * ns + 4);
+        uint64_t* off = (uint64_t*)talloc(8 * ns + 8);
+        cuda_check(launch_sell_slices(hp.d_col_ptr, n, rows_out, counts, d_bases, perm, width, off, (uint32_t)ns,
+                                      stream_), "slices");
+        uint64_t sell_size = 0;
+        d2h(&sell_size, off + ns, 8);
+        // 4. fill
+        uint32_t* sell_src = (uint32_t*)dalloc(4 * pad4(sell_size));
+        uint32_t* sell_w = weighted ? (uint32_t*)dalloc(4 * pad4(sell_size)) : nullptr;
+        part_desc[p] = (SellSlice*)talloc(sizeof(SellSlice) * (ns + 1));
+        part_ns[p] = (uint32_t)ns;
+        cuda_check(launch_sell_fill(hp.d_col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, sell_src, sell_w,
+                                    part_desc[p], stream_), "fill slices");
+        // 5. hub rows -> parts of T edges
+        uint32_t* hub_list = (uint32_t*)talloc(4 * nh_rows + 4);
+        uint32_t* part_off = (uint32_t*)talloc(4 * nh_rows + 4);
+        cuda_check(launch_hub_rows(hp.d_col_ptr, n, hub_out, counts + nw, d_bases + nw, hub_list, (uint32_t)nh_rows,
+                                   T, part_off, stream_), "hub rows");
+        uint32_t nparts = 0;
+        d2h(&nparts, part_off + nh_rows, 4);
+        if ((uint64_t)total_hubs + nparts > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub parts");
+        part_hubs[p] = (HubPart*)talloc(sizeof(HubPart) * ((size_t)nparts + 1));
+        part_nh[p] = nparts;
+        cuda_check(launch_hub_parts(hp.d_col_ptr, hub_list, part_off, (uint32_t)nh_rows, T, p, total_hubs,
+                                    part_hubs[p], stream_), "hub parts");
+        pd_[p].sell_src = sell_src;
+        pd_[p].sell_w = sell_w;
+        pd_[p].perm = perm;
+        pd_[p].hsrc = ssrc;
+        pd_[p].hw = sw;
+        total_slices += ns;
+        total_hubs += nparts;
     }
-    // heavy slices first, so the hardware scheduler's tail is made of light ones
-    std::stable_sort(slices.begin(), slices.end(), [](const SellSlice& x, const SellSlice& y) { return x.width > y.width; });
-    if (slices.size() > 0xFFFFFFF0ull || hubs.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "graph too large");
-    n_slices_ = (uint32_t)slices.size();
-    n_hubs_ = (uint32_t)hubs.size();
+    if (total_slices > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "graph too large");
+    n_slices_ = (uint32_t)total_slices;
+    n_hubs_ = total_hubs;
     cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
                "upload parts");
-    d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(slices.size(), 1));
-    if (!slices.empty())
-        cuda_check(cudaMemcpyAsync(d_slices_, slices.data(), sizeof(SellSlice) * slices.size(), cudaMemcpyHostToDevice,
-                                   stream_), "upload slices");
-    const size_t nh1 = std::max<size_t>(hubs.size(), 1);
+    // 6. all partitions' slices, heavy first; hub parts concatenated (t0 already global)
+    SellSlice* all = (SellSlice*)talloc(sizeof(SellSlice) * (total_slices + 1));
+    uint64_t at = 0;
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        if (part_ns[p])
+            cuda_check(cudaMemcpyAsync(all + at, part_desc[p], sizeof(SellSlice) * part_ns[p],
+                                       cudaMemcpyDeviceToDevice, stream_), "gather slices");
+        at += part_ns[p];
+    }
+    d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(total_slices, 1));
+    cuda_check(launch_order_slices(all, n_slices_, d_slices_, stream_), "order slices");
+    const size_t nh1 = std::max<size_t>(total_hubs, 1);
     d_hubs_ = (HubPart*)dalloc(sizeof(HubPart) * nh1);
-    if (!hubs.empty())
-        cuda_check(cudaMemcpyAsync(d_hubs_, hubs.data(), sizeof(HubPart) * hubs.size(), cudaMemcpyHostToDevice, stream_),
-                   "upload hubs");
+    at = 0;
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        if (part_nh[p])
+            cuda_check(cudaMemcpyAsync(d_hubs_ + at, part_hubs[p], sizeof(HubPart) * part_nh[p],
+                                       cudaMemcpyDeviceToDevice, stream_), "gather hub parts");
+        at += part_nh[p];
+    }
     d_hub_val_ = (uint32_t*)dalloc(4 * nh1);
     d_hub_arrive_ = (uint32_t*)dalloc(4 * nh1);
     cuda_check(cudaMemsetAsync(d_hub_arrive_, 0, 4 * nh1, stream_), "memset");
-    cuda_check(cudaStreamSynchronize(stream_), "upload");   // host vectors die here
+    cuda_check(cudaStreamSynchronize(stream_), "sell build");
+    check_device_error();
     sell_ready_ = true;
 }
 
@@ -384,18 +493,20 @@ void Engine::finalize() {
         hp.ghost_base = n_ghost_total_;
         if ((uint64_t)n_ghost_total_ + hp.ghost_gid.size() > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many cached vertices");
         n_ghost_total_ += (uint32_t)hp.ghost_gid.size();
-        total_edges_ += hp.src.size();
-        if (hp.w.empty() && !hp.src.empty()) weighted_ = false;
+        total_edges_ += hp.n_edges();
+        if (!hp.weighted() && hp.n_edges()) weighted_ = false;
     }
 
     pd_.assign(n_parts_, PartDev{});
     for (uint32_t p = 0; p < n_parts_; ++p) {
         HostPart& hp = parts_[p];
         // plain CSC copies: the out-degree pass and the bounds check read them
-        hp.d_col_ptr = upload_u32(hp.col_ptr, pad4(hp.n_own + 1));
-        hp.d_src = upload_u32(hp.src, pad4(hp.src.size()));
+        if (!hp.on_device) {
+            hp.d_col_ptr = upload_u32(hp.col_ptr, pad4(hp.n_own + 1));
+            hp.d_src = upload_u32(hp.src, pad4(hp.src.size()));
+        }
         pd_[p] = PartDev{hp.d_col_ptr, hp.d_src, nullptr, hp.n_own, hp.v_begin,
-                         (uint32_t)hp.ghost_gid.size(), hp.ghost_base, (uint64_t)hp.src.size(),
+                         (uint32_t)hp.ghost_gid.size(), hp.ghost_base, hp.n_edges(),
                          nullptr, nullptr, nullptr, nullptr, nullptr};
     }
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);

@@ -33,6 +33,15 @@ struct HostPart {
     uint32_t* d_w = nullptr;
     uint32_t ghost_base = 0;
     uint64_t gdq_base = 0, n_boundary = 0;
+    // CSC loaded straight into device memory (single-partition CSC loads): the
+    // device arrays above belong to the partition and the host vectors stay
+    // empty until something needs them (ensure_host)
+    bool on_device = false;
+    uint64_t dev_edges = 0;
+    bool dev_weighted = false;
+
+    uint64_t n_edges() const { return on_device ? dev_edges : src.size(); }
+    bool weighted() const { return on_device ? dev_weighted : !w.empty(); }
 };
 
 class Engine {
@@ -71,6 +80,10 @@ private:
     void account(bool force);
     void check_device_error();
     void copy_in(void* dst, const void* src, size_t bytes);   // host or device src -> host dst
+    void load_csc_device(HostPart& hp, uint64_t n_edges, const void* col_ptr, const uint32_t* src,
+                         const uint32_t* weights);
+    void release_part(HostPart& hp);
+    void ensure_host(HostPart& hp);
     void prepare_batch(bool streamed);
     void free_batch();
     double time_pipeline(uint64_t block_edges, bool pipelined, bool dry, int reps);

@@ -114,6 +114,24 @@ __global__ void k_validate(const uint32_t* __restrict__ col_ptr, uint32_t n_own,
         if (col_ptr[v] > col_ptr[v + 1]) atomicOr(err, kErrBounds);
 }
 
+// CSC imported as given: col_ptr (u64) -> u32 with its checks (bit 0 of
+// err: not running from 0 to n_edges or decreasing), sources < n_local (bit 1)
+__global__ void k_csc_import(const uint64_t* __restrict__ cp64, uint32_t n, uint64_t n_edges,
+                             uint32_t* __restrict__ cp32, const uint32_t* __restrict__ src, uint32_t n_local,
+                             uint32_t* err) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (uint64_t v = t0; v <= n; v += stride) {
+        const uint64_t c = cp64[v];
+        const bool bad = c > n_edges || (v == 0 && c != 0) || (v == n && c != n_edges) || (v < n && cp64[v + 1] < c);
+        if (bad) atomicOr(err, 1u);
+        cp32[v] = (uint32_t)c;
+    }
+    bool oob = false;
+    for (uint64_t e = t0; e < n_edges; e += stride) oob |= src[e] >= n_local;
+    if (__any_sync(0xFFFFFFFFu, oob) && (threadIdx.x & 31) == 0) atomicOr(err, 2u);
+}
+
 // ------------------------------------------------------- initial values
 
 
@@ -290,6 +308,14 @@ cudaError_t launch_validate_csc(const uint32_t* col_ptr, uint32_t n_own, const u
     if (work == 0) return cudaSuccess;
     const uint64_t blocks = std::min<uint64_t>((work + 255) / 256, 152ull * 16);
     k_validate<<<(unsigned)blocks, 256, 0, s>>>(col_ptr, n_own, src, n_edges, n_local, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_import(const uint64_t* cp64, uint32_t n, uint64_t n_edges, uint32_t* cp32,
+                              const uint32_t* src, uint32_t n_local, uint32_t* err, cudaStream_t s) {
+    const uint64_t work = std::max<uint64_t>((uint64_t)n + 1, n_edges);
+    const uint64_t blocks = std::min<uint64_t>((work + 255) / 256, 152ull * 16);
+    k_csc_import<<<(unsigned)blocks, 256, 0, s>>>(cp64, n, n_edges, cp32, src, n_local, err);
     return cudaGetLastError();
 }
 

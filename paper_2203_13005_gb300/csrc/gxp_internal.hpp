@@ -229,6 +229,8 @@ uint32_t tile_count(uint32_t n_own, uint64_t n_edges, uint32_t tile_items);
 
 cudaError_t launch_outdeg(const PartDev& p, const uint32_t* d_src, const uint32_t* d_ghost_gid,
                           uint32_t* d_outdeg, cudaStream_t s);
+cudaError_t launch_csc_import(const uint64_t* cp64, uint32_t n, uint64_t n_edges, uint32_t* cp32,
+                              const uint32_t* src, uint32_t n_local, uint32_t* err, cudaStream_t s);
 cudaError_t launch_validate_csc(const uint32_t* d_col_ptr, uint32_t n_own, const uint32_t* d_src,
                                 uint64_t n_edges, uint32_t n_local, uint32_t* d_err, cudaStream_t s);
 
@@ -249,6 +251,26 @@ cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_
                               uint32_t* frontier, cudaStream_t s);
 cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long* out, cudaStream_t s);
 uint32_t msssp_grid(uint64_t units);
+
+// sliced-ELL build on the device (sell_build.cu)
+cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t* src, const uint32_t* w,
+                             uint32_t* ssrc, uint32_t* sw, uint2* scratch_runs, uint32_t* scratch_cnt,
+                             cudaStream_t s);   // scratch_runs: n + n_edges / 2048 + 1 entries
+cudaError_t launch_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H, uint32_t* rows_out,
+                                uint32_t* hub_out, uint32_t* nonhub_cnt, uint32_t* hub_cnt, cudaStream_t s);
+cudaError_t launch_sell_slices(const uint32_t* col_ptr, uint32_t n, const uint32_t* rows_out,
+                               const uint32_t* nonhub_cnt, const uint32_t* slice_base, uint32_t* perm,
+                               uint32_t* width, uint64_t* off, uint32_t n_slices, cudaStream_t s);
+cudaError_t launch_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
+                             const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
+                             uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s);
+cudaError_t launch_hub_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t* hub_out, const uint32_t* hub_cnt,
+                            const uint32_t* hub_base, uint32_t* hub_list, uint32_t n_hub_rows, uint32_t T,
+                            uint32_t* part_off, cudaStream_t s);
+cudaError_t launch_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, const uint32_t* part_off,
+                             uint32_t n_hub_rows, uint32_t T, uint32_t part, uint32_t part_base, HubPart* hubs,
+                             cudaStream_t s);
+cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, cudaStream_t s);
 
 // serving (serve.cu): 64-slot personalized PageRank and slot management
 cudaError_t launch_ppr_superstep(const PprArgs& a, cudaStream_t s);

@@ -283,6 +283,51 @@ def test_formats_and_device_inputs_agree():
             assert np.array_equal(c.values(), d_ref), name
 
 
+def test_csc_single_partition_loads_on_device():
+    """A single-partition CSC goes straight to device memory (host or device
+    arrays) and is checked there; the batched path still works on it."""
+    import torch
+    n = 400
+    src, dst, w = _rand_graph(6, n, 3000)
+    order = np.argsort(dst, kind="stable")
+    col_ptr = np.zeros(n + 1, np.uint64)
+    np.cumsum(np.bincount(dst, minlength=n), out=col_ptr[1:])
+    s_sorted, w_sorted = np.ascontiguousarray(src[order]), np.ascontiguousarray(w[order])
+    d_ref, steps_ref, _ = oracle.sssp(n, src, dst, w, 5)
+    d_ref7, _, _ = oracle.sssp(n, src, dst, w, 7)
+    variants = {
+        "host": (col_ptr, s_sorted, w_sorted),
+        "device": (torch.from_numpy(col_ptr.view(np.int64)).cuda(), torch.from_numpy(s_sorted.view(np.int32)).cuda(),
+                   torch.from_numpy(w_sorted.view(np.int32)).cuda()),
+    }
+    for name, (a, b, ww) in variants.items():
+        with _ctx(n) as c:
+            c.load_partition(0, gxp.GXP_FMT_CSC, len(src), a, b, ww)
+            assert c.run(gxp.GXP_ALGO_SSSP, 5) == steps_ref, name
+            assert np.array_equal(c.values(), d_ref), name
+            dist, _ = c.sssp_batch(np.array([5, 7], np.uint32))
+            assert np.array_equal(dist[:, 0], d_ref) and np.array_equal(dist[:, 1], d_ref7), name
+            c.load_partition(0, gxp.GXP_FMT_CSC, len(src), a, b, ww)   # reload replaces it
+            assert c.run(gxp.GXP_ALGO_SSSP, 7) >= 1
+            assert np.array_equal(c.values(), d_ref7), name
+    k = int(np.argmax(np.diff(col_ptr.astype(np.int64)) > 0))
+    decreasing = col_ptr.copy()
+    decreasing[k + 1] = decreasing[k] - 1 if decreasing[k] > 0 else 0
+    decreasing[k] = col_ptr[k + 1]
+    bad_end = col_ptr.copy()
+    bad_end[n] += 1
+    bad_src = s_sorted.copy()
+    bad_src[len(src) // 2] = n
+    with _ctx(n) as c:
+        for cp, sv in ((decreasing, s_sorted), (bad_end, s_sorted), (col_ptr, bad_src)):
+            with pytest.raises(gxp.GxpError) as ei:
+                c.load_partition(0, gxp.GXP_FMT_CSC, len(src), cp, sv, w_sorted)
+            assert ei.value.code == gxp.GXP_E_INVAL
+        c.load_partition(0, gxp.GXP_FMT_CSC, len(src), col_ptr, s_sorted, w_sorted)   # still usable
+        c.run(gxp.GXP_ALGO_SSSP, 5)
+        assert np.array_equal(c.values(), d_ref)
+
+
 def test_errors_are_status_codes():
     with _ctx(4) as c:
         with pytest.raises(gxp.GxpError) as ei:
