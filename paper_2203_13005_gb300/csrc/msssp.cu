@@ -40,11 +40,14 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t d, uint32_t w) {
 
 template <bool kDry>
 __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
-    __shared__ uint32_t s_imp[2];
+    __shared__ uint32_t s_imp[2], s_done;
     __shared__ unsigned long long s_changed;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 2) s_imp[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) s_changed = 0ull;
+    if (threadIdx.x == 0) {
+        s_changed = 0ull;
+        s_done = 0u;
+    }
     __syncthreads();
     const bool live = ((~a.idle_mask >> (2 * lane)) & 3ull) != 0ull;   // either of my 2 slots busy
     uint32_t imp_lo = 0u, imp_hi = 0u;   // improved slots 0..31 / 32..63 (bit = slot)
@@ -119,14 +122,25 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
             imp_hi |= hi;
         }
     }
-    // block totals in shared memory, then one global atomic per word and block
-    if (lane == 0 && changed_units) atomicAdd(&s_changed, (unsigned long long)changed_units);
-    if (lane == 0 && imp_lo) atomicOr(&s_imp[0], imp_lo);
-    if (lane == 0 && imp_hi) atomicOr(&s_imp[1], imp_hi);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_changed) atomicAdd(a.changed, s_changed);
-    if (!kDry && a.slot_improved != nullptr && threadIdx.x < 2 && s_imp[threadIdx.x])
-        atomicOr(&a.slot_improved[threadIdx.x], s_imp[threadIdx.x]);
+    // block totals in shared memory; the block's last warp to finish issues
+    // one global atomic per word (no barrier: early warps leave at once)
+    if (lane == 0) {
+        if (changed_units) atomicAdd(&s_changed, (unsigned long long)changed_units);
+        if (imp_lo) atomicOr(&s_imp[0], imp_lo);
+        if (imp_hi) atomicOr(&s_imp[1], imp_hi);
+        __threadfence_block();
+        const bool last = atomicAdd(&s_done, 1u) == (uint32_t)(kMsBlock / 32) - 1u;
+        if (last) {
+            __threadfence_block();
+            const unsigned long long c = atomicAdd(&s_changed, 0ull);
+            if (c) atomicAdd(a.changed, c);
+            const uint32_t i0 = atomicOr(&s_imp[0], 0u), i1 = atomicOr(&s_imp[1], 0u);
+            if (!kDry && a.slot_improved != nullptr) {
+                if (i0) atomicOr(&a.slot_improved[0], i0);
+                if (i1) atomicOr(&a.slot_improved[1], i1);
+            }
+        }
+    }
 }
 
 __global__ void k_msssp_init(uint32_t* dist, uint64_t n_vertices) {

@@ -59,6 +59,7 @@ struct PprSlots {
     float2 d[32], add[32];
     uint2 src[32];
     unsigned long long dang[64];   // this block's dangling mass of r_{t+1}
+    uint32_t warps_done;
 
     __device__ void init(const PprArgs& a) {
         const int s = threadIdx.x;
@@ -71,6 +72,7 @@ struct PprSlots {
             reinterpret_cast<uint32_t*>(src)[s] = busy ? a.slot_source[s] : kInf;
             dang[s] = 0ull;
         }
+        if (threadIdx.x == 0) warps_done = 0u;
         __syncthreads();
     }
 
@@ -91,10 +93,22 @@ struct PprSlots {
         }
     }
 
-    // the block's dangling sums -> one global atomic per slot
+    // the block's dangling sums -> one global atomic per slot, issued by the
+    // block's last warp to finish (no barrier: early warps leave at once)
     __device__ void flush(unsigned long long* out) {
-        __syncthreads();
-        if (threadIdx.x < 64 && dang[threadIdx.x]) atomicAdd(&out[threadIdx.x], dang[threadIdx.x]);
+        __syncwarp();
+        const int lane = threadIdx.x & 31;
+        uint32_t last = 0u;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&warps_done, 1u) == (blockDim.x >> 5) - 1u ? 1u : 0u;
+        }
+        if (!__shfl_sync(0xFFFFFFFFu, last, 0)) return;
+        __threadfence_block();
+        for (int i = lane; i < 64; i += 32) {
+            const unsigned long long v = atomicAdd(&dang[i], 0ull);
+            if (v) atomicAdd(&out[i], v);
+        }
     }
 };
 
