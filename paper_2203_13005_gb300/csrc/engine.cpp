@@ -460,7 +460,8 @@ void Engine::build_sell() {
         at += part_ns[p];
     }
     d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(total_slices, 1));
-    cuda_check(launch_order_slices(all, n_slices_, d_slices_, stream_), "order slices");
+    uint32_t* order_scratch = (uint32_t*)talloc(order_slices_scratch_bytes(n_slices_));
+    cuda_check(launch_order_slices(all, n_slices_, d_slices_, order_scratch, stream_), "order slices");
     const size_t nh1 = std::max<size_t>(total_hubs, 1);
     d_hubs_ = (HubPart*)dalloc(sizeof(HubPart) * nh1);
     at = 0;

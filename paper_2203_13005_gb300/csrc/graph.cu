@@ -100,7 +100,9 @@ __global__ void k_outdeg(const uint32_t* __restrict__ src, uint64_t n_edges, uin
          e += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t u = src[e];
         const uint32_t g = u < n_own ? v_begin + u : ghost_gid[u - n_own];
-        atomicAdd(&outdeg[g], 1u);
+        // one atomic per distinct source among the active lanes (hub sources repeat)
+        const unsigned peers = __match_any_sync(__activemask(), g);
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&outdeg[g], (uint32_t)__popc(peers));
     }
 }
 

@@ -270,7 +270,8 @@ cudaError_t launch_hub_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t*
 cudaError_t launch_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, const uint32_t* part_off,
                              uint32_t n_hub_rows, uint32_t T, uint32_t part, uint32_t part_base, HubPart* hubs,
                              cudaStream_t s);
-cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, cudaStream_t s);
+cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, uint32_t* scratch, cudaStream_t s);
+size_t order_slices_scratch_bytes(uint32_t n);
 
 // serving (serve.cu): 64-slot personalized PageRank and slot management
 cudaError_t launch_ppr_superstep(const PprArgs& a, cudaStream_t s);

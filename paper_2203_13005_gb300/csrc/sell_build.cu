@@ -2,22 +2,23 @@
 // blocks of Section II-B, in the form the superstep kernel reads):
 //
 //  1. k_sort_rows_warp / k_sort_rows_block: each row's in-edges sorted by
-//     (source, weight), so the k-th sources of a slice's rows fall in
+//     (source, weight) (by source when unweighted), so the k-th sources of a slice's rows fall in
 //     similar id ranges. Rows of up to 32 / 256 edges are bitonic-sorted in
 //     a warp's registers, rows of up to kSortMax edges in shared memory;
 //     longer (hub) rows are sorted in runs of kSortMax edges, so each run a
 //     warp gathers is ordered.
 //  2. k_sell_windows: per window of kSellWindow rows, a stable counting sort
-//     of the rows with at most H in-edges by descending in-degree (one warp
-//     per window, bins in shared memory; degrees above kExactBins share
-//     power-of-two bins), and the list of hub rows (more than H in-edges).
+//     of the rows with at most H in-edges by descending in-degree (one CTA
+//     per window, per-warp bins in shared memory; degrees above kExactBins
+//     share power-of-two bins), and the list of hub rows (more than H in-edges).
 //  3. k_sell_slices: slices of 32 consecutive sorted rows, their widths and
 //     row slots; k_scan_widths: element offsets of the slices.
 //  4. k_sell_fill: the column-major slice arrays (one warp per slice).
 //  5. k_hub_rows / k_scan_parts / k_hub_parts: hub rows in id order, split
 //     into parts of T edges.
-//  6. k_order_slices: all partitions' slice descriptors stably ordered by
-//     decreasing width class (heavy slices first).
+//  6. k_order_count / k_order_offsets / k_order_scatter: all partitions'
+//     slice descriptors stably ordered by decreasing width (heavy slices first:
+//     the hardware then schedules light ones at the tail).
 #include <algorithm>
 
 #include "gxp_internal.hpp"
@@ -27,18 +28,38 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kSortMax = 2048;     // longest row sorted (shared-memory bitonic)
-constexpr uint32_t kExactBins = 4096;   // in-degrees sorted exactly up to here
-constexpr uint32_t kBins = kExactBins + 34;
+constexpr uint32_t kExactBins = 1024;   // in-degrees / widths ordered exactly up to here
+constexpr uint32_t kBins = kExactBins + 34;   // above: one bin per power of two
+constexpr int kSortWarps = 8;             // warps of a counting-sort CTA
+constexpr uint32_t kSortChunk = kSellWindow / kSortWarps;   // items per warp
 
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+// Sort keys: (source << 32 | weight) for weighted rows, the source alone
+// otherwise (bitonic sorting is deterministic, so equal sources keep a fixed
+// order either way).
+template <bool kW> struct SortKey;
+template <> struct SortKey<true> {
+    using T = uint64_t;
+    static constexpr T kMax = ~0ull;
+    __device__ static T make(uint32_t s, const uint32_t* w, uint32_t i) { return ((uint64_t)s << 32) | w[i]; }
+    __device__ static uint32_t src(T k) { return (uint32_t)(k >> 32); }
+    __device__ static uint32_t wt(T k) { return (uint32_t)k; }
+};
+template <> struct SortKey<false> {
+    using T = uint32_t;
+    static constexpr T kMax = ~0u;
+    __device__ static T make(uint32_t s, const uint32_t*, uint32_t) { return s; }
+    __device__ static uint32_t src(T k) { return k; }
+    __device__ static uint32_t wt(T) { return 0u; }
+};
 
-// Bitonic sort of 32 * kSlots keys held as x[s] at index s * 32 + lane.
-template <int kSlots>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&x)[kSlots], int lane) {
+// Bitonic sort of 32 * kSlots keys held as x[s] at index s * 32 + lane;
+// stopping after the stage of size n (a power of two) sorts keys [0, n).
+template <int kSlots, class T>
+__device__ __forceinline__ void warp_bitonic(T (&x)[kSlots], int lane, int n) {
     constexpr int N = 32 * kSlots;
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
+        if (k > n) break;
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= 32) {
@@ -47,7 +68,7 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&x)[kSlots], int lane) {
                     const int ps = s ^ (j >> 5);
                     if (ps > s) {
                         const bool up = ((s * 32 + lane) & k) == 0;
-                        const uint64_t a = x[s], b = x[ps];
+                        const T a = x[s], b = x[ps];
                         if ((a > b) == up) {
                             x[s] = b;
                             x[ps] = a;
@@ -57,38 +78,42 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&x)[kSlots], int lane) {
             } else {
 #pragma unroll
                 for (int s = 0; s < kSlots; ++s) {
-                    const uint64_t o = __shfl_xor_sync(kFull, x[s], j);
+                    const T o = __shfl_xor_sync(kFull, x[s], j);
                     const bool up = ((s * 32 + lane) & k) == 0;
                     const bool lower = (lane & j) == 0;
-                    x[s] = (lower == up) ? umin64(x[s], o) : umax64(x[s], o);
+                    x[s] = (lower == up) ? (x[s] < o ? x[s] : o) : (x[s] < o ? o : x[s]);
                 }
             }
         }
     }
 }
 
-template <int kSlots>
+template <int kSlots, bool kW>
 __device__ __forceinline__ void sort_row_in_warp(uint32_t b, uint32_t d, const uint32_t* src, const uint32_t* w,
                                                  uint32_t* ssrc, uint32_t* sw, int lane) {
-    uint64_t x[kSlots];
+    using K = SortKey<kW>;
+    typename K::T x[kSlots];
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
         const uint32_t i = s * 32 + lane;
-        x[s] = i < d ? ((uint64_t)src[b + i] << 32) | (w ? w[b + i] : 0u) : ~0ull;
+        x[s] = i < d ? K::make(src[b + i], w, b + i) : K::kMax;
     }
-    warp_bitonic<kSlots>(x, lane);
+    int np2 = 2;
+    while (np2 < (int)d) np2 <<= 1;
+    warp_bitonic<kSlots>(x, lane, np2);
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
         const uint32_t i = s * 32 + lane;
         if (i < d) {
-            ssrc[b + i] = (uint32_t)(x[s] >> 32);
-            if (sw) sw[b + i] = (uint32_t)x[s];
+            ssrc[b + i] = K::src(x[s]);
+            if (kW) sw[b + i] = K::wt(x[s]);
         }
     }
 }
 
 // one warp per row: sorts rows of up to 256 edges, lists the runs of
 // kSortMax edges of longer rows ({row, first edge of the run}) for the block sort
+template <bool kW>
 __global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const uint32_t* src, const uint32_t* w,
                                  uint32_t* ssrc, uint32_t* sw, uint2* big_runs, uint32_t* n_big) {
     const int lane = threadIdx.x & 31;
@@ -97,9 +122,9 @@ __global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const uint
     for (uint64_t v = warp0; v < n; v += n_warps) {
         const uint32_t b = col_ptr[v], d = col_ptr[v + 1] - b;
         if (d <= 32) {
-            sort_row_in_warp<1>(b, d, src, w, ssrc, sw, lane);
+            sort_row_in_warp<1, kW>(b, d, src, w, ssrc, sw, lane);
         } else if (d <= 256) {
-            sort_row_in_warp<8>(b, d, src, w, ssrc, sw, lane);
+            sort_row_in_warp<8, kW>(b, d, src, w, ssrc, sw, lane);
         } else {
             const uint32_t runs = (d + kSortMax - 1) / kSortMax;
             uint32_t at = 0;
@@ -111,10 +136,12 @@ __global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const uint
 }
 
 // one CTA per listed run (257 .. kSortMax edges): bitonic sort in shared memory
+template <bool kW>
 __global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr, const uint32_t* src,
                                                          const uint32_t* w, uint32_t* ssrc, uint32_t* sw,
                                                          const uint2* big_runs, const uint32_t* n_big) {
-    __shared__ uint64_t x[kSortMax];
+    using K = SortKey<kW>;
+    __shared__ typename K::T x[kSortMax];
     const uint32_t cnt = *n_big;
     for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
         const uint2 run = big_runs[r];
@@ -123,8 +150,7 @@ __global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr
         uint32_t N = 32;
         while (N < d) N <<= 1;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
-            x[i] = i < d ? ((uint64_t)src[b + i] << 32) | (w ? w[b + i] : 0u) : ~0ull;
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) x[i] = i < d ? K::make(src[b + i], w, b + i) : K::kMax;
         __syncthreads();
         for (uint32_t k = 2; k <= N; k <<= 1)
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -132,7 +158,7 @@ __global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr
                     const uint32_t p = i ^ j;
                     if (p > i) {
                         const bool up = (i & k) == 0;
-                        const uint64_t a = x[i], c = x[p];
+                        const typename K::T a = x[i], c = x[p];
                         if ((a > c) == up) {
                             x[i] = c;
                             x[p] = a;
@@ -142,8 +168,8 @@ __global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr
                 __syncthreads();
             }
         for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
-            ssrc[b + i] = (uint32_t)(x[i] >> 32);
-            if (sw) sw[b + i] = (uint32_t)x[i];
+            ssrc[b + i] = K::src(x[i]);
+            if (kW) sw[b + i] = K::wt(x[i]);
         }
     }
 }
@@ -152,75 +178,122 @@ __device__ __forceinline__ uint32_t deg_bin(uint32_t d) {
     return d <= kExactBins ? d : kExactBins + (31u - (uint32_t)__clz(d));
 }
 
-// bins[k] <- number of entries in bins above k (exclusive offsets in
-// descending bin order); lane l of the warp handles a chunk of bins
-__device__ void descending_offsets(uint32_t* bins, int lane) {
-    constexpr uint32_t kChunk = (kBins + 31) / 32;
-    const int hi = (int)kBins - 1 - lane * (int)kChunk;   // this lane's bins: hi, hi-1, ...
-    uint32_t sum = 0;
-    for (int i = 0; i < (int)kChunk; ++i)
-        if (hi - i >= 0) sum += bins[hi - i];
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
+// Exclusive offsets in descending bin order over a [kSortWarps][kBins]
+// table of per-warp counts, warps in order inside a bin (a stable counting
+// sort); the whole CTA takes part.
+__device__ void warp_bin_offsets(uint32_t (*hist)[kBins], uint32_t* tot) {
+    for (uint32_t b = threadIdx.x; b < kBins; b += blockDim.x) {
+        uint32_t t = 0;
+        for (int w = 0; w < kSortWarps; ++w) t += hist[w][b];
+        tot[b] = t;
     }
-    uint32_t run = incl - sum;
-    for (int i = 0; i < (int)kChunk; ++i)
-        if (hi - i >= 0) {
-            const uint32_t c = bins[hi - i];
-            bins[hi - i] = run;
+    __syncthreads();
+    if (threadIdx.x < 32) {   // descending exclusive scan of tot: lane l takes a chunk of bins
+        const int lane = threadIdx.x;
+        constexpr uint32_t kChunk = (kBins + 31) / 32;
+        const int hi = (int)kBins - 1 - lane * (int)kChunk;
+        uint32_t sum = 0;
+        for (int i = 0; i < (int)kChunk; ++i)
+            if (hi - i >= 0) sum += tot[hi - i];
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t run = incl - sum;
+        for (int i = 0; i < (int)kChunk; ++i)
+            if (hi - i >= 0) {
+                const uint32_t c = tot[hi - i];
+                tot[hi - i] = run;
+                run += c;
+            }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < kBins; b += blockDim.x) {
+        uint32_t run = tot[b];
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = hist[w][b];
+            hist[w][b] = run;
             run += c;
         }
-    __syncwarp();
+    }
+    __syncthreads();
 }
 
-// one warp (one CTA) per window: stable counting sort of the non-hub rows by
-// descending in-degree, hub rows in id order; window-relative outputs
-__global__ void __launch_bounds__(32) k_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H,
-                                                     uint32_t* rows_out, uint32_t* hub_out, uint32_t* nonhub_cnt,
-                                                     uint32_t* hub_cnt) {
-    __shared__ uint32_t bins[kBins];
-    const int lane = threadIdx.x;
+// Stable scatter of one warp's items [i0, i1) by descending bin: key(i)
+// returns the bin, or kBins for an item that is skipped.
+template <class Key, class Put>
+__device__ void warp_scatter(uint32_t i0, uint32_t i1, uint32_t* offs, Key key, Put put) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t j0 = i0; j0 < i1; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t k = j < i1 ? key(j) : kBins;
+        const bool ok = k < kBins;
+        const uint32_t grp = __match_any_sync(kFull, ok ? k : 0x80000000u | (uint32_t)lane);   // alone if skipped
+        if (ok) put(j, offs[k] + __popc(grp & lt));
+        __syncwarp();
+        if (ok && (grp & lt) == 0u) offs[k] += __popc(grp);
+        __syncwarp();
+    }
+}
+
+// One CTA per window of kSellWindow rows: stable counting sort of the rows
+// with at most H in-edges by descending in-degree (each warp counts and then
+// scatters its 1/kSortWarps of the window), hub rows in id order;
+// window-relative outputs.
+__global__ void __launch_bounds__(kSortWarps * 32) k_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H,
+                                                                  uint32_t* rows_out, uint32_t* hub_out,
+                                                                  uint32_t* nonhub_cnt, uint32_t* hub_cnt) {
+    __shared__ uint32_t hist[kSortWarps][kBins];
+    __shared__ uint32_t tot[kBins];
+    __shared__ uint32_t hubs[kSortWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t win = blockIdx.x;
     const uint32_t w0 = win * kSellWindow;
     const uint32_t w1 = (uint32_t)min((uint64_t)w0 + kSellWindow, (uint64_t)n);
-    for (uint32_t i = lane; i < kBins; i += 32) bins[i] = 0u;
-    __syncwarp();
-    for (uint32_t v0 = w0; v0 < w1; v0 += 32) {
+    const uint32_t c0 = min(w1, w0 + warp * kSortChunk), c1 = min(w1, c0 + kSortChunk);
+    for (uint32_t i = threadIdx.x; i < kSortWarps * kBins; i += blockDim.x) (&hist[0][0])[i] = 0u;
+    __syncthreads();
+    uint32_t nh = 0;
+    for (uint32_t v0 = c0; v0 < c1; v0 += 32) {
         const uint32_t v = v0 + lane;
-        if (v < w1) {
-            const uint32_t d = col_ptr[v + 1] - col_ptr[v];
-            if (d <= H) atomicAdd(&bins[deg_bin(d)], 1u);
-        }
-    }
-    __syncwarp();
-    descending_offsets(bins, lane);
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t hubs = 0;
-    for (uint32_t v0 = w0; v0 < w1; v0 += 32) {
-        const uint32_t v = v0 + lane;
-        bool ok = false, hub = false;
-        uint32_t key = 0x80000000u | (uint32_t)lane;   // groups alone
-        if (v < w1) {
+        bool hub = false;
+        if (v < c1) {
             const uint32_t d = col_ptr[v + 1] - col_ptr[v];
             hub = d > H;
-            ok = !hub;
-            if (ok) key = deg_bin(d);
+            if (!hub) atomicAdd(&hist[warp][deg_bin(d)], 1u);
         }
-        const uint32_t grp = __match_any_sync(kFull, key);
-        const uint32_t hb = __ballot_sync(kFull, hub);
-        if (ok) rows_out[w0 + bins[key] + __popc(grp & lt)] = v;
-        if (hub) hub_out[w0 + hubs + __popc(hb & lt)] = v;
-        __syncwarp();
-        if (ok && (grp & lt) == 0u) bins[key] += __popc(grp);
-        hubs += __popc(hb);
-        __syncwarp();
+        nh += __popc(__ballot_sync(kFull, hub));
     }
-    if (lane == 0) {
-        nonhub_cnt[win] = (w1 - w0) - hubs;
-        hub_cnt[win] = hubs;
+    if (lane == 0) hubs[warp] = nh;
+    __syncthreads();
+    warp_bin_offsets(hist, tot);
+    uint32_t hub_at = 0, hub_total = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+        if (w < warp) hub_at += hubs[w];
+        hub_total += hubs[w];
+    }
+    warp_scatter(
+        c0, c1, hist[warp],
+        [&](uint32_t v) {
+            const uint32_t d = col_ptr[v + 1] - col_ptr[v];
+            return d > H ? kBins : deg_bin(d);
+        },
+        [&](uint32_t v, uint32_t pos) { rows_out[w0 + pos] = v; });
+    // hub rows, in id order (warp-ordered ranks)
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t v0 = c0; v0 < c1; v0 += 32) {
+        const uint32_t v = v0 + lane;
+        const bool hub = v < c1 && col_ptr[v + 1] - col_ptr[v] > H;
+        const uint32_t hb = __ballot_sync(kFull, hub);
+        if (hub) hub_out[w0 + hub_at + __popc(hb & lt)] = v;
+        hub_at += __popc(hb);
+    }
+    if (threadIdx.x == 0) {
+        nonhub_cnt[win] = (w1 - w0) - hub_total;
+        hub_cnt[win] = hub_total;
     }
 }
 
@@ -336,27 +409,58 @@ __global__ void k_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, c
     }
 }
 
-// one warp: stable order of all slice descriptors by decreasing width (exact
-// up to kExactBins, by power-of-two class above)
-__global__ void __launch_bounds__(32) k_order_slices(const SellSlice* in, uint32_t n, SellSlice* out) {
-    __shared__ uint32_t bins[kBins];
-    const int lane = threadIdx.x;
-    for (uint32_t i = lane; i < kBins; i += 32) bins[i] = 0u;
-    __syncwarp();
-    for (uint32_t i = lane; i < n; i += 32) atomicAdd(&bins[deg_bin(in[i].width)], 1u);
-    __syncwarp();
-    descending_offsets(bins, lane);
-    const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t i0 = 0; i0 < n; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        const bool ok = i < n;
-        const uint32_t key = ok ? deg_bin(in[i].width) : 0x80000000u | (uint32_t)lane;
-        const uint32_t grp = __match_any_sync(kFull, key);
-        if (ok) out[bins[key] + __popc(grp & lt)] = in[i];
-        __syncwarp();
-        if (ok && (grp & lt) == 0u) bins[key] += __popc(grp);
-        __syncwarp();
+// All slice descriptors stably ordered by decreasing width (exact up to
+// kExactBins, by power of two above), in three steps over chunks of
+// kSellWindow descriptors: per-warp counts, offsets, per-warp scatter.
+__global__ void __launch_bounds__(kSortWarps * 32) k_order_count(const SellSlice* in, uint32_t n, uint32_t* ghist) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ uint32_t hist[kSortWarps][kBins];
+    for (uint32_t i = threadIdx.x; i < kSortWarps * kBins; i += blockDim.x) (&hist[0][0])[i] = 0u;
+    __syncthreads();
+    const uint32_t c0 = min(n, blockIdx.x * kSellWindow + warp * kSortChunk), c1 = min(n, c0 + kSortChunk);
+    for (uint32_t i = c0 + lane; i < c1; i += 32) atomicAdd(&hist[warp][deg_bin(in[i].width)], 1u);
+    __syncthreads();
+    uint32_t* g = ghist + (uint64_t)blockIdx.x * kSortWarps * kBins;
+    for (uint32_t i = threadIdx.x; i < kSortWarps * kBins; i += blockDim.x) g[i] = (&hist[0][0])[i];
+}
+
+// single CTA: per-(chunk, warp) offsets for every bin, bins descending, chunks
+// and warps in order
+__global__ void __launch_bounds__(1024) k_order_offsets(uint32_t* ghist, uint32_t n_warps_total) {
+    __shared__ uint32_t tot[kBins];
+    for (uint32_t b = threadIdx.x; b < kBins; b += blockDim.x) {
+        uint32_t t = 0;
+        for (uint32_t w = 0; w < n_warps_total; ++w) t += ghist[(uint64_t)w * kBins + b];
+        tot[b] = t;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = (int)kBins - 1; b >= 0; --b) {
+            const uint32_t c = tot[b];
+            tot[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < kBins; b += blockDim.x) {
+        uint32_t run = tot[b];
+        for (uint32_t w = 0; w < n_warps_total; ++w) {
+            const uint32_t c = ghist[(uint64_t)w * kBins + b];
+            ghist[(uint64_t)w * kBins + b] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_order_scatter(const SellSlice* in, uint32_t n, uint32_t* ghist,
+                                                                   SellSlice* out) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t c0 = min(n, blockIdx.x * kSellWindow + warp * kSortChunk), c1 = min(n, c0 + kSortChunk);
+    uint32_t* offs = ghist + ((uint64_t)blockIdx.x * kSortWarps + warp) * kBins;
+    warp_scatter(
+        c0, c1, offs, [&](uint32_t i) { return deg_bin(in[i].width); },
+        [&](uint32_t i, uint32_t pos) { out[pos] = in[i]; });
 }
 
 uint32_t grid_warps(uint64_t warps, uint32_t block) {
@@ -372,8 +476,13 @@ cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t
     cudaError_t e = cudaMemsetAsync(scratch_cnt, 0, 4, s);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    k_sort_rows_warp<<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, src, w, ssrc, sw, scratch_runs, scratch_cnt);
-    k_sort_rows_block<<<152 * 4, 256, 0, s>>>(col_ptr, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+    if (w) {
+        k_sort_rows_warp<true><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_block<true><<<152 * 8, 256, 0, s>>>(col_ptr, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+    } else {
+        k_sort_rows_warp<false><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_block<false><<<152 * 8, 256, 0, s>>>(col_ptr, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+    }
     return cudaGetLastError();
 }
 
@@ -381,7 +490,7 @@ cudaError_t launch_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H,
                                 uint32_t* hub_out, uint32_t* nonhub_cnt, uint32_t* hub_cnt, cudaStream_t s) {
     const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
     if (nw == 0) return cudaSuccess;
-    k_sell_windows<<<nw, 32, 0, s>>>(col_ptr, n, H, rows_out, hub_out, nonhub_cnt, hub_cnt);
+    k_sell_windows<<<nw, kSortWarps * 32, 0, s>>>(col_ptr, n, H, rows_out, hub_out, nonhub_cnt, hub_cnt);
     return cudaGetLastError();
 }
 
@@ -421,10 +530,19 @@ cudaError_t launch_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, cudaStream_t s) {
+cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, uint32_t* scratch,
+                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_order_slices<<<1, 32, 0, s>>>(in, n, out);
+    const uint32_t chunks = (n + kSellWindow - 1) / kSellWindow;
+    k_order_count<<<chunks, kSortWarps * 32, 0, s>>>(in, n, scratch);
+    k_order_offsets<<<1, 1024, 0, s>>>(scratch, chunks * kSortWarps);
+    k_order_scatter<<<chunks, kSortWarps * 32, 0, s>>>(in, n, scratch, out);
     return cudaGetLastError();
+}
+
+size_t order_slices_scratch_bytes(uint32_t n) {
+    const uint64_t chunks = (n + kSellWindow - 1) / kSellWindow;
+    return 4 * (size_t)(chunks + 1) * kSortWarps * kBins;
 }
 
 }  // namespace gxp
