@@ -66,6 +66,13 @@ void Engine::prepare_batch(bool streamed) {
             }
         }
         b.unit_edge.push_back(E);
+        // streamed edges are packed into 4 bytes when they fit (the stream is
+        // bound by the host link); resident edges stay 8 bytes (the kernel is
+        // bound by instruction issue, and unpacking costs more than it saves)
+        uint32_t wmax = 0;
+        for (uint32_t x : hp.w) wmax = std::max(wmax, x);
+        b.packed = packable(V, wmax);
+        b.esize = b.packed ? 4u : 8u;
         b.d_units = (uint4*)dalloc(sizeof(uint4) * std::max<size_t>(b.units.size(), 1));
         if (!b.units.empty())
             cuda_check(cudaMemcpy(b.d_units, b.units.data(), sizeof(uint4) * b.units.size(), cudaMemcpyHostToDevice),
@@ -85,24 +92,26 @@ void Engine::prepare_batch(bool streamed) {
         cuda_check(cudaEventCreate(&b.ev_t1), "event");
         b.ready = true;
     }
-    auto fill = [&](uint2* dst) {
-        for (uint64_t e = 0; e < E; ++e) dst[e] = make_uint2(hp.src[e], hp.w[e]);
+    auto fill = [&](void* dst, bool packed) {
+        if (packed) {
+            uint32_t* d = static_cast<uint32_t*>(dst);
+            for (uint64_t e = 0; e < E; ++e) d[e] = hp.w[e] << kPackSrcBits | hp.src[e];
+        } else {
+            uint2* d = static_cast<uint2*>(dst);
+            for (uint64_t e = 0; e < E; ++e) d[e] = make_uint2(hp.src[e], hp.w[e]);
+        }
     };
+    const size_t ebytes = (size_t)b.esize * E;
     if (streamed && !b.pinned_ready) {
-        cuda_check(cudaHostAlloc((void**)&b.h_edges, sizeof(uint2) * std::max<uint64_t>(E, 1), cudaHostAllocDefault),
-                   "pinned edge buffer");
-        fill(b.h_edges);
+        cuda_check(cudaHostAlloc(&b.h_edges, std::max<size_t>(ebytes, 8), cudaHostAllocDefault), "pinned edge buffer");
+        fill(b.h_edges, b.packed);
         b.pinned_ready = true;
     }
     if (!streamed && !b.resident) {
-        b.d_edges = (uint2*)dalloc(sizeof(uint2) * std::max<uint64_t>(E, 1));
-        if (b.pinned_ready) {
-            cuda_check(cudaMemcpy(b.d_edges, b.h_edges, sizeof(uint2) * E, cudaMemcpyHostToDevice), "upload edges");
-        } else {
-            std::vector<uint2> tmp(E);
-            fill(tmp.data());
-            cuda_check(cudaMemcpy(b.d_edges, tmp.data(), sizeof(uint2) * E, cudaMemcpyHostToDevice), "upload edges");
-        }
+        b.d_edges = dalloc(std::max<size_t>(8 * E, 8));
+        std::vector<uint2> tmp(E);
+        fill(tmp.data(), false);
+        cuda_check(cudaMemcpy(b.d_edges, tmp.data(), 8 * E, cudaMemcpyHostToDevice), "upload edges");
         b.resident = true;
     }
 }
@@ -136,6 +145,7 @@ void Engine::superstep_batch(const std::vector<uint64_t>& cuts, bool streamed, b
     cuda_check(cudaMemsetAsync(b.d_changed, 0, 8 * std::max<size_t>(nb, 1), stream_), "memset");
     MsArgs a{};
     a.units = b.d_units;
+    a.packed = streamed && b.packed;
     a.dist = b.d_dist;
     a.frontier_cur = fr_cur;
     a.frontier_next = fr_next;
@@ -162,8 +172,8 @@ void Engine::superstep_batch(const std::vector<uint64_t>& cuts, bool streamed, b
         if (i >= 3 || !pipelined) {
             if (i >= 1) cuda_check(cudaStreamWaitEvent(b.s_h2d, b.ev_free[pipelined ? slot : (int)((i - 1) % 3)], 0), "wait");
         }
-        cuda_check(cudaMemcpyAsync(b.d_ring[slot], b.h_edges + e0, sizeof(uint2) * (e1 - e0), cudaMemcpyHostToDevice,
-                                   b.s_h2d), "download block");
+        cuda_check(cudaMemcpyAsync(b.d_ring[slot], static_cast<const char*>(b.h_edges) + (size_t)b.esize * e0,
+                                   (size_t)b.esize * (e1 - e0), cudaMemcpyHostToDevice, b.s_h2d), "download block");
         cuda_check(cudaEventRecord(b.ev_loaded[slot], b.s_h2d), "event");
         // compute (c)
         cuda_check(cudaStreamWaitEvent(stream_, b.ev_loaded[slot], 0), "wait");
@@ -234,7 +244,7 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
         const uint64_t sample = std::min<uint64_t>(std::max<uint64_t>(E, 1), 1ull << 24);
         auto ensure = [&](uint64_t ring, size_t blocks) {
             if (ring > b.ring_edges) {
-                for (int i = 0; i < 3; ++i) b.d_ring[i] = (uint2*)dalloc(sizeof(uint2) * ring);
+                for (int i = 0; i < 3; ++i) b.d_ring[i] = dalloc((size_t)b.esize * ring);
                 b.ring_edges = ring;
             }
             if (blocks > b.max_blocks) {
@@ -253,7 +263,8 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
             float best = 1e30f;
             for (int i = 0; i < 3; ++i) {
                 cuda_check(cudaEventRecord(t0, stream_), "event");
-                cuda_check(cudaMemcpyAsync(b.d_ring[0], b.h_edges, sizeof(uint2) * sample, cudaMemcpyHostToDevice, stream_), "copy");
+                cuda_check(cudaMemcpyAsync(b.d_ring[0], b.h_edges, (size_t)b.esize * sample, cudaMemcpyHostToDevice,
+                                           stream_), "copy");
                 cuda_check(cudaEventRecord(t1, stream_), "event");
                 cuda_check(cudaEventSynchronize(t1), "sync");
                 float ms;
@@ -267,6 +278,7 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
             const auto cuts_s = block_cuts(sample);
             MsArgs a{};
             a.units = b.d_units;
+            a.packed = b.packed;
             a.u_begin = 0;
             a.u_end = cuts_s[1];
             a.edges = b.d_ring[0];
@@ -340,7 +352,7 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
         uint64_t mx = 0;
         for (size_t i = 0; i + 1 < cuts.size(); ++i) mx = std::max<uint64_t>(mx, b.unit_edge[cuts[i + 1]] - b.unit_edge[cuts[i]]);
         if (mx > b.ring_edges) {
-            for (int i = 0; i < 3; ++i) b.d_ring[i] = (uint2*)dalloc(sizeof(uint2) * mx);
+            for (int i = 0; i < 3; ++i) b.d_ring[i] = dalloc((size_t)b.esize * mx);
             b.ring_edges = mx;
         }
     }

@@ -133,9 +133,11 @@ private:
         std::vector<uint4> units;          // {dst, first edge, edges, split}
         std::vector<uint64_t> unit_edge;   // first edge of each unit, + total at the end
         uint4* d_units = nullptr;
-        uint2* h_edges = nullptr;          // pinned (source, weight) in destination order
-        uint2* d_edges = nullptr;          // resident copy
-        uint2* d_ring[3] = {nullptr, nullptr, nullptr};
+        void* h_edges = nullptr;           // pinned streamed edges, destination order (esize bytes each)
+        void* d_edges = nullptr;           // resident copy, (source, weight) uint2
+        void* d_ring[3] = {nullptr, nullptr, nullptr};
+        uint32_t esize = 8;                // streamed edge: 8 = (source, weight) uint2, 4 = packed uint32
+        bool packed = false;
         uint64_t ring_edges = 0;
         uint32_t* d_dist = nullptr;        // [V][64]
         uint32_t* d_frontier[2] = {nullptr, nullptr};

@@ -158,10 +158,17 @@ struct SellArgs {
 
 // Arguments of the batched multi-source SSSP superstep kernel (one edge block).
 constexpr uint32_t kUnitEdges = 256;   // in-edges of one destination per warp work unit
+// packed edge (4 bytes): weight << 24 | source, when sources < 2^24 and weights < 256
+constexpr uint32_t kPackSrcBits = 24;
+inline bool packable(uint64_t n_vertices, uint32_t max_weight) {
+    return n_vertices <= (1ull << kPackSrcBits) && max_weight < 256u;
+}
 struct MsArgs {
     const uint4* units;          // {dst, first edge (global), edges, split-row flag}
     uint64_t u_begin, u_end;     // this block's units
-    const uint2* edges;          // (source, weight); edges[i] is global edge edge_base + i
+    const void* edges;           // edges[i] is global edge edge_base + i: (source, weight) uint2,
+                                 // or with `packed` one uint32 (weight << 24 | source)
+    uint32_t packed;
     uint64_t edge_base;
     uint32_t* dist;              // [V][64]
     const uint32_t* frontier_cur;

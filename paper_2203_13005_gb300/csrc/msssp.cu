@@ -4,7 +4,9 @@
 // the pipeline shuffle of Section III-A) serves all sources.
 //
 // Layout: dist[v][64] uint32 (one 256-byte row per vertex); an edge is a
-// (source, weight) uint2 in destination order. Work unit = up to
+// (source, weight) uint2 in destination order, or one uint32 (weight << 24 |
+// source) when sources and weights fit, halving the bytes every superstep
+// reads (and streams). Work unit = up to
 // kUnitEdges in-edges of one destination; a warp owns a unit and each lane
 // two source slots:
 //   MSGGen   the warp reads 32 in-edges at once (one per lane, coalesced)
@@ -38,7 +40,16 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t d, uint32_t w) {
     return s;
 }
 
-template <bool kDry>
+template <bool kPacked>
+__device__ __forceinline__ uint2 load_edge(const void* base, uint64_t i) {
+    if (kPacked) {
+        const uint32_t p = __ldg(static_cast<const uint32_t*>(base) + i);
+        return make_uint2(p & ((1u << kPackSrcBits) - 1u), p >> kPackSrcBits);
+    }
+    return __ldg(static_cast<const uint2*>(base) + i);
+}
+
+template <bool kDry, bool kPacked>
 __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
     __shared__ uint32_t s_imp[2], s_done;
     __shared__ unsigned long long s_changed;
@@ -57,7 +68,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
     for (uint64_t k = a.u_begin + warp0; k < a.u_end; k += n_warps) {
         const uint4 un = a.units[k];   // v, first edge (global), edges, split flag
         const uint32_t v = un.x, len = un.z;
-        const uint2* e = a.edges + (un.y - a.edge_base);
+        const uint64_t e = un.y - a.edge_base;   // first edge of the unit in this block
         uint2 acc = make_uint2(kInf, kInf);
         bool any = false;
         for (uint32_t base = 0; base < len; base += 32u) {
@@ -65,7 +76,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
             uint2 my = make_uint2(0u, 0u);
             bool act = false;
             if (base + lane < len) {
-                my = __ldg(e + base + lane);
+                my = load_edge<kPacked>(a.edges, e + base + lane);
                 act = (__ldg(a.frontier_cur + (my.x >> 5)) >> (my.x & 31u)) & 1u;
             }
             uint32_t mask = __ballot_sync(kFull, act);
@@ -170,8 +181,13 @@ __global__ void k_popc(const uint32_t* bits, uint64_t words, unsigned long long*
 
 cudaError_t launch_msssp(const MsArgs& a, bool dry, uint32_t grid, cudaStream_t s) {
     if (a.u_end <= a.u_begin) return cudaSuccess;
-    if (dry) k_msssp<true><<<grid, kMsBlock, 0, s>>>(a);
-    else k_msssp<false><<<grid, kMsBlock, 0, s>>>(a);
+    if (a.packed) {
+        if (dry) k_msssp<true, true><<<grid, kMsBlock, 0, s>>>(a);
+        else k_msssp<false, true><<<grid, kMsBlock, 0, s>>>(a);
+    } else {
+        if (dry) k_msssp<true, false><<<grid, kMsBlock, 0, s>>>(a);
+        else k_msssp<false, false><<<grid, kMsBlock, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -114,7 +114,11 @@ uint32_t Server::add_graph(uint64_t n, uint64_t m, const uint32_t* src_in, const
     }
     if (bad) fail(GXP_E_INVAL, "vertex id out of range");
     for (uint64_t v = 0; v < n; ++v) col[v + 1] += col[v];
-    std::vector<uint2> edges(m);
+    // resident edges stay 8 bytes: the 64-slot superstep is bound by instruction
+    // issue, and unpacking a 4-byte edge costs more than the bytes it saves
+    const bool packed = false;
+    std::vector<uint2> edges(packed ? 0 : m);
+    std::vector<uint32_t> epacked(packed ? m : 0);
     std::vector<uint32_t> esrc(m);
 #pragma omp parallel num_threads(T)
     {
@@ -125,7 +129,9 @@ uint32_t Server::add_graph(uint64_t n, uint64_t m, const uint32_t* src_in, const
             const uint32_t d = dst[e];
             if (d < lo || d >= hi) continue;
             const uint64_t p = pos[d - lo]++;
-            edges[p] = make_uint2(src[e], w ? w[e] : 1u);
+            const uint32_t wt = w ? w[e] : 1u;
+            if (packed) epacked[p] = wt << kPackSrcBits | src[e];
+            else edges[p] = make_uint2(src[e], wt);
             esrc[p] = src[e];
         }
     }
@@ -171,7 +177,8 @@ uint32_t Server::add_graph(uint64_t n, uint64_t m, const uint32_t* src_in, const
     };
     G->d_units_all = (uint4*)up(all.data(), sizeof(uint4) * all.size());
     G->d_units_nz = (uint4*)up(nz.data(), sizeof(uint4) * nz.size());
-    G->d_edges = (uint2*)up(edges.data(), sizeof(uint2) * m);
+    G->packed = packed;
+    G->d_edges = packed ? up(epacked.data(), 4 * m) : up(edges.data(), sizeof(uint2) * m);
     G->d_src = (uint32_t*)up(esrc.data(), 4 * m);
     std::vector<float> inv(n);
     for (uint64_t v = 0; v < n; ++v) inv[v] = outdeg[v] ? 1.0f / (float)outdeg[v] : 0.0f;
@@ -421,6 +428,7 @@ void Server::lane_step(Lane& L, ServedGraph& G, uint64_t admit) {
         a.u_begin = 0;
         a.u_end = G.n_units_nz;
         a.edges = G.d_edges;
+        a.packed = G.packed;
         a.edge_base = 0;
         a.dist = L.d_dist;
         a.frontier_cur = L.d_frontier[L.cur];

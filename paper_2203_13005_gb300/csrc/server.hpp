@@ -81,7 +81,8 @@ struct ServedGraph {
     uint64_t n_units_all = 0;
     uint4* d_units_nz = nullptr;    // vertices with in-edges (SSSP)
     uint64_t n_units_nz = 0;
-    uint2* d_edges = nullptr;       // (source, weight), destination order
+    void* d_edges = nullptr;        // (source, weight) uint2 or packed uint32, destination order
+    bool packed = false;
     uint32_t* d_src = nullptr;      // source, destination order
     float* d_inv_outdeg = nullptr;  // 1 / out-degree, 0 for vertices without out-edges
     uint2* d_split_rows = nullptr;

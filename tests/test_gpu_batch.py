@@ -114,3 +114,18 @@ def test_batch_rmat24_streamed_two_sources_vs_oracle():
     with _ctx(n, src, dst, w) as c:
         dist, rep = c.sssp_batch(sources, streamed=True, use_graph=True)
     _check(n, src, dst, w, sources[:2], dist)
+
+
+def test_batch_wide_weights_unpacked_edges():
+    # weights above 255 do not fit the 4-byte packed edge: the 8-byte layout runs
+    rng = np.random.default_rng(77)
+    n, m = 3000, 40000
+    src = rng.integers(0, n, m, dtype=np.uint32)
+    dst = rng.integers(0, n, m, dtype=np.uint32)
+    w = rng.integers(1, 100000, m, dtype=np.uint32)
+    sources = synth.sources_with_out_edges(n, src, 16, 5)
+    with _ctx(n, src, dst, w) as c:
+        dist, _ = c.sssp_batch(sources)
+        dist_s, _ = c.sssp_batch(sources, streamed=True, block_edges=5000)
+    assert np.array_equal(dist, dist_s)
+    _check(n, src, dst, w, sources, dist)

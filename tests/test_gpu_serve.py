@@ -295,3 +295,22 @@ def test_device_output_buffer(graphs):
         assert srv.poll(q, out)
         ref, _, _ = oracle.sssp(n, src, dst, w, s)
         assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
+
+
+def test_served_sssp_wide_weights():
+    # weights above 255: the server keeps 8-byte edges for this graph
+    rng = np.random.default_rng(78)
+    n, m = 2000, 30000
+    src = rng.integers(0, n, m, dtype=np.uint32)
+    dst = rng.integers(0, n, m, dtype=np.uint32)
+    w = rng.integers(1, 70000, m, dtype=np.uint32)
+    ctx = gxp.Context(0)
+    srv = gxp.Server(ctx)
+    with ctx:
+        srv.add_graph(n, src, dst, w)
+        srv.start()
+        srcs = _sources(n, src, 6, 3)
+        qs = [srv.submit(0, SSSP, int(s)) for s in srcs]
+        for q, s in zip(qs, srcs):
+            ref, _, _ = oracle.sssp(n, src, dst, w, int(s))
+            assert np.array_equal(srv.result(q, SSSP, 0), ref)
