@@ -215,6 +215,82 @@ def run_msssp(args):
     ctx.close()
 
 
+def run_sssp(args):
+    """SSSP (Bellman-Ford, min merge) on R-MAT scale 16 from source 0 to
+    convergence: supersteps are enqueued in chunks with one host read of
+    their changed counts per chunk (gxp_run). GTEPS = supersteps x edges /
+    run time; the roofline is taken per superstep kernel over a full sweep
+    (the whole 13 MB working set is L2-resident, so it is quoted against HBM
+    only for comparison)."""
+    import torch
+    from paper_2203_13005_gb300 import gxp
+    wl = synth.SSSP_RMAT16
+    src, dst, w = wl.edges()
+    n, m = wl.n_vertices, wl.n_edges
+    stream = torch.cuda.Stream()
+    ctx = gxp.Context(0)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.create_graph(n, 1)
+    ctx.load_coo(src, dst, w)
+    for _ in range(args.warmup):
+        steps = ctx.run(gxp.GXP_ALGO_SSSP, 0)
+    reps = max(args.steps, 10)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(reps):
+            steps = ctx.run(gxp.GXP_ALGO_SSSP, 0)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    # per-superstep kernel time: one run's supersteps, each bracketed by events
+    g, mm, a = gxp.TEMPLATES[gxp.GXP_ALGO_SSSP]
+    ctx.begin(gxp.GXP_ALGO_SSSP, 0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for b, e in evs:
+        b.record(stream)
+        ctx.lib.gxp_superstep(ctx.h, gxp.GXP_ALGO_SSSP, g, mm, a, None)
+        e.record(stream)
+    torch.cuda.synchronize()
+    k_us = statistics.mean(b.elapsed_time(e) for b, e in evs) * 1e3
+    bytes_sweep = 12 * m + 12 * n + n // 4   # src + w + gathered value per edge; col_ptr, d read, d write, bitmap
+    # end to end: COO from host memory -> load -> run -> distances back
+    out = np.empty(n, dtype=np.uint32)
+    e2e = []
+    for i in range(4):
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        c2 = gxp.Context(0)
+        c2.create_graph(n, 1)
+        c2.load_coo(src, dst, w)
+        c2.run(gxp.GXP_ALGO_SSSP, 0)
+        c2.values(out=out)
+        torch.cuda.synchronize()
+        if i:
+            e2e.append(time.perf_counter() - c0)
+        c2.close()
+    e2e_s = statistics.median(e2e)
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": steps * m / (ms * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": reps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl.name, "vertices": n, "edges": m, "source": 0, "supersteps": steps,
+                   "step": "one gxp_run to convergence (supersteps enqueued in chunks of 4, 8, 16)",
+                   "l2": "13 MB working set: L2-resident"},
+        "roofline": {"bound": "hbm", "achieved": bytes_sweep / (k_us * 1e-6) / 1e9, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": bytes_sweep / (k_us * 1e-6) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"], "kernel": "k_sell<SSSP>", "avg_launch_us": k_us,
+                     "algorithmic_bytes_per_launch": bytes_sweep},
+        "e2e": {"value": steps * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 12 * m,
+                "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_s * 1e3},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_cc(args):
     """Connected components (min-label propagation) on the Erdős–Rényi graph with
     2^24 vertices and 2^28 directed edges in 8 partitions with sync caching and
@@ -447,7 +523,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default=WL.name,
-                    choices=[WL.name, synth.MSSSP_RMAT24.name, synth.CC_ER24_P8.name, "serve"],
+                    choices=[WL.name, synth.SSSP_RMAT16.name, synth.MSSSP_RMAT24.name, synth.CC_ER24_P8.name,
+                             "serve"],
                     help="extra workloads print their own line; the default is the headline")
     ap.add_argument("--serve-rate", type=float, default=synth.SERVE_RATE, help="serve: offered queries/s")
     ap.add_argument("--serve-seconds", type=float, default=synth.SERVE_SECONDS, help="serve: arrival window")
@@ -468,6 +545,9 @@ def main():
         return
     if args.workload == synth.CC_ER24_P8.name:
         run_cc(args)
+        return
+    if args.workload == synth.SSSP_RMAT16.name:
+        run_sssp(args)
         return
     if args.workload == "serve":
         run_serve(args)

@@ -44,6 +44,7 @@ bool is_device_ptr(const void* p) {
 Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
     gxp_config_default(&cfg_);
     if (cfg) cfg_ = *cfg;
+    auto_tiles_ = cfg_.tile_items == 0 && cfg_.hub_items == 0;
     if (cfg_.tile_items == 0) cfg_.tile_items = kDefaultTile;
     if (cfg_.hub_items == 0) cfg_.hub_items = cfg_.tile_items / 2;
     if (cfg_.timeout_ns == 0) cfg_.timeout_ns = 2000000000ull;
@@ -346,7 +347,17 @@ uint32_t* Engine::upload_u32(const std::vector<uint32_t>& h, size_t n_pad) {
 // split into parts; then all slices ordered heavy-first. A few small counts
 // come back to the host to size the arrays.
 void Engine::build_sell() {
-    const uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
+    uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
+    if (auto_tiles_) {
+        // by default the longest work item shrinks with the graph: a slice row
+        // of up to H in-edges and a hub part of T edges stay short next to the
+        // average work per warp (H = 1024 / T = 2048 from ~64 M edges up)
+        uint64_t h = std::max<uint64_t>(32, total_edges_ >> 16);
+        uint64_t p2 = 32;
+        while (p2 * 2 <= h) p2 *= 2;
+        H = (uint32_t)std::min<uint64_t>(1024, p2);
+        T = std::min<uint32_t>(2048, std::max<uint32_t>(256, 2 * H));
+    }
     std::vector<void*> tmp;   // freed when the build ends
     auto talloc = [&](size_t bytes) {
         void* q = nullptr;
@@ -675,6 +686,7 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
     a.damping = damping_;
     a.inv_n = 1.0 / (double)n_vertices_;
     a.ppr_source = ppr_source_;
+    a.skip_if_quiet = (early_exit_ && step_ > 0 && algo_ != Algo::PR) ? 1u : 0u;
     cuda_check(cudaEventRecord(ev_a_, stream_), "event");
     cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
     if (n_parts_ > 1) {
@@ -702,18 +714,26 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
     cuda_check(cudaEventRecord(ev_b_, stream_), "event");
     cur_ = nx;
     ++step_;
-    if (want || step_ - accounted_ >= 32) account(true);
+    if (want || step_ - accounted_ >= 32) account(false);
     return st_.last_changed;
 }
 
 // Fold the device-side stats of the supersteps not yet read into st_.
-void Engine::account(bool) {
-    if (accounted_ == step_) return;
+// Fold the device-side stats of the supersteps not yet read into st_ (one
+// copy of the stat ring). With stop_at_quiet, stop at the first superstep
+// that changed nothing and roll the step counter back to it (the supersteps
+// enqueued after it ran on a fixed point and changed nothing either); its
+// index is returned, else 0.
+uint64_t Engine::account(bool stop_at_quiet) {
+    if (accounted_ == step_) return 0;
     cuda_check(cudaStreamSynchronize(stream_), "superstep");
     check_device_error();
+    ring_host_.resize(kStatRing);
+    cuda_check(cudaMemcpy(ring_host_.data(), d_stats_, sizeof(StepStats) * kStatRing, cudaMemcpyDeviceToHost),
+               "read stats");
+    uint64_t quiet = 0;
     for (uint64_t t = accounted_ + 1; t <= step_; ++t) {
-        StepStats s;
-        cuda_check(cudaMemcpy(&s, d_stats_ + (t % kStatRing), sizeof(s), cudaMemcpyDeviceToHost), "read stats");
+        const StepStats& s = ring_host_[t % kStatRing];
         unsigned long long ch = 0, dg = 0, l1 = 0;
         for (int i = 0; i < kStatLanes; ++i) {
             ch += s.changed[i];
@@ -733,18 +753,30 @@ void Engine::account(bool) {
             if (s.skipped) st_.syncs_skipped++;
             else st_.syncs_done++;
         }
+        if (stop_at_quiet && ch == 0) {
+            quiet = t;
+            break;
+        }
     }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) st_.last_superstep_ms = ms;
     else cudaGetLastError();
+    if (quiet && quiet < step_) {
+        // the next two supersteps accumulate into these slots: clear the overshoot's values
+        for (uint64_t t = quiet + 1; t <= quiet + 2; ++t)
+            cuda_check(cudaMemsetAsync(d_stats_ + (t % kStatRing), 0, sizeof(StepStats), stream_), "memset");
+        step_ = quiet;
+        cur_ = (int)(quiet & 1u);   // the buffer the quiet superstep wrote (later ones may have returned early)
+    }
     accounted_ = step_;
+    return quiet;
 }
 
 void Engine::sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap, uint64_t* n_out, int* skipped) {
     if (!begun_ || step_ == 0) fail(GXP_E_STATE, "no superstep has run");
     if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
     if (!n_out) fail(GXP_E_INVAL, "n_out is required");
-    account(true);
+    account(false);
     if (n_parts_ == 1) {
         *n_out = 0;
         if (skipped) *skipped = 1;
@@ -772,13 +804,26 @@ uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max
     uint32_t steps = 0;
     if (algo_ == Algo::PR) {
         for (; steps < max_steps; ++steps) superstep(algo, g, m, ap, false);
-        account(true);
+        account(false);
         return steps;
     }
+    // SSSP / CC: supersteps are enqueued in growing chunks and the host reads
+    // their changed counts once per chunk; the run ends at the first
+    // superstep that changed nothing (the count includes it)
+    // and the ones after a quiet superstep return at once on the device
+    uint32_t chunk = 4;
+    struct EarlyExit {
+        bool& f;
+        ~EarlyExit() { f = false; }
+    } guard{early_exit_};
+    early_exit_ = true;
     while (steps < max_steps) {
-        const uint64_t ch = superstep(algo, g, m, ap, true);
-        ++steps;
-        if (ch == 0) break;
+        const uint32_t k = std::min<uint32_t>(chunk, max_steps - steps);
+        for (uint32_t i = 0; i < k; ++i) superstep(algo, g, m, ap, false);
+        const uint64_t quiet = account(true);
+        if (quiet) return (uint32_t)quiet;
+        steps += k;
+        chunk = std::min<uint32_t>(2 * chunk, 16);
     }
     return steps;
 }
@@ -810,14 +855,14 @@ void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
         cnt = parts_[part].n_own;
     }
     if (n != cnt) fail(GXP_E_INVAL, "n must equal the number of vertices given");
-    account(true);
+    account(false);
     cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
     cuda_check(launch_init_ghosts(algo_, n_ghost_total_, d_ghost_gid_, d_own_[cur_], d_ghost_, stream_), "refresh caches");
     cuda_check(cudaStreamSynchronize(stream_), "set values");
 }
 
 void Engine::stats(gxp_stats* out) {
-    if (begun_) account(true);
+    if (begun_) account(false);
     *out = st_;
     out->device_bytes = graph_bytes_;
 }

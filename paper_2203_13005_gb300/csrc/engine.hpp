@@ -77,7 +77,8 @@ private:
     void build_sell();
     void build_caches();
     uint32_t* upload_u32(const std::vector<uint32_t>& h, size_t n_pad);
-    void account(bool force);
+    uint64_t account(bool stop_at_quiet);
+    std::vector<StepStats> ring_host_;
     void check_device_error();
     void copy_in(void* dst, const void* src, size_t bytes);   // host or device src -> host dst
     void load_csc_device(HostPart& hp, uint64_t n_edges, const void* col_ptr, const uint32_t* src,
@@ -156,6 +157,8 @@ private:
     Algo algo_ = Algo::SSSP;
     uint32_t source_ = 0;
     uint32_t ppr_source_ = kInf;   // personalized PageRank: its source; else kInf
+    bool early_exit_ = false;      // inside gxp_run: supersteps after a quiet one return at once
+    bool auto_tiles_ = false;      // tile / hub sizes chosen from the graph's size
     float damping_ = 0.85f;
     int cur_ = 0;
     uint64_t step_ = 0, accounted_ = 0;

@@ -154,6 +154,7 @@ struct SellArgs {
     float damping;
     double inv_n;
     uint32_t ppr_source;         // PageRank: kInf; personalized PageRank: the source vertex
+    uint32_t skip_if_quiet;      // 1: return at once if the previous superstep changed nothing
 };
 
 // Arguments of the batched multi-source SSSP superstep kernel (one edge block).

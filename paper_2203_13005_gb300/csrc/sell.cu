@@ -94,6 +94,13 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats_clear);
         for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
     }
+    if (a.skip_if_quiet) {
+        // min-label algorithms at a fixed point: nothing can change any more
+        unsigned long long c = a.stats_in->changed[lane] + a.stats_in->changed[lane + 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (c == 0ull) return;   // same for every thread of the grid
+    }
     if (tid == 0) {
         s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
         s_done = 0u;

@@ -328,6 +328,28 @@ def test_csc_single_partition_loads_on_device():
         assert np.array_equal(c.values(), d_ref)
 
 
+@pytest.mark.parametrize("parts", [1, 3])
+def test_run_stops_at_first_quiet_superstep(parts):
+    """gxp_run enqueues supersteps in chunks; the ones after the first quiet
+    superstep return at once on the device and are rolled back."""
+    n = 500
+    src, dst, w = _rand_graph(9, n, 4000)
+    d_ref, steps_ref, _ = oracle.sssp(n, src, dst, w, 1)
+    with _ctx(n, parts=parts) as c:
+        c.load_coo(src, dst, w)
+        assert c.run(gxp.GXP_ALGO_SSSP, 1) == steps_ref
+        st = c.stats()
+        assert st["supersteps"] == steps_ref and st["last_changed"] == 0
+        assert np.array_equal(c.values(), d_ref)
+        assert c.superstep() == 0                      # continuing from the fixed point
+        assert np.array_equal(c.values(), d_ref)
+        assert c.stats()["supersteps"] == steps_ref + 1
+        assert c.run(gxp.GXP_ALGO_SSSP, 1, max_steps=2) == 2
+        assert c.run(gxp.GXP_ALGO_CC) >= 1
+        labels, _, _ = oracle.cc(n, src, dst)
+        assert np.array_equal(c.values(), labels)
+
+
 def test_errors_are_status_codes():
     with _ctx(4) as c:
         with pytest.raises(gxp.GxpError) as ei:
