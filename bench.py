@@ -402,62 +402,93 @@ def run_serve(args):
         e.run(gxp.GXP_ALGO_SSSP, int(elig[g][0]))
         e.run(gxp.GXP_ALGO_PPR, int(elig[g][0]), synth.SERVE_DAMPING, synth.SERVE_ITERS)
 
-    # open-loop replay of the stream
-    lock = threading.Lock()
-    qidx = {}
-    lat = np.full(N, np.nan)
-    info = [None] * N
-    finish = [0.0]
-    drain_limit = args.serve_drain
-    t_base = [0.0]
+    def replay(rate_q, dur_q):
+        """Open-loop replay of a Poisson stream at rate_q for dur_q seconds:
+        latency = scheduled arrival -> result in pinned host memory."""
+        st = synth.serve_stream(rate_q, dur_q, [len(e) for e in elig], synth.SERVE_SEED)
+        n_q = len(st["t"])
+        srcs_q = np.array([elig[g][p] for g, p in zip(st["graph"], st["pick"])], dtype=np.uint32)
+        lock = threading.Lock()
+        qidx = {}
+        lat = np.full(n_q, np.nan)
+        info = [None] * n_q
+        finish = [0.0]
+        t_base = [0.0]
+        rep0 = srv.report()
 
-    def collector():
-        got = 0
-        while got < N:
-            q = srv.next_done(1000)
-            if q == 0:
-                if time.perf_counter() - t_base[0] > dur + drain_limit:
-                    break
-                continue
-            with lock:
-                i = qidx.get(q)
-            while i is None:   # submit() returned but the id is not recorded yet
-                time.sleep(1e-5)
+        def collector():
+            got = 0
+            while got < n_q:
+                q = srv.next_done(1000)
+                if q == 0:
+                    if time.perf_counter() - t_base[0] > dur_q + args.serve_drain:
+                        break
+                    continue
                 with lock:
                     i = qidx.get(q)
-            info[i] = srv.info(q)
-            srv.poll(q, buf)
-            t = time.perf_counter()
-            lat[i] = t - (t_base[0] + stream["t"][i])
-            finish[0] = t
-            got += 1
+                while i is None:   # submit() returned but the id is not recorded yet
+                    time.sleep(1e-5)
+                    with lock:
+                        i = qidx.get(q)
+                info[i] = srv.info(q)
+                srv.poll(q, buf)
+                t = time.perf_counter()
+                lat[i] = t - (t_base[0] + st["t"][i])
+                finish[0] = t
+                got += 1
 
-    col = threading.Thread(target=collector)
-    with ClockSampler(0) as clk:
-        t_base[0] = time.perf_counter() + 0.05
-        col.start()
-        for i in range(N):
-            target = t_base[0] + stream["t"][i]
-            while True:
-                d = target - time.perf_counter()
-                if d <= 0:
+        col = threading.Thread(target=collector)
+        with ClockSampler(0) as clk:
+            t_base[0] = time.perf_counter() + 0.05
+            col.start()
+            for i in range(n_q):
+                target = t_base[0] + st["t"][i]
+                while True:
+                    d = target - time.perf_counter()
+                    if d <= 0:
+                        break
+                    time.sleep(d - 2e-4 if d > 5e-4 else 0)
+                q = srv.submit(int(st["graph"][i]), int(st["kind"][i]), int(srcs_q[i]),
+                               synth.SERVE_DAMPING, synth.SERVE_ITERS)
+                with lock:
+                    qidx[q] = i
+            col.join()
+        # whatever the drain limit left behind is collected before the next phase
+        while True:
+            q = srv.next_done(200)
+            if q == 0:
+                r = srv.report()
+                if r["queued"] + r["running"] == 0:
                     break
-                time.sleep(d - 2e-4 if d > 5e-4 else 0)
-            with lock:
-                qidx[submit(i)] = i
-        col.join()
-    rep = srv.report()
-    done = ~np.isnan(lat)
-    lat_ms = lat[done] * 1e3
-    span = finish[0] - t_base[0]
-    by = {}
-    for g, wl in enumerate(served):
-        for kind, kn in ((0, "sssp"), (1, "ppr")):
-            sel = done & (stream["graph"] == g) & (stream["kind"] == kind)
-            by[f"{kn}_rmat{wl.scale}"] = {"n": int(sel.sum()), "p50_ms": _pct(lat[sel] * 1e3, 50),
-                                          "p99_ms": _pct(lat[sel] * 1e3, 99)}
-    qms = [x["queue_ms"] for x in info if x]
-    rms = [x["run_ms"] for x in info if x]
+                continue
+            srv.poll(q, buf)
+        rep = srv.report()
+        done = ~np.isnan(lat)
+        lat_ms = lat[done] * 1e3
+        span = finish[0] - t_base[0]
+        by = {}
+        for g, wl in enumerate(served):
+            for kind, kn in ((0, "sssp"), (1, "ppr")):
+                sel = done & (st["graph"] == g) & (st["kind"] == kind)
+                by[f"{kn}_rmat{wl.scale}"] = {"n": int(sel.sum()), "p50_ms": _pct(lat[sel] * 1e3, 50),
+                                              "p99_ms": _pct(lat[sel] * 1e3, 99)}
+        qms = [x["queue_ms"] for x in info if x]
+        rms = [x["run_ms"] for x in info if x]
+        return {
+            "offered_qps": rate_q, "duration_s": dur_q, "submitted": int(n_q), "completed": int(done.sum()),
+            "achieved_qps": float(done.sum() / span) if span > 0 else 0.0, "span_s": span,
+            "backlog_at_end": int(n_q - done.sum()),
+            "latency": {"p50_ms": _pct(lat_ms, 50), "p90_ms": _pct(lat_ms, 90), "p99_ms": _pct(lat_ms, 99),
+                        "max_ms": float(lat_ms.max()) if len(lat_ms) else None,
+                        "queue_p50_ms": _pct(qms, 50), "queue_p99_ms": _pct(qms, 99),
+                        "run_p50_ms": _pct(rms, 50), "run_p99_ms": _pct(rms, 99), "by_lane": by},
+            "lane_supersteps": {"sssp": rep["sssp_supersteps"] - rep0["sssp_supersteps"],
+                                "ppr": rep["ppr_supersteps"] - rep0["ppr_supersteps"]},
+            "clocks": clk.summary(),
+        }
+
+    main = replay(rate, dur)
+    second = replay(args.serve_rate2, dur) if args.serve_rate2 > 0 else None
 
     # closed loop on the first K queries: one at a time vs all queued at once
     K = min(N, args.serve_closed)
@@ -486,26 +517,25 @@ def run_serve(args):
         keep = np.isin(stream["graph"], [i for i, h in enumerate(host) if h is not None])
         base = serve_cpu_baseline({k: v[keep] for k, v in stream.items()}, host)
         base["sample"] += " (its queries on the scale-18 and scale-20 graphs)"
+    rep = srv.report()
     line = {
-        "metric": "served-query p50/p99 latency", "value": float(done.sum() / span) if span > 0 else 0.0,
+        "metric": "served-query p50/p99 latency", "value": main["achieved_qps"],
         "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": main["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32+f32", "data": "synthetic",
         "config": {"workload": "serve_rmat" + "_".join(str(wl.scale) for wl in served), "offered_qps": rate,
                    "duration_s": dur,
                    "mix": f"graph uniform over {len(served)}, SSSP/PPR 1:1, sources uniform over out-degree >= 1",
                    "ppr": {"damping": synth.SERVE_DAMPING, "iters": synth.SERVE_ITERS},
                    "max_slots": 64, "results_per_graph": 128, "priorities": bool(args.serve_priorities)},
-        "latency": {"p50_ms": _pct(lat_ms, 50), "p90_ms": _pct(lat_ms, 90), "p99_ms": _pct(lat_ms, 99),
-                    "max_ms": float(lat_ms.max()) if len(lat_ms) else None,
-                    "queue_p50_ms": _pct(qms, 50), "queue_p99_ms": _pct(qms, 99),
-                    "run_p50_ms": _pct(rms, 50), "run_p99_ms": _pct(rms, 99), "by_lane": by},
-        "submitted": int(N), "completed": int(done.sum()), "backlog_at_end": int(N - done.sum()),
-        "lane_supersteps": {"sssp": rep["sssp_supersteps"], "ppr": rep["ppr_supersteps"]},
+        "latency": main["latency"],
+        "submitted": main["submitted"], "completed": main["completed"], "backlog_at_end": main["backlog_at_end"],
+        "lane_supersteps": main["lane_supersteps"],
+        "at_lower_rate": second,
         "closed_loop": {"queries": int(K), "one_at_a_time_qps": K / single_s, "batched_qps": K / batched_s,
                         "speedup": single_s / batched_s},
         "server_device_bytes": rep["device_bytes"], "graph_load_s": load_s,
-        "cpu_baseline": base, "clocks": clk.summary(),
+        "cpu_baseline": base, "clocks": main["clocks"],
     }
     print(json.dumps(line), flush=True)
     srv.stop()
@@ -532,6 +562,8 @@ def main():
     ap.add_argument("--serve-closed", type=int, default=1000, help="serve: queries of the closed-loop comparison")
     ap.add_argument("--serve-scales", default="18,20,22,24", help="serve: R-MAT scales of the served graphs")
     ap.add_argument("--serve-priorities", action="store_true", help="serve: smaller graphs' lanes first")
+    ap.add_argument("--serve-rate2", type=float, default=800.0,
+                    help="serve: a second open-loop run at this rate (0: none)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.warmup < 3:
