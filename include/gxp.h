@@ -101,7 +101,11 @@ typedef struct gxp_config {
     uint32_t check_bounds;      /* 1: kernels range-check every gathered index */
     uint32_t max_slots;         /* unused (serving takes gxp_serve_opts.max_slots); 0 */
     uint32_t pipeline_depth;    /* ring slots of the pipeline shuffle; 0 = 3 */
-    uint32_t reserved[7];
+    uint32_t keep_ids;          /* 0: a single-partition graph is renumbered internally by
+                                   decreasing in-degree, so the most gathered values share cache
+                                   lines (values, sources and labels are mapped back: results
+                                   are in input ids); 1: keep the input order */
+    uint32_t reserved[6];
 } gxp_config;
 
 /* Fill *cfg with the defaults above (all zero = defaults). */

@@ -90,6 +90,9 @@ void Engine::free_graph_device() {
     graph_bytes_ = 0;
     for (auto& hp : parts_)
         if (!hp.on_device) hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
+    work_.clear();
+    relabeled_ = false;
+    d_new2old_ = d_old2new_ = d_perm_tmp_ = nullptr;
     finalized_ = false;
     sell_ready_ = false;
     begun_ = false;
@@ -389,22 +392,25 @@ void Engine::build_sell() {
         const uint32_t n = hp.n_own;
         const uint64_t E = hp.n_edges();
         // 1. rows sorted by (source, weight); the sorted copy also serves the hub parts
-        uint32_t* d_w = hp.d_w;
+        const uint32_t* col_ptr = work_[p].col;
+        const uint32_t* src_w = work_[p].src;
+        const uint32_t* d_w = work_[p].w;
         if (weighted && !d_w) {
-            d_w = (uint32_t*)talloc(4 * E);
-            cuda_check(cudaMemcpyAsync(d_w, hp.w.data(), 4 * E, cudaMemcpyHostToDevice, stream_), "upload weights");
+            uint32_t* up = (uint32_t*)talloc(4 * E);
+            cuda_check(cudaMemcpyAsync(up, hp.w.data(), 4 * E, cudaMemcpyHostToDevice, stream_), "upload weights");
+            d_w = up;
         }
         uint32_t* ssrc = (uint32_t*)dalloc(4 * pad4(E));
         uint32_t* sw = weighted ? (uint32_t*)dalloc(4 * pad4(E)) : nullptr;
         uint2* big = (uint2*)talloc(8 * ((size_t)n + E / 2048 + 1));
         uint32_t* cnt = (uint32_t*)talloc(4);
-        cuda_check(launch_sort_rows(hp.d_col_ptr, n, hp.d_src, d_w, ssrc, sw, big, cnt, stream_), "sort rows");
+        cuda_check(launch_sort_rows(col_ptr, n, src_w, d_w, ssrc, sw, big, cnt, stream_), "sort rows");
         // 2. windows
         const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
         uint32_t* rows_out = (uint32_t*)talloc(4 * (size_t)n);
         uint32_t* hub_out = (uint32_t*)talloc(4 * (size_t)n);
         uint32_t* counts = (uint32_t*)talloc(8 * (size_t)nw + 8);   // non-hub counts, then hub counts
-        cuda_check(launch_sell_windows(hp.d_col_ptr, n, H, rows_out, hub_out, counts, counts + nw, stream_),
+        cuda_check(launch_sell_windows(col_ptr, n, H, rows_out, hub_out, counts, counts + nw, stream_),
                    "sort windows");
         std::vector<uint32_t> hc(2 * (size_t)nw + 2, 0);
         if (nw) d2h(hc.data(), counts, 8 * (size_t)nw);
@@ -425,7 +431,7 @@ void Engine::build_sell() {
         uint32_t* perm = (uint32_t*)dalloc(4 * pad4(ns * 32));
         uint32_t* width = (uint32_t*)talloc(4 * ns + 4);
         uint64_t* off = (uint64_t*)talloc(8 * ns + 8);
-        cuda_check(launch_sell_slices(hp.d_col_ptr, n, rows_out, counts, d_bases, perm, width, off, (uint32_t)ns,
+        cuda_check(launch_sell_slices(col_ptr, n, rows_out, counts, d_bases, perm, width, off, (uint32_t)ns,
                                       stream_), "slices");
         uint64_t sell_size = 0;
         d2h(&sell_size, off + ns, 8);
@@ -434,19 +440,19 @@ void Engine::build_sell() {
         uint32_t* sell_w = weighted ? (uint32_t*)dalloc(4 * pad4(sell_size)) : nullptr;
         part_desc[p] = (SellSlice*)talloc(sizeof(SellSlice) * (ns + 1));
         part_ns[p] = (uint32_t)ns;
-        cuda_check(launch_sell_fill(hp.d_col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, sell_src, sell_w,
+        cuda_check(launch_sell_fill(col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, sell_src, sell_w,
                                     part_desc[p], stream_), "fill slices");
         // 5. hub rows -> parts of T edges
         uint32_t* hub_list = (uint32_t*)talloc(4 * nh_rows + 4);
         uint32_t* part_off = (uint32_t*)talloc(4 * nh_rows + 4);
-        cuda_check(launch_hub_rows(hp.d_col_ptr, n, hub_out, counts + nw, d_bases + nw, hub_list, (uint32_t)nh_rows,
+        cuda_check(launch_hub_rows(col_ptr, n, hub_out, counts + nw, d_bases + nw, hub_list, (uint32_t)nh_rows,
                                    T, part_off, stream_), "hub rows");
         uint32_t nparts = 0;
         d2h(&nparts, part_off + nh_rows, 4);
         if ((uint64_t)total_hubs + nparts > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many hub parts");
         part_hubs[p] = (HubPart*)talloc(sizeof(HubPart) * ((size_t)nparts + 1));
         part_nh[p] = nparts;
-        cuda_check(launch_hub_parts(hp.d_col_ptr, hub_list, part_off, (uint32_t)nh_rows, T, p, total_hubs,
+        cuda_check(launch_hub_parts(col_ptr, hub_list, part_off, (uint32_t)nh_rows, T, p, total_hubs,
                                     part_hubs[p], stream_), "hub parts");
         pd_[p].sell_src = sell_src;
         pd_[p].sell_w = sell_w;
@@ -521,6 +527,44 @@ void Engine::finalize() {
                          (uint32_t)hp.ghost_gid.size(), hp.ghost_base, hp.n_edges(),
                          nullptr, nullptr, nullptr, nullptr, nullptr};
     }
+    // working CSC of each partition: the loaded one, or for a single partition
+    // (unless keep_ids) a copy renumbered by decreasing in-degree
+    work_.assign(n_parts_, WorkCsc{});
+    for (uint32_t p = 0; p < n_parts_; ++p) work_[p] = WorkCsc{parts_[p].d_col_ptr, parts_[p].d_src, parts_[p].d_w};
+    relabeled_ = false;
+    if (n_parts_ == 1 && !cfg_.keep_ids && V > 1) {
+        HostPart& hp = parts_[0];
+        const uint64_t E = hp.n_edges();
+        const uint32_t* dw = hp.d_w;
+        void* wtmp = nullptr;
+        if (hp.weighted() && !dw) {
+            cuda_check(cudaMalloc(&wtmp, 4 * std::max<uint64_t>(E, 1)), "cudaMalloc");
+            if (E) cuda_check(cudaMemcpyAsync(wtmp, hp.w.data(), 4 * E, cudaMemcpyHostToDevice, stream_), "upload");
+            dw = (const uint32_t*)wtmp;
+        }
+        d_new2old_ = (uint32_t*)dalloc(4 * pad4(V));
+        d_old2new_ = (uint32_t*)dalloc(4 * pad4(V));
+        d_perm_tmp_ = (uint32_t*)dalloc(4 * pad4(V));
+        uint32_t* rcol = (uint32_t*)dalloc(4 * pad4(V + 1));
+        uint32_t* rsrc = (uint32_t*)dalloc(4 * pad4(E));
+        uint32_t* rw = hp.weighted() ? (uint32_t*)dalloc(4 * pad4(E)) : nullptr;
+        cuda_check(cudaMemsetAsync(rcol, 0, 4 * pad4(V + 1), stream_), "memset");
+        cuda_check(cudaMemsetAsync(rsrc + E, 0, 4 * (pad4(E) - E), stream_), "memset");
+        void* scratch = nullptr;
+        cudaError_t e = cudaMalloc(&scratch, relabel_scratch_bytes(V));
+        if (e == cudaSuccess)
+            e = launch_relabel(hp.d_col_ptr, hp.d_src, dw, V, d_new2old_, d_old2new_, rcol, rsrc, rw,
+                               (uint32_t*)scratch, stream_);
+        cudaError_t e2 = cudaStreamSynchronize(stream_);
+        if (scratch) cudaFree(scratch);
+        if (wtmp) cudaFree(wtmp);
+        cuda_check(e, "relabel");
+        cuda_check(e2, "relabel");
+        work_[0] = WorkCsc{rcol, rsrc, rw};
+        pd_[0].col_ptr = rcol;
+        pd_[0].src = rsrc;
+        relabeled_ = true;
+    }
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
     cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
                "upload parts");
@@ -540,7 +584,7 @@ void Engine::finalize() {
     d_outdeg_ = (uint32_t*)dalloc(4 * pad4(V));
     cuda_check(cudaMemsetAsync(d_outdeg_, 0, 4 * pad4(V), stream_), "memset");
     for (uint32_t p = 0; p < n_parts_; ++p)
-        cuda_check(launch_outdeg(pd[p], parts_[p].d_src, d_ghost_gid_ + parts_[p].ghost_base, d_outdeg_, stream_),
+        cuda_check(launch_outdeg(pd[p], work_[p].src, d_ghost_gid_ + parts_[p].ghost_base, d_outdeg_, stream_),
                    "out-degrees");
 
     for (int b = 0; b < 2; ++b) {
@@ -639,8 +683,12 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     if (!sell_ready_) build_sell();
     const uint32_t V = (uint32_t)n_vertices_;
     cuda_check(cudaMemsetAsync(d_stats_, 0, sizeof(StepStats) * kStatRing, stream_), "memset");
-    const uint32_t ppr_source = personalized ? source : kInf;
-    cuda_check(launch_init_values(a, ppr_source, V, source, d_own_[0], d_rank_[0], d_outdeg_, d_stats_, stream_),
+    uint32_t src_int = source;   // the source in internal ids
+    if (relabeled_ && (a == Algo::SSSP || personalized))
+        cuda_check(cudaMemcpy(&src_int, d_old2new_ + source, 4, cudaMemcpyDeviceToHost), "map source");
+    const uint32_t ppr_source = personalized ? src_int : kInf;
+    cuda_check(launch_init_values(a, ppr_source, V, src_int, d_own_[0], d_rank_[0], d_outdeg_, d_stats_,
+                                  relabeled_ ? d_new2old_ : nullptr, stream_),
                "init values");
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
@@ -839,6 +887,11 @@ void Engine::get_values(uint32_t part, void* out, uint64_t n) {
     }
     if (n != cnt) fail(GXP_E_INVAL, "n must equal the number of vertices requested");
     const void* src = algo_ == Algo::PR ? (const void*)(d_rank_[cur_] + off) : (const void*)(d_own_[cur_] + off);
+    if (relabeled_) {   // internal order -> input ids
+        cuda_check(launch_permute_u32((const uint32_t*)src, d_old2new_, (uint32_t)cnt, d_perm_tmp_, false, stream_),
+                   "map values");
+        src = d_perm_tmp_;
+    }
     cuda_check(cudaMemcpyAsync(out, src, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
     cuda_check(cudaStreamSynchronize(stream_), "copy values");
     check_device_error();
@@ -856,7 +909,13 @@ void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
     }
     if (n != cnt) fail(GXP_E_INVAL, "n must equal the number of vertices given");
     account(false);
-    cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
+    if (relabeled_) {   // input ids -> internal order
+        cuda_check(cudaMemcpyAsync(d_perm_tmp_, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
+        cuda_check(launch_permute_u32(d_perm_tmp_, d_old2new_, (uint32_t)cnt, d_own_[cur_], true, stream_),
+                   "map values");
+    } else {
+        cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
+    }
     cuda_check(launch_init_ghosts(algo_, n_ghost_total_, d_ghost_gid_, d_own_[cur_], d_ghost_, stream_), "refresh caches");
     cuda_check(cudaStreamSynchronize(stream_), "set values");
 }

@@ -102,6 +102,16 @@ private:
     std::vector<HostPart> parts_;
     bool have_graph_ = false, finalized_ = false, sell_ready_ = false;
     std::vector<PartDev> pd_;   // host copy of the per-partition device views
+    struct WorkCsc {            // the CSC the layout build and out-degrees read
+        const uint32_t* col = nullptr;
+        const uint32_t* src = nullptr;
+        const uint32_t* w = nullptr;
+    };
+    std::vector<WorkCsc> work_;
+    bool relabeled_ = false;    // single partition renumbered by decreasing in-degree
+    uint32_t* d_new2old_ = nullptr;
+    uint32_t* d_old2new_ = nullptr;
+    uint32_t* d_perm_tmp_ = nullptr;
 
     // device graph-level buffers
     std::vector<void*> graph_allocs_;

@@ -138,13 +138,13 @@ __global__ void k_csc_import(const uint64_t* __restrict__ cp64, uint32_t n, uint
 
 
 __global__ void k_init_values(int algo, uint32_t ppr_source, uint32_t n, uint32_t source, uint32_t* own,
-                              float* rank, const uint32_t* outdeg, StepStats* st) {
+                              float* rank, const uint32_t* outdeg, StepStats* st, const uint32_t* label_of) {
     unsigned long long dang = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (algo == (int)Algo::SSSP) {
             own[v] = (v == source) ? 0u : kInf;
         } else if (algo == (int)Algo::CC) {
-            own[v] = v;
+            own[v] = label_of ? label_of[v] : v;   // CC labels are input ids
         } else {
             // PageRank: r_0 = 1/N everywhere; personalized PageRank: r_0 = e_source
             const float r0 = ppr_source == kInf ? (float)(1.0 / (double)n) : (v == ppr_source ? 1.0f : 0.0f);
@@ -322,10 +322,10 @@ cudaError_t launch_csc_import(const uint64_t* cp64, uint32_t n, uint64_t n_edges
 }
 
 cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n, uint32_t source, uint32_t* own, float* rank,
-                               const uint32_t* outdeg, StepStats* st, cudaStream_t s) {
+                               const uint32_t* outdeg, StepStats* st, const uint32_t* label_of, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 152u * 8);
-    k_init_values<<<blocks, 256, 0, s>>>((int)a, ppr_source, n, source, own, rank, outdeg, st);
+    k_init_values<<<blocks, 256, 0, s>>>((int)a, ppr_source, n, source, own, rank, outdeg, st, label_of);
     return cudaGetLastError();
 }
 

@@ -244,7 +244,7 @@ cudaError_t launch_validate_csc(const uint32_t* d_col_ptr, uint32_t n_own, const
 
 cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n_vertices, uint32_t source,
                                uint32_t* own_cur, float* rank_cur, const uint32_t* outdeg,
-                               StepStats* stats0, cudaStream_t s);
+                               StepStats* stats0, const uint32_t* label_of, cudaStream_t s);
 cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* ghost_gid_all,
                                const uint32_t* own_cur, uint32_t* ghost, cudaStream_t s);
 
@@ -280,6 +280,16 @@ cudaError_t launch_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, 
                              cudaStream_t s);
 cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, uint32_t* scratch, cudaStream_t s);
 size_t order_slices_scratch_bytes(uint32_t n);
+
+// vertex relabelling by decreasing in-degree (sell_build.cu): new2old / old2new,
+// and the CSC renumbered (rcol[n + 1], rsrc, rw); scratch: relabel_scratch_bytes
+size_t relabel_scratch_bytes(uint32_t n);
+cudaError_t launch_relabel(const uint32_t* col_ptr, const uint32_t* src, const uint32_t* w, uint32_t n,
+                           uint32_t* new2old, uint32_t* old2new, uint32_t* rcol, uint32_t* rsrc, uint32_t* rw,
+                           uint32_t* scratch, cudaStream_t s);
+// out[v] = in[map[v]] (gather) or out[map[v]] = in[v] (scatter)
+cudaError_t launch_permute_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out, bool scatter,
+                               cudaStream_t s);
 
 // serving (serve.cu): 64-slot personalized PageRank and slot management
 cudaError_t launch_ppr_superstep(const PprArgs& a, cudaStream_t s);

@@ -463,6 +463,142 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_order_scatter(const SellSli
         [&](uint32_t i, uint32_t pos) { out[pos] = in[i]; });
 }
 
+// ------------------------------------------------------ vertex relabelling
+// new id i = rank of the vertex in a stable order by decreasing in-degree, so
+// the most gathered values share cache lines (exact up to kExactBins, by
+// power of two above)
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_vdeg_count(const uint32_t* col_ptr, uint32_t n,
+                                                                uint32_t* ghist) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ uint32_t hist[kSortWarps][kBins];
+    for (uint32_t i = threadIdx.x; i < kSortWarps * kBins; i += blockDim.x) (&hist[0][0])[i] = 0u;
+    __syncthreads();
+    const uint32_t c0 = min(n, blockIdx.x * kSellWindow + warp * kSortChunk), c1 = min(n, c0 + kSortChunk);
+    for (uint32_t v = c0 + lane; v < c1; v += 32) atomicAdd(&hist[warp][deg_bin(col_ptr[v + 1] - col_ptr[v])], 1u);
+    __syncthreads();
+    uint32_t* g = ghist + (uint64_t)blockIdx.x * kSortWarps * kBins;
+    for (uint32_t i = threadIdx.x; i < kSortWarps * kBins; i += blockDim.x) g[i] = (&hist[0][0])[i];
+}
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_vdeg_scatter(const uint32_t* col_ptr, uint32_t n,
+                                                                  uint32_t* ghist, uint32_t* new2old) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t c0 = min(n, blockIdx.x * kSellWindow + warp * kSortChunk), c1 = min(n, c0 + kSortChunk);
+    uint32_t* offs = ghist + ((uint64_t)blockIdx.x * kSortWarps + warp) * kBins;
+    warp_scatter(
+        c0, c1, offs, [&](uint32_t v) { return deg_bin(col_ptr[v + 1] - col_ptr[v]); },
+        [&](uint32_t v, uint32_t pos) { new2old[pos] = v; });
+}
+
+// old2new = inverse of new2old; rdeg[i] = in-degree of new vertex i
+__global__ void k_invert(const uint32_t* col_ptr, const uint32_t* new2old, uint32_t n, uint32_t* old2new,
+                         uint32_t* rdeg) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = new2old[i];
+        old2new[v] = i;
+        rdeg[i] = col_ptr[v + 1] - col_ptr[v];
+    }
+}
+
+// three-phase exclusive scan of u32 counts: x[0..n) -> out[0..n], out[n] = total
+constexpr uint32_t kScanChunk = 2048;
+__global__ void __launch_bounds__(256) k_scan_sums(const uint32_t* x, uint32_t n, uint32_t* sums) {
+    __shared__ uint32_t red[8];
+    const uint32_t c0 = blockIdx.x * kScanChunk, c1 = min(n, c0 + kScanChunk);
+    uint32_t s = 0;
+    for (uint32_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) s += x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* sums, uint32_t m) {
+    __shared__ uint32_t part[1024];
+    const uint32_t t = threadIdx.x, per = (m + 1023) / 1024;
+    const uint32_t a = min(m, t * per), b = min(m, a + per);
+    uint32_t s = 0;
+    for (uint32_t i = a; i < b; ++i) s += sums[i];
+    part[t] = s;
+    __syncthreads();
+    for (uint32_t o = 1; o < 1024; o <<= 1) {
+        const uint32_t v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - s;
+    for (uint32_t i = a; i < b; ++i) {
+        const uint32_t c = sums[i];
+        sums[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* x, uint32_t n, const uint32_t* sums,
+                                                    uint32_t* out) {
+    __shared__ uint32_t warp_tot[8];
+    const uint32_t c0 = blockIdx.x * kScanChunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // thread t owns 8 consecutive elements of the chunk
+    constexpr uint32_t kPer = kScanChunk / 256;
+    const uint32_t base = c0 + threadIdx.x * kPer;
+    uint32_t v[kPer], s = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        v[k] = base + k < n ? x[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
+    uint32_t run = sums[blockIdx.x] + wbase + incl - s;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+        if (base + k + 1 == n) out[n] = run;
+    }
+}
+
+// one warp per new row: its old row's edges with sources renumbered
+__global__ void k_relabel_edges(const uint32_t* col_ptr, const uint32_t* src, const uint32_t* w,
+                                const uint32_t* new2old, const uint32_t* old2new, const uint32_t* rcol, uint32_t n,
+                                uint32_t* rsrc, uint32_t* rw) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp0; i < n; i += n_warps) {
+        const uint32_t v = new2old[i];
+        const uint32_t b = col_ptr[v], d = col_ptr[v + 1] - b, o = rcol[i];
+        for (uint32_t k = lane; k < d; k += 32) {
+            rsrc[o + k] = old2new[src[b + k]];
+            if (rw) rw[o + k] = w[b + k];
+        }
+    }
+}
+
+__global__ void k_gather_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) out[v] = in[map[v]];
+}
+
+__global__ void k_scatter_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) out[map[v]] = in[v];
+}
+
 uint32_t grid_warps(uint64_t warps, uint32_t block) {
     const uint64_t b = (warps * 32 + block - 1) / block;
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(b, 152ull * 64));
@@ -543,6 +679,46 @@ cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out,
 size_t order_slices_scratch_bytes(uint32_t n) {
     const uint64_t chunks = (n + kSellWindow - 1) / kSellWindow;
     return 4 * (size_t)(chunks + 1) * kSortWarps * kBins;
+}
+
+}  // namespace gxp
+
+namespace gxp {
+
+size_t relabel_scratch_bytes(uint32_t n) {
+    const uint64_t chunks = (n + kSellWindow - 1) / kSellWindow;
+    const uint64_t scan_blocks = (n + kScanChunk - 1) / kScanChunk;
+    return 4 * ((size_t)(chunks + 1) * kSortWarps * kBins + (size_t)scan_blocks + 1 + (size_t)n + 1);
+}
+
+cudaError_t launch_relabel(const uint32_t* col_ptr, const uint32_t* src, const uint32_t* w, uint32_t n,
+                           uint32_t* new2old, uint32_t* old2new, uint32_t* rcol, uint32_t* rsrc, uint32_t* rw,
+                           uint32_t* scratch, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t chunks = (n + kSellWindow - 1) / kSellWindow;
+    const uint32_t scan_blocks = (n + kScanChunk - 1) / kScanChunk;
+    uint32_t* ghist = scratch;
+    uint32_t* sums = ghist + (size_t)(chunks + 1) * kSortWarps * kBins;
+    uint32_t* rdeg = sums + scan_blocks + 1;
+    k_vdeg_count<<<chunks, kSortWarps * 32, 0, s>>>(col_ptr, n, ghist);
+    k_order_offsets<<<1, 1024, 0, s>>>(ghist, chunks * kSortWarps);
+    k_vdeg_scatter<<<chunks, kSortWarps * 32, 0, s>>>(col_ptr, n, ghist, new2old);
+    const uint32_t g = std::min<uint32_t>((n + 255) / 256, 152u * 16);
+    k_invert<<<g, 256, 0, s>>>(col_ptr, new2old, n, old2new, rdeg);
+    k_scan_sums<<<scan_blocks, 256, 0, s>>>(rdeg, n, sums);
+    k_scan_top<<<1, 1024, 0, s>>>(sums, scan_blocks);
+    k_scan_apply<<<scan_blocks, 256, 0, s>>>(rdeg, n, sums, rcol);
+    k_relabel_edges<<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, src, w, new2old, old2new, rcol, n, rsrc, rw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out, bool scatter,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t g = std::min<uint32_t>((n + 255) / 256, 152u * 16);
+    if (scatter) k_scatter_u32<<<g, 256, 0, s>>>(in, map, n, out);
+    else k_gather_u32<<<g, 256, 0, s>>>(in, map, n, out);
+    return cudaGetLastError();
 }
 
 }  // namespace gxp

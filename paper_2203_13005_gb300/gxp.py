@@ -43,7 +43,7 @@ GXP_QUERY_QUEUED, GXP_QUERY_RUNNING, GXP_QUERY_DONE, GXP_QUERY_FAILED = 0, 1, 2,
 class gxp_config(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("tile_items", C.c_uint32), ("hub_items", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("check_bounds", C.c_uint32), ("max_slots", C.c_uint32),
-                ("pipeline_depth", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+                ("pipeline_depth", C.c_uint32), ("keep_ids", C.c_uint32), ("reserved", C.c_uint32 * 6)]
 
 
 class gxp_stats(C.Structure):
@@ -164,11 +164,11 @@ class Context:
     """One gxp_ctx: a device, a partitioned graph and a running algorithm."""
 
     def __init__(self, device: int = 0, tile_items: int = 0, hub_items: int = 0,
-                 check_bounds: bool = False, timeout_ns: int = 0, mem_budget: int = 0):
+                 check_bounds: bool = False, timeout_ns: int = 0, mem_budget: int = 0, keep_ids: bool = False):
         self.lib = load()
         cfg = gxp_config()
         self.lib.gxp_config_default(C.byref(cfg))
-        cfg.tile_items, cfg.hub_items = tile_items, hub_items
+        cfg.tile_items, cfg.hub_items, cfg.keep_ids = tile_items, hub_items, int(keep_ids)
         cfg.check_bounds, cfg.timeout_ns, cfg.mem_budget = int(check_bounds), timeout_ns, mem_budget
         h = C.c_void_p()
         rc = self.lib.gxp_init(device, C.byref(cfg), C.byref(h))

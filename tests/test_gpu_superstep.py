@@ -350,6 +350,35 @@ def test_run_stops_at_first_quiet_superstep(parts):
         assert np.array_equal(c.values(), labels)
 
 
+def test_relabelled_and_input_order_agree():
+    """A single partition is renumbered by in-degree inside the engine unless
+    keep_ids is set; results come back in input ids either way."""
+    wl = synth.SSSP_RMAT16.scaled(12)
+    src, dst, w = wl.edges()
+    n = wl.n_vertices
+    d_ref, steps_ref, _ = oracle.sssp(n, src, dst, w, 3)
+    labels_ref, _, _ = oracle.cc(n, np.concatenate([src, dst]), np.concatenate([dst, src]))
+    r_ref, _, _ = oracle.pagerank(n, src, dst, 0.85, 20)
+    out = {}
+    for keep in (False, True):
+        with gxp.Context(0, keep_ids=keep) as c:
+            c.create_graph(n, 1)
+            c.load_coo(src, dst, w)
+            assert c.run(gxp.GXP_ALGO_SSSP, 3) == steps_ref
+            assert np.array_equal(c.values(), d_ref)
+            d_mid = c.values()
+            c.set_values(d_mid)                         # checkpoint round trip through the mapping
+            assert c.superstep() == 0 and np.array_equal(c.values(), d_ref)
+            c.run(gxp.GXP_ALGO_PAGERANK, max_steps=20)
+            out[keep] = c.values().copy()
+            _pr_check(out[keep], r_ref)
+        with gxp.Context(0, keep_ids=keep) as c:
+            c.create_graph(n, 1)
+            c.load_coo(np.concatenate([src, dst]), np.concatenate([dst, src]))
+            c.run(gxp.GXP_ALGO_CC)
+            assert np.array_equal(c.values(), labels_ref)
+
+
 def test_errors_are_status_codes():
     with _ctx(4) as c:
         with pytest.raises(gxp.GxpError) as ei:
