@@ -392,19 +392,12 @@ void Engine::build_sell() {
         const uint32_t n = hp.n_own;
         const uint64_t E = hp.n_edges();
         // 1. rows sorted by (source, weight); the sorted copy also serves the hub parts
-        const uint32_t* col_ptr = work_[p].col;
-        const uint32_t* src_w = work_[p].src;
-        const uint32_t* d_w = work_[p].w;
-        if (weighted && !d_w) {
-            uint32_t* up = (uint32_t*)talloc(4 * E);
-            cuda_check(cudaMemcpyAsync(up, hp.w.data(), 4 * E, cudaMemcpyHostToDevice, stream_), "upload weights");
-            d_w = up;
-        }
+        const uint32_t* col_ptr = work_[p].col;   // offsets of the rows the build writes
         uint32_t* ssrc = (uint32_t*)dalloc(4 * pad4(E));
         uint32_t* sw = weighted ? (uint32_t*)dalloc(4 * pad4(E)) : nullptr;
         uint2* big = (uint2*)talloc(8 * ((size_t)n + E / 2048 + 1));
         uint32_t* cnt = (uint32_t*)talloc(4);
-        cuda_check(launch_sort_rows(col_ptr, n, src_w, d_w, ssrc, sw, big, cnt, stream_), "sort rows");
+        cuda_check(launch_sort_rows(col_ptr, n, work_[p].in, ssrc, sw, big, cnt, stream_), "sort rows");
         // 2. windows
         const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
         uint32_t* rows_out = (uint32_t*)talloc(4 * (size_t)n);
@@ -527,42 +520,37 @@ void Engine::finalize() {
                          (uint32_t)hp.ghost_gid.size(), hp.ghost_base, hp.n_edges(),
                          nullptr, nullptr, nullptr, nullptr, nullptr};
     }
-    // working CSC of each partition: the loaded one, or for a single partition
-    // (unless keep_ids) a copy renumbered by decreasing in-degree
+    // what the layout build reads: each partition's CSC as loaded (weights on
+    // the device), and for a single partition (unless keep_ids) an order of
+    // its vertices by decreasing in-degree with the renumbered offsets; the
+    // row sort then reads old rows, renumbers their sources and writes new rows
     work_.assign(n_parts_, WorkCsc{});
-    for (uint32_t p = 0; p < n_parts_; ++p) work_[p] = WorkCsc{parts_[p].d_col_ptr, parts_[p].d_src, parts_[p].d_w};
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        HostPart& hp = parts_[p];
+        const uint32_t* dw = hp.d_w;
+        if (hp.weighted() && !dw) {
+            dw = upload_u32(hp.w, pad4(hp.w.size()));
+        }
+        work_[p] = WorkCsc{hp.d_col_ptr, RowSource{hp.d_col_ptr, hp.d_src, dw, nullptr, nullptr}};
+    }
     relabeled_ = false;
     if (n_parts_ == 1 && !cfg_.keep_ids && V > 1) {
         HostPart& hp = parts_[0];
-        const uint64_t E = hp.n_edges();
-        const uint32_t* dw = hp.d_w;
-        void* wtmp = nullptr;
-        if (hp.weighted() && !dw) {
-            cuda_check(cudaMalloc(&wtmp, 4 * std::max<uint64_t>(E, 1)), "cudaMalloc");
-            if (E) cuda_check(cudaMemcpyAsync(wtmp, hp.w.data(), 4 * E, cudaMemcpyHostToDevice, stream_), "upload");
-            dw = (const uint32_t*)wtmp;
-        }
         d_new2old_ = (uint32_t*)dalloc(4 * pad4(V));
         d_old2new_ = (uint32_t*)dalloc(4 * pad4(V));
         d_perm_tmp_ = (uint32_t*)dalloc(4 * pad4(V));
         uint32_t* rcol = (uint32_t*)dalloc(4 * pad4(V + 1));
-        uint32_t* rsrc = (uint32_t*)dalloc(4 * pad4(E));
-        uint32_t* rw = hp.weighted() ? (uint32_t*)dalloc(4 * pad4(E)) : nullptr;
         cuda_check(cudaMemsetAsync(rcol, 0, 4 * pad4(V + 1), stream_), "memset");
-        cuda_check(cudaMemsetAsync(rsrc + E, 0, 4 * (pad4(E) - E), stream_), "memset");
         void* scratch = nullptr;
         cudaError_t e = cudaMalloc(&scratch, relabel_scratch_bytes(V));
-        if (e == cudaSuccess)
-            e = launch_relabel(hp.d_col_ptr, hp.d_src, dw, V, d_new2old_, d_old2new_, rcol, rsrc, rw,
-                               (uint32_t*)scratch, stream_);
+        if (e == cudaSuccess) e = launch_relabel(hp.d_col_ptr, V, d_new2old_, d_old2new_, rcol, (uint32_t*)scratch, stream_);
         cudaError_t e2 = cudaStreamSynchronize(stream_);
         if (scratch) cudaFree(scratch);
-        if (wtmp) cudaFree(wtmp);
         cuda_check(e, "relabel");
         cuda_check(e2, "relabel");
-        work_[0] = WorkCsc{rcol, rsrc, rw};
-        pd_[0].col_ptr = rcol;
-        pd_[0].src = rsrc;
+        work_[0].col = rcol;
+        work_[0].in.row_map = d_new2old_;
+        work_[0].in.src_map = d_old2new_;
         relabeled_ = true;
     }
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
@@ -583,9 +571,13 @@ void Engine::finalize() {
     // vertex arrays are padded so 16-byte-aligned bulk copies of any slice stay inside
     d_outdeg_ = (uint32_t*)dalloc(4 * pad4(V));
     cuda_check(cudaMemsetAsync(d_outdeg_, 0, 4 * pad4(V), stream_), "memset");
+    uint32_t* outdeg_in = relabeled_ ? d_perm_tmp_ : d_outdeg_;   // input ids, then renumbered
+    if (relabeled_) cuda_check(cudaMemsetAsync(outdeg_in, 0, 4 * pad4(V), stream_), "memset");
     for (uint32_t p = 0; p < n_parts_; ++p)
-        cuda_check(launch_outdeg(pd[p], work_[p].src, d_ghost_gid_ + parts_[p].ghost_base, d_outdeg_, stream_),
+        cuda_check(launch_outdeg(pd[p], parts_[p].d_src, d_ghost_gid_ + parts_[p].ghost_base, outdeg_in, stream_),
                    "out-degrees");
+    if (relabeled_)
+        cuda_check(launch_permute_u32(outdeg_in, d_old2new_, V, d_outdeg_, true, stream_), "out-degrees");
 
     for (int b = 0; b < 2; ++b) {
         d_own_[b] = (uint32_t*)dalloc(4 * pad4(V));

@@ -102,10 +102,9 @@ private:
     std::vector<HostPart> parts_;
     bool have_graph_ = false, finalized_ = false, sell_ready_ = false;
     std::vector<PartDev> pd_;   // host copy of the per-partition device views
-    struct WorkCsc {            // the CSC the layout build and out-degrees read
-        const uint32_t* col = nullptr;
-        const uint32_t* src = nullptr;
-        const uint32_t* w = nullptr;
+    struct WorkCsc {            // what the layout build reads
+        const uint32_t* col = nullptr;   // offsets of the rows it writes
+        RowSource in{};                  // where each row's edges come from
     };
     std::vector<WorkCsc> work_;
     bool relabeled_ = false;    // single partition renumbered by decreasing in-degree

@@ -261,8 +261,18 @@ cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long
 uint32_t msssp_grid(uint64_t units);
 
 // sliced-ELL build on the device (sell_build.cu)
-cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t* src, const uint32_t* w,
-                             uint32_t* ssrc, uint32_t* sw, uint2* scratch_runs, uint32_t* scratch_cnt,
+// The CSC a build reads: row v of the result is input row row_map[v] (or v),
+// with its sources renumbered through src_map (or kept).
+struct RowSource {
+    const uint32_t* col_ptr;
+    const uint32_t* src;
+    const uint32_t* w;          // nullptr: unweighted
+    const uint32_t* row_map;    // nullptr: identity
+    const uint32_t* src_map;    // nullptr: identity
+};
+// rows of col_ptr (the result's offsets) sorted by (source, weight) into ssrc / sw
+cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const RowSource& in, uint32_t* ssrc, uint32_t* sw,
+                             uint2* scratch_runs, uint32_t* scratch_cnt,
                              cudaStream_t s);   // scratch_runs: n + n_edges / 2048 + 1 entries
 cudaError_t launch_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H, uint32_t* rows_out,
                                 uint32_t* hub_out, uint32_t* nonhub_cnt, uint32_t* hub_cnt, cudaStream_t s);
@@ -281,11 +291,10 @@ cudaError_t launch_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, 
 cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, uint32_t* scratch, cudaStream_t s);
 size_t order_slices_scratch_bytes(uint32_t n);
 
-// vertex relabelling by decreasing in-degree (sell_build.cu): new2old / old2new,
-// and the CSC renumbered (rcol[n + 1], rsrc, rw); scratch: relabel_scratch_bytes
+// vertex relabelling by decreasing in-degree (sell_build.cu): new2old / old2new
+// and the renumbered offsets rcol[n + 1]; scratch: relabel_scratch_bytes
 size_t relabel_scratch_bytes(uint32_t n);
-cudaError_t launch_relabel(const uint32_t* col_ptr, const uint32_t* src, const uint32_t* w, uint32_t n,
-                           uint32_t* new2old, uint32_t* old2new, uint32_t* rcol, uint32_t* rsrc, uint32_t* rw,
+cudaError_t launch_relabel(const uint32_t* col_ptr, uint32_t n, uint32_t* new2old, uint32_t* old2new, uint32_t* rcol,
                            uint32_t* scratch, cudaStream_t s);
 // out[v] = in[map[v]] (gather) or out[map[v]] = in[v] (scatter)
 cudaError_t launch_permute_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out, bool scatter,

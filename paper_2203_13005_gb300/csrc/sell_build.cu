@@ -89,14 +89,20 @@ __device__ __forceinline__ void warp_bitonic(T (&x)[kSlots], int lane, int n) {
 }
 
 template <int kSlots, bool kW>
-__device__ __forceinline__ void sort_row_in_warp(uint32_t b, uint32_t d, const uint32_t* src, const uint32_t* w,
-                                                 uint32_t* ssrc, uint32_t* sw, int lane) {
+__device__ __forceinline__ void sort_row_in_warp(uint32_t b, uint32_t ib, uint32_t d, const uint32_t* src,
+                                                 const uint32_t* w, const uint32_t* src_map, uint32_t* ssrc,
+                                                 uint32_t* sw, int lane) {
     using K = SortKey<kW>;
     typename K::T x[kSlots];
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
         const uint32_t i = s * 32 + lane;
-        x[s] = i < d ? K::make(src[b + i], w, b + i) : K::kMax;
+        if (i < d) {
+            const uint32_t u = src[ib + i];
+            x[s] = K::make(src_map ? src_map[u] : u, w, ib + i);
+        } else {
+            x[s] = K::kMax;
+        }
     }
     int np2 = 2;
     while (np2 < (int)d) np2 <<= 1;
@@ -114,17 +120,18 @@ __device__ __forceinline__ void sort_row_in_warp(uint32_t b, uint32_t d, const u
 // one warp per row: sorts rows of up to 256 edges, lists the runs of
 // kSortMax edges of longer rows ({row, first edge of the run}) for the block sort
 template <bool kW>
-__global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const uint32_t* src, const uint32_t* w,
-                                 uint32_t* ssrc, uint32_t* sw, uint2* big_runs, uint32_t* n_big) {
+__global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const RowSource in, uint32_t* ssrc,
+                                 uint32_t* sw, uint2* big_runs, uint32_t* n_big) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t v = warp0; v < n; v += n_warps) {
         const uint32_t b = col_ptr[v], d = col_ptr[v + 1] - b;
+        const uint32_t ib = in.col_ptr[in.row_map ? in.row_map[v] : (uint32_t)v];
         if (d <= 32) {
-            sort_row_in_warp<1, kW>(b, d, src, w, ssrc, sw, lane);
+            sort_row_in_warp<1, kW>(b, ib, d, in.src, in.w, in.src_map, ssrc, sw, lane);
         } else if (d <= 256) {
-            sort_row_in_warp<8, kW>(b, d, src, w, ssrc, sw, lane);
+            sort_row_in_warp<8, kW>(b, ib, d, in.src, in.w, in.src_map, ssrc, sw, lane);
         } else {
             const uint32_t runs = (d + kSortMax - 1) / kSortMax;
             uint32_t at = 0;
@@ -137,9 +144,8 @@ __global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const uint
 
 // one CTA per listed run (257 .. kSortMax edges): bitonic sort in shared memory
 template <bool kW>
-__global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr, const uint32_t* src,
-                                                         const uint32_t* w, uint32_t* ssrc, uint32_t* sw,
-                                                         const uint2* big_runs, const uint32_t* n_big) {
+__global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr, const RowSource in, uint32_t* ssrc,
+                                                         uint32_t* sw, const uint2* big_runs, const uint32_t* n_big) {
     using K = SortKey<kW>;
     __shared__ typename K::T x[kSortMax];
     const uint32_t cnt = *n_big;
@@ -147,10 +153,18 @@ __global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr
         const uint2 run = big_runs[r];
         const uint32_t b = col_ptr[run.x] + run.y;
         const uint32_t d = min(kSortMax, col_ptr[run.x + 1] - b);
+        const uint32_t ib = in.col_ptr[in.row_map ? in.row_map[run.x] : run.x] + run.y;
         uint32_t N = 32;
         while (N < d) N <<= 1;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) x[i] = i < d ? K::make(src[b + i], w, b + i) : K::kMax;
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+            if (i < d) {
+                const uint32_t u = in.src[ib + i];
+                x[i] = K::make(in.src_map ? in.src_map[u] : u, in.w, ib + i);
+            } else {
+                x[i] = K::kMax;
+            }
+        }
         __syncthreads();
         for (uint32_t k = 2; k <= N; k <<= 1)
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -574,23 +588,6 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* x, uint32_t 
     }
 }
 
-// one warp per new row: its old row's edges with sources renumbered
-__global__ void k_relabel_edges(const uint32_t* col_ptr, const uint32_t* src, const uint32_t* w,
-                                const uint32_t* new2old, const uint32_t* old2new, const uint32_t* rcol, uint32_t n,
-                                uint32_t* rsrc, uint32_t* rw) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t i = warp0; i < n; i += n_warps) {
-        const uint32_t v = new2old[i];
-        const uint32_t b = col_ptr[v], d = col_ptr[v + 1] - b, o = rcol[i];
-        for (uint32_t k = lane; k < d; k += 32) {
-            rsrc[o + k] = old2new[src[b + k]];
-            if (rw) rw[o + k] = w[b + k];
-        }
-    }
-}
-
 __global__ void k_gather_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) out[v] = in[map[v]];
 }
@@ -606,18 +603,17 @@ uint32_t grid_warps(uint64_t warps, uint32_t block) {
 
 }  // namespace
 
-cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t* src, const uint32_t* w,
-                             uint32_t* ssrc, uint32_t* sw, uint2* scratch_runs, uint32_t* scratch_cnt,
-                             cudaStream_t s) {
+cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const RowSource& in, uint32_t* ssrc, uint32_t* sw,
+                             uint2* scratch_runs, uint32_t* scratch_cnt, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(scratch_cnt, 0, 4, s);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    if (w) {
-        k_sort_rows_warp<true><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, src, w, ssrc, sw, scratch_runs, scratch_cnt);
-        k_sort_rows_block<true><<<152 * 8, 256, 0, s>>>(col_ptr, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+    if (in.w) {
+        k_sort_rows_warp<true><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, in, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_block<true><<<152 * 8, 256, 0, s>>>(col_ptr, in, ssrc, sw, scratch_runs, scratch_cnt);
     } else {
-        k_sort_rows_warp<false><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, src, w, ssrc, sw, scratch_runs, scratch_cnt);
-        k_sort_rows_block<false><<<152 * 8, 256, 0, s>>>(col_ptr, src, w, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_warp<false><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, in, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_block<false><<<152 * 8, 256, 0, s>>>(col_ptr, in, ssrc, sw, scratch_runs, scratch_cnt);
     }
     return cudaGetLastError();
 }
@@ -691,8 +687,7 @@ size_t relabel_scratch_bytes(uint32_t n) {
     return 4 * ((size_t)(chunks + 1) * kSortWarps * kBins + (size_t)scan_blocks + 1 + (size_t)n + 1);
 }
 
-cudaError_t launch_relabel(const uint32_t* col_ptr, const uint32_t* src, const uint32_t* w, uint32_t n,
-                           uint32_t* new2old, uint32_t* old2new, uint32_t* rcol, uint32_t* rsrc, uint32_t* rw,
+cudaError_t launch_relabel(const uint32_t* col_ptr, uint32_t n, uint32_t* new2old, uint32_t* old2new, uint32_t* rcol,
                            uint32_t* scratch, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint32_t chunks = (n + kSellWindow - 1) / kSellWindow;
@@ -708,7 +703,6 @@ cudaError_t launch_relabel(const uint32_t* col_ptr, const uint32_t* src, const u
     k_scan_sums<<<scan_blocks, 256, 0, s>>>(rdeg, n, sums);
     k_scan_top<<<1, 1024, 0, s>>>(sums, scan_blocks);
     k_scan_apply<<<scan_blocks, 256, 0, s>>>(rdeg, n, sums, rcol);
-    k_relabel_edges<<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, src, w, new2old, old2new, rcol, n, rsrc, rw);
     return cudaGetLastError();
 }
 
