@@ -602,33 +602,28 @@ void Engine::finalize() {
 // global-data-queue layout for the sync of Algorithm 3.
 void Engine::build_caches() {
     const uint32_t V = (uint32_t)n_vertices_;
-    std::vector<uint32_t> mptr((size_t)V + 1, 0);
-    for (auto& hp : parts_)
-        for (uint32_t g : hp.ghost_gid) mptr[(size_t)g + 1]++;
-    for (uint32_t v = 0; v < V; ++v) mptr[v + 1] += mptr[v];
-    std::vector<uint32_t> fill(mptr.begin(), mptr.end() - 1);
-    std::vector<uint32_t> midx(std::max<uint32_t>(mptr[V], 1));
-    for (auto& hp : parts_)
-        for (size_t s = 0; s < hp.ghost_gid.size(); ++s) midx[fill[hp.ghost_gid[s]]++] = hp.ghost_base + (uint32_t)s;
     const size_t words = ((size_t)V + 31) / 32 + 2;
+    // boundary vertices: cached by some other partition
     std::vector<uint32_t> bbits(words, 0);
+    for (auto& hp : parts_)
+        for (uint32_t g : hp.ghost_gid) bbits[g >> 5] |= 1u << (g & 31);
     uint64_t gdq_total = 0;
     max_words_ = 0;
     for (auto& hp : parts_) {
         hp.n_boundary = 0;
-        for (uint32_t v = hp.v_begin; v < hp.v_begin + hp.n_own; ++v)
-            if (mptr[v + 1] > mptr[v]) {
-                bbits[v >> 5] |= 1u << (v & 31);
-                hp.n_boundary++;
-            }
+        const uint32_t wl = hp.v_begin >> 5, wh = (hp.v_begin + hp.n_own + 31) >> 5;
+        for (uint32_t wi = wl; wi < wh; ++wi) {
+            uint32_t bits = bbits[wi];
+            const uint32_t base = wi * 32u;
+            if (base < hp.v_begin) bits &= ~0u << (hp.v_begin - base);
+            if (base + 32u > hp.v_begin + hp.n_own) bits &= (hp.v_begin + hp.n_own - base) >= 32u ? ~0u : ((1u << (hp.v_begin + hp.n_own - base)) - 1u);
+            hp.n_boundary += (uint32_t)__builtin_popcount(bits);
+        }
         hp.gdq_base = gdq_total;
         gdq_total += hp.n_boundary;
-        const uint32_t wl = hp.v_begin >> 5, wh = (hp.v_begin + hp.n_own + 31) >> 5;
         max_words_ = std::max(max_words_, hp.n_own ? wh - wl : 0u);
     }
     if (gdq_total > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "global data queue too large");
-    d_mirror_ptr_ = (uint32_t*)dalloc(4 * ((size_t)V + 1));
-    d_mirror_idx_ = (uint32_t*)dalloc(4 * midx.size());
     d_boundary_ = (uint32_t*)dalloc(4 * words);
     d_changed_ = (uint32_t*)dalloc(4 * words);
     d_gdq_ids_ = (uint32_t*)dalloc(4 * std::max<uint64_t>(gdq_total, 1));
@@ -641,8 +636,6 @@ void Engine::build_caches() {
     d_block_offsets_ = (uint32_t*)dalloc(4 * (size_t)n_parts_ * sync_blocks_x_);
     d_part_counts_ = (uint32_t*)dalloc(4 * n_parts_);
     d_done_ctr_ = (uint32_t*)dalloc(4);
-    cuda_check(cudaMemcpyAsync(d_mirror_ptr_, mptr.data(), 4 * mptr.size(), cudaMemcpyHostToDevice, stream_), "upload");
-    cuda_check(cudaMemcpyAsync(d_mirror_idx_, midx.data(), 4 * midx.size(), cudaMemcpyHostToDevice, stream_), "upload");
     cuda_check(cudaMemcpyAsync(d_boundary_, bbits.data(), 4 * words, cudaMemcpyHostToDevice, stream_), "upload");
     cuda_check(cudaMemcpyAsync(d_gdq_base_, gb.data(), 8 * n_parts_, cudaMemcpyHostToDevice, stream_), "upload");
     cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * words, stream_), "memset");
@@ -736,8 +729,8 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         s.changed_bits = d_changed_;
         s.boundary_bits = d_boundary_;
         s.own_val = d_own_[nx];
-        s.mirror_ptr = d_mirror_ptr_;
-        s.mirror_idx = d_mirror_idx_;
+        s.ghost_gid = d_ghost_gid_;
+        s.n_ghost = n_ghost_total_;
         s.ghost = d_ghost_;
         s.gdq_ids = d_gdq_ids_;
         s.gdq_vals = d_gdq_vals_;

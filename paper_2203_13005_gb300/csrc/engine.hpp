@@ -127,7 +127,6 @@ private:
     uint32_t* d_ghost_gid_ = nullptr;
     uint32_t n_ghost_total_ = 0;
     uint32_t *d_changed_ = nullptr, *d_boundary_ = nullptr;
-    uint32_t *d_mirror_ptr_ = nullptr, *d_mirror_idx_ = nullptr;
     uint32_t *d_gdq_ids_ = nullptr, *d_gdq_vals_ = nullptr;
     uint64_t* d_gdq_base_ = nullptr;
     uint32_t *d_block_counts_ = nullptr, *d_block_offsets_ = nullptr, *d_part_counts_ = nullptr;

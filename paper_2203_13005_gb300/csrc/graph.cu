@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_count(const SyncArgs a) {
     }
 }
 
-// Write each partition's global data queue (ascending ids) and update every
-// cached copy of the uploaded vertices.
+// Write each partition's global data queue (ascending ids): the changed
+// boundary vertices with their new values.
 __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
     __shared__ uint32_t s_warp[kSyncBlock / 32];
     if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
@@ -275,7 +275,18 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
         a.gdq_ids[pos] = gid;
         a.gdq_vals[pos] = val;
         ++pos;
-        for (uint32_t m = a.mirror_ptr[gid]; m < a.mirror_ptr[gid + 1]; ++m) a.ghost[a.mirror_idx[m]] = val;
+    }
+}
+
+// Caching (Section III-B): every cached copy of an uploaded vertex takes its
+// new value. Each partition's cache list is sorted by global id, so a thread
+// per cached copy reads the changed bits and the owners' values in
+// ascending order and writes the cache sequentially.
+__global__ void k_sync_pull(const SyncArgs a) {
+    if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_ghost; g += gridDim.x * blockDim.x) {
+        const uint32_t gid = a.ghost_gid[g];
+        if ((a.changed_bits[gid >> 5] >> (gid & 31u)) & 1u) a.ghost[g] = a.own_val[gid];
     }
 }
 
@@ -342,6 +353,8 @@ cudaError_t launch_sync(const SyncArgs& a, uint32_t, cudaStream_t s) {
     dim3 grid(a.blocks_x, a.n_parts);
     k_sync_count<<<grid, kSyncBlock, 0, s>>>(a);
     k_sync_write<<<grid, kSyncBlock, 0, s>>>(a);
+    if (a.n_ghost)
+        k_sync_pull<<<std::min<uint32_t>((a.n_ghost + 255) / 256, 152u * 16), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -214,9 +214,9 @@ struct SyncArgs {
     const uint32_t* changed_bits;
     const uint32_t* boundary_bits;
     const uint32_t* own_val;          // values after the superstep, [V]
-    const uint32_t* mirror_ptr;       // [V+1] CSR over owned vertices
-    const uint32_t* mirror_idx;       // flat ghost index of each cached copy
-    uint32_t* ghost;                  // [sum n_ghost] caches to update
+    const uint32_t* ghost_gid;        // [n_ghost] global id of each cached copy (sorted per partition)
+    uint32_t n_ghost;                 // cached copies over all partitions
+    uint32_t* ghost;                  // [n_ghost] caches to update
     uint32_t* gdq_ids;                // [sum of boundary counts]
     uint32_t* gdq_vals;
     const uint64_t* gdq_base;         // [n_parts] offset of each partition's gdq
