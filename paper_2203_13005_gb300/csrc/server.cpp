@@ -165,7 +165,7 @@ uint32_t Server::add_graph(uint64_t n, uint64_t m, const uint32_t* src_in, const
     auto G = std::make_unique<ServedGraph>();
     G->n = n;
     G->m = m;
-    G->weighted = w != nullptr;
+    G->weighted = w_in != nullptr;   // an edgeless graph given a (vacuous) weight array serves SSSP too
     G->n_units_all = all.size();
     G->n_units_nz = nz.size();
     G->n_split_rows = (uint32_t)(split.size() - 1);
