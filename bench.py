@@ -31,6 +31,8 @@ sys.path.insert(0, REPO)
 from paper_2203_13005_gb300 import synth  # noqa: E402
 
 METRIC = "GTEPS & % HBM roofline per GAS superstep"
+# superstep directions of the min-label runs (gxp_direction)
+DIRECTIONS = {"auto": 0, "pull": 1, "push": 2}
 ITERS = 20
 DAMPING = 0.85
 WL = synth.PAGERANK_RMAT22
@@ -216,19 +218,21 @@ def run_msssp(args):
 
 
 def run_sssp(args):
-    """SSSP (Bellman-Ford, min merge) on R-MAT scale 16 from source 0 to
-    convergence: supersteps are enqueued in chunks with one host read of
-    their changed counts per chunk (gxp_run). GTEPS = supersteps x edges /
-    run time; the roofline is taken per superstep kernel over a full sweep
-    (the whole 13 MB working set is L2-resident, so it is quoted against HBM
-    only for comparison)."""
+    """SSSP (Bellman-Ford, min merge) on R-MAT scale 16 (or 22) from source 0
+    to convergence: supersteps are enqueued in chunks with one host read of
+    their changed counts per chunk (gxp_run), each superstep pulling or
+    pushing as --direction says. GTEPS = supersteps x edges / run time; the
+    roofline is taken per pull superstep over a full sweep (at scale 16 the
+    whole 13 MB working set is L2-resident, so it is quoted against HBM only
+    for comparison)."""
     import torch
     from paper_2203_13005_gb300 import gxp
-    wl = synth.SSSP_RMAT16
+    wl = synth.SSSP_RMAT22 if args.workload == synth.SSSP_RMAT22.name else synth.SSSP_RMAT16
     src, dst, w = wl.edges()
     n, m = wl.n_vertices, wl.n_edges
     stream = torch.cuda.Stream()
-    ctx = gxp.Context(0)
+    direction = DIRECTIONS[args.direction]
+    ctx = gxp.Context(0, direction=direction, push_div=args.push_div)
     ctx.set_stream(stream.cuda_stream)
     ctx.create_graph(n, 1)
     ctx.load_coo(src, dst, w)
@@ -244,16 +248,29 @@ def run_sssp(args):
         t1.record(stream)
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / reps
-    # per-superstep kernel time: one run's supersteps, each bracketed by events
+    st = ctx.stats()
     g, mm, a = gxp.TEMPLATES[gxp.GXP_ALGO_SSSP]
-    ctx.begin(gxp.GXP_ALGO_SSSP, 0)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for b, e in evs:
-        b.record(stream)
-        ctx.lib.gxp_superstep(ctx.h, gxp.GXP_ALGO_SSSP, g, mm, a, None)
-        e.record(stream)
-    torch.cuda.synchronize()
-    k_us = statistics.mean(b.elapsed_time(e) for b, e in evs) * 1e3
+
+    def superstep_us(c):
+        # one run's supersteps, each bracketed by events on the context's stream
+        c.begin(gxp.GXP_ALGO_SSSP, 0)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for b, e in evs:
+            b.record(stream)
+            c.lib.gxp_superstep(c.h, gxp.GXP_ALGO_SSSP, g, mm, a, None)
+            e.record(stream)
+        torch.cuda.synchronize()
+        return [b.elapsed_time(e) * 1e3 for b, e in evs]
+
+    per_step_us = superstep_us(ctx)
+    # the pull kernel's roofline: every superstep in pull direction
+    cp = gxp.Context(0, direction=gxp.GXP_DIR_PULL)
+    cp.set_stream(stream.cuda_stream)
+    cp.create_graph(n, 1)
+    cp.load_coo(src, dst, w)
+    superstep_us(cp)
+    k_us = statistics.mean(superstep_us(cp))
+    cp.close()
     bytes_sweep = 12 * m + 12 * n + n // 4   # src + w + gathered value per edge; col_ptr, d read, d write, bitmap
     # end to end: COO from host memory -> load -> run -> distances back
     out = np.empty(n, dtype=np.uint32)
@@ -261,7 +278,7 @@ def run_sssp(args):
     for i in range(4):
         torch.cuda.synchronize()
         c0 = time.perf_counter()
-        c2 = gxp.Context(0)
+        c2 = gxp.Context(0, direction=direction, push_div=args.push_div)
         c2.create_graph(n, 1)
         c2.load_coo(src, dst, w)
         c2.run(gxp.GXP_ALGO_SSSP, 0)
@@ -278,7 +295,14 @@ def run_sssp(args):
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl.name, "vertices": n, "edges": m, "source": 0, "supersteps": steps,
                    "step": "one gxp_run to convergence (supersteps enqueued in chunks of 4, 8, 16)",
-                   "l2": "13 MB working set: L2-resident"},
+                   "value": "supersteps x edges / run time (the Jacobi sweeps the run stands for)",
+                   "l2": (f"{bytes_sweep / 1e6:.0f} MB working set: "
+                          + ("L2-resident" if bytes_sweep < 129e6 else "larger than L2")),
+                   "direction": args.direction,
+                   "push_div": args.push_div or 8, "push_supersteps": st["push_supersteps"],
+                   "edges_relaxed_per_run": st["edges_scanned"],
+                   "superstep_us": [round(x, 2) for x in per_step_us],
+                   "graph500_gteps": m / (ms * 1e-3) / 1e9},
         "roofline": {"bound": "hbm", "achieved": bytes_sweep / (k_us * 1e-6) / 1e9, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": bytes_sweep / (k_us * 1e-6) / 1e9 / peaks["hbm_gbs"], "traffic": None,
                      "peak_source": peaks["source"], "kernel": "k_sell<SSSP>", "avg_launch_us": k_us,
@@ -553,9 +577,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default=WL.name,
-                    choices=[WL.name, synth.SSSP_RMAT16.name, synth.MSSSP_RMAT24.name, synth.CC_ER24_P8.name,
+                    choices=[WL.name, synth.SSSP_RMAT16.name, synth.SSSP_RMAT22.name, synth.MSSSP_RMAT24.name,
+                             synth.CC_ER24_P8.name,
                              "serve"],
                     help="extra workloads print their own line; the default is the headline")
+    ap.add_argument("--direction", default="auto", choices=sorted(DIRECTIONS),
+                    help="sssp_rmat16: direction of the supersteps")
+    ap.add_argument("--push-div", type=int, default=0, help="sssp_rmat16: auto pushes while frontier work x div <= E")
     ap.add_argument("--serve-rate", type=float, default=synth.SERVE_RATE, help="serve: offered queries/s")
     ap.add_argument("--serve-seconds", type=float, default=synth.SERVE_SECONDS, help="serve: arrival window")
     ap.add_argument("--serve-drain", type=float, default=60.0, help="serve: seconds allowed after the window")
@@ -578,7 +606,7 @@ def main():
     if args.workload == synth.CC_ER24_P8.name:
         run_cc(args)
         return
-    if args.workload == synth.SSSP_RMAT16.name:
+    if args.workload in (synth.SSSP_RMAT16.name, synth.SSSP_RMAT22.name):
         run_sssp(args)
         return
     if args.workload == "serve":

@@ -105,8 +105,28 @@ typedef struct gxp_config {
                                    decreasing in-degree, so the most gathered values share cache
                                    lines (values, sources and labels are mapped back: results
                                    are in input ids); 1: keep the input order */
-    uint32_t reserved[6];
+    uint32_t direction;         /* gxp_direction of SSSP / CC supersteps on a single partition:
+                                   GXP_DIR_AUTO (0, default), GXP_DIR_PULL or GXP_DIR_PUSH.
+                                   Graphs of several partitions always pull. */
+    uint32_t push_div;          /* GXP_DIR_AUTO pushes a superstep when (frontier out-edges +
+                                   frontier items) * push_div <= the graph's edges; 0 = 8 */
+    uint32_t reserved[4];
 } gxp_config;
+
+/* Direction of the min-label supersteps (SSSP, CC). Both give the same values
+ * and the same changed sets after every superstep (Jacobi order):
+ *  - PULL: every destination merges all of its in-edges (dst-sorted layout);
+ *  - PUSH: only the out-edges of the vertices changed by the previous
+ *    superstep (the frontier) are relaxed, into the next values with atomic
+ *    min (src-sorted copy of the edges, built at the first gxp_begin that
+ *    needs it: 4 bytes per vertex + 4 or 8 bytes per edge);
+ *  - AUTO: per superstep on the device, push while the frontier's out-edges
+ *    are a small share of all edges (push_div), else pull. */
+typedef enum gxp_direction {
+    GXP_DIR_AUTO = 0,
+    GXP_DIR_PULL = 1,
+    GXP_DIR_PUSH = 2
+} gxp_direction;
 
 /* Fill *cfg with the defaults above (all zero = defaults). */
 GXP_API void gxp_config_default(gxp_config* cfg);
@@ -125,7 +145,8 @@ typedef struct gxp_stats {
     double   last_dangling;         /* PageRank: dangling mass D of the current ranks */
     double   last_superstep_ms;     /* device time of the last superstep incl. its sync */
     uint64_t device_bytes;          /* device memory held by the context */
-    uint64_t reserved[6];
+    uint64_t push_supersteps;       /* of the supersteps, those run in push direction */
+    uint64_t reserved[5];
 } gxp_stats;
 
 /* ------------------------------------------------------------ lifecycle -- */

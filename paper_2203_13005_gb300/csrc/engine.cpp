@@ -50,6 +50,8 @@ Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
     if (cfg_.timeout_ns == 0) cfg_.timeout_ns = 2000000000ull;
     if (cfg_.max_slots == 0) cfg_.max_slots = 64;
     if (cfg_.pipeline_depth == 0) cfg_.pipeline_depth = 3;
+    if (cfg_.push_div == 0) cfg_.push_div = 8;
+    if (cfg_.direction > GXP_DIR_PUSH) fail(GXP_E_INVAL, "direction must be GXP_DIR_AUTO, _PULL or _PUSH");
     if (cfg_.tile_items > (1u << 24) || cfg_.hub_items > (1u << 24))
         fail(GXP_E_INVAL, "tile_items and hub_items must not exceed 2^24");
     int n_dev = 0;
@@ -69,6 +71,8 @@ Engine::~Engine() {
     for (auto& hp : parts_) release_part(hp);
     if (ev_a_) cudaEventDestroy(ev_a_);
     if (ev_b_) cudaEventDestroy(ev_b_);
+    if (h_ctl_) cudaFreeHost(h_ctl_);
+    if (h_ring_) cudaFreeHost(h_ring_);
     if (own_stream_) cudaStreamDestroy(own_stream_);
 }
 
@@ -85,6 +89,12 @@ void* Engine::dalloc(size_t bytes) {
 
 void Engine::free_graph_device() {
     free_batch();   // graphs and pinned buffers that refer to the device buffers below
+    for (auto& g : run_graph_) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    d_ctl_ = nullptr;
+    h_old2new_.clear();
     for (void* p : graph_allocs_) cudaFree(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
@@ -93,6 +103,9 @@ void Engine::free_graph_device() {
     work_.clear();
     relabeled_ = false;
     d_new2old_ = d_old2new_ = d_perm_tmp_ = nullptr;
+    out_ready_ = frontier_ = false;
+    d_out_ptr_ = d_out_dst_ = d_out_w_ = nullptr;
+    d_list_[0] = d_list_[1] = nullptr;
     finalized_ = false;
     sell_ready_ = false;
     begun_ = false;
@@ -552,6 +565,9 @@ void Engine::finalize() {
         work_[0].in.row_map = d_new2old_;
         work_[0].in.src_map = d_old2new_;
         relabeled_ = true;
+        // host copy of the map: sources are renumbered without a device round trip
+        h_old2new_.resize(V);
+        cuda_check(cudaMemcpy(h_old2new_.data(), d_old2new_, 4ull * V, cudaMemcpyDeviceToHost), "relabel map");
     }
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
     cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
@@ -663,20 +679,32 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     const bool personalized = algo == GXP_ALGO_PPR;
     if ((a == Algo::SSSP || personalized) && source >= n_vertices_) fail(GXP_E_INVAL, "source out of range");
     if (a == Algo::PR && !(damping >= 0.0f && damping < 1.0f)) fail(GXP_E_INVAL, "damping must be in [0, 1)");
+    if (a != Algo::PR && n_parts_ > 1 && cfg_.direction == GXP_DIR_PUSH)
+        fail(GXP_E_UNSUPPORTED, "push direction is implemented for single-partition graphs");
     if (!finalized_) finalize();
     if (a == Algo::SSSP && !weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights on every partition");
     if (!sell_ready_) build_sell();
     const uint32_t V = (uint32_t)n_vertices_;
+    begun_ = false;   // until the state below is complete
     cuda_check(cudaMemsetAsync(d_stats_, 0, sizeof(StepStats) * kStatRing, stream_), "memset");
     uint32_t src_int = source;   // the source in internal ids
-    if (relabeled_ && (a == Algo::SSSP || personalized))
-        cuda_check(cudaMemcpy(&src_int, d_old2new_ + source, 4, cudaMemcpyDeviceToHost), "map source");
+    if (relabeled_ && (a == Algo::SSSP || personalized)) src_int = h_old2new_[source];
     const uint32_t ppr_source = personalized ? src_int : kInf;
     cuda_check(launch_init_values(a, ppr_source, V, src_int, d_own_[0], d_rank_[0], d_outdeg_, d_stats_,
                                   relabeled_ ? d_new2old_ : nullptr, stream_),
                "init values");
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
+    frontier_ = a != Algo::PR && n_parts_ == 1 && cfg_.direction != GXP_DIR_PULL;
+    if (frontier_) {
+        build_out_edges();
+        // both value buffers start equal: the push superstep lowers the next
+        // buffer in place, which must hold values no lower than the current
+        cuda_check(cudaMemcpyAsync(d_own_[1], d_own_[0], 4ull * V, cudaMemcpyDeviceToDevice, stream_), "copy values");
+        cur_ = 0;
+        step_ = 0;
+        seed_frontier(a == Algo::SSSP ? src_int : kInf);   // CC: every label is new
+    }
     algo_ = a;
     ppr_source_ = ppr_source;
     source_ = source;
@@ -685,6 +713,48 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     step_ = accounted_ = 0;
     st_ = gxp_stats{};
     begun_ = true;
+}
+
+// Launch arguments of the superstep kernel for superstep step_ (the kernel
+// derives the buffers and stat slots of superstep t from t).
+SellArgs Engine::sell_args() const {
+    SellArgs a{};
+    a.slices = d_slices_;
+    a.n_slices = n_slices_;
+    a.hubs = d_hubs_;
+    a.n_hubs = n_hubs_;
+    a.parts = d_parts_;
+    a.own[0] = d_own_[0];
+    a.own[1] = d_own_[1];
+    a.rank[0] = d_rank_[0];
+    a.rank[1] = d_rank_[1];
+    a.stats = d_stats_;
+    a.lists[0] = d_list_[0];
+    a.lists[1] = d_list_[1];
+    a.step = step_;
+    a.ghost = d_ghost_;
+    a.outdeg = d_outdeg_;
+    a.changed_bits = n_parts_ > 1 ? d_changed_ : nullptr;
+    a.hub_val = d_hub_val_;
+    a.hub_arrive = d_hub_arrive_;
+    a.err = d_err_;
+    a.check_bounds = cfg_.check_bounds;
+    a.damping = damping_;
+    a.inv_n = 1.0 / (double)n_vertices_;
+    a.ppr_source = ppr_source_;
+    a.early_exit = (early_exit_ && algo_ != Algo::PR) ? 1u : 0u;
+    if (frontier_) {   // the kernel picks the direction on the device from the frontier's size
+        a.fc.list_out = d_list_[1];   // non-null: lists on
+        a.fc.direction = cfg_.direction;
+        a.fc.push_div = cfg_.push_div;
+        a.fc.total_edges = total_edges_;
+        a.fc.list_cap = list_cap_;
+        a.fc.err = d_err_;
+        a.out_ptr = d_out_ptr_;
+        a.out_dst = d_out_dst_;
+        a.out_w = algo_ == Algo::SSSP ? d_out_w_ : nullptr;
+    }
+    return a;
 }
 
 uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply ap, bool want) {
@@ -696,30 +766,7 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
                     (algo_ == Algo::PR && g == GXP_GEN_CONTRIB && m == GXP_MERGE_SUM && ap == GXP_APPLY_PAGERANK);
     if (!ok) fail(GXP_E_UNSUPPORTED, "unsupported (msggen, merge, apply) template for this algorithm");
     const int nx = cur_ ^ 1;
-    SellArgs a{};
-    a.slices = d_slices_;
-    a.n_slices = n_slices_;
-    a.hubs = d_hubs_;
-    a.n_hubs = n_hubs_;
-    a.parts = d_parts_;
-    a.own_cur = d_own_[cur_];
-    a.own_nxt = d_own_[nx];
-    a.ghost = d_ghost_;
-    a.rank_cur = d_rank_[cur_];
-    a.rank_nxt = d_rank_[nx];
-    a.outdeg = d_outdeg_;
-    a.changed_bits = n_parts_ > 1 ? d_changed_ : nullptr;
-    a.hub_val = d_hub_val_;
-    a.hub_arrive = d_hub_arrive_;
-    a.stats_in = d_stats_ + (step_ % kStatRing);
-    a.stats_out = d_stats_ + ((step_ + 1) % kStatRing);
-    a.stats_clear = d_stats_ + ((step_ + 2) % kStatRing);
-    a.err = d_err_;
-    a.check_bounds = cfg_.check_bounds;
-    a.damping = damping_;
-    a.inv_n = 1.0 / (double)n_vertices_;
-    a.ppr_source = ppr_source_;
-    a.skip_if_quiet = (early_exit_ && step_ > 0 && algo_ != Algo::PR) ? 1u : 0u;
+    const SellArgs a = sell_args();
     cuda_check(cudaEventRecord(ev_a_, stream_), "event");
     cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
     if (n_parts_ > 1) {
@@ -740,7 +787,7 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         s.part_counts = d_part_counts_;
         s.done_ctr = d_done_ctr_;
         s.blocks_x = sync_blocks_x_;
-        s.stats_out = a.stats_out;
+        s.stats_out = d_stats_ + (step_ + 1) % kStatRing;
         cuda_check(launch_sync(s, max_words_, stream_), "sync kernels");
         cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)n_vertices_ + 31) / 32 + 2), stream_), "memset");
     }
@@ -757,13 +804,15 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
 // that changed nothing and roll the step counter back to it (the supersteps
 // enqueued after it ran on a fixed point and changed nothing either); its
 // index is returned, else 0.
-uint64_t Engine::account(bool stop_at_quiet) {
+uint64_t Engine::account(bool stop_at_quiet, bool ring_copied) {
     if (accounted_ == step_) return 0;
-    cuda_check(cudaStreamSynchronize(stream_), "superstep");
+    if (!ring_copied) {
+        cuda_check(cudaStreamSynchronize(stream_), "superstep");
+        ring_host_.resize(kStatRing);
+        cuda_check(cudaMemcpy(ring_host_.data(), d_stats_, sizeof(StepStats) * kStatRing, cudaMemcpyDeviceToHost),
+                   "read stats");
+    }
     check_device_error();
-    ring_host_.resize(kStatRing);
-    cuda_check(cudaMemcpy(ring_host_.data(), d_stats_, sizeof(StepStats) * kStatRing, cudaMemcpyDeviceToHost),
-               "read stats");
     uint64_t quiet = 0;
     for (uint64_t t = accounted_ + 1; t <= step_; ++t) {
         const StepStats& s = ring_host_[t % kStatRing];
@@ -774,7 +823,8 @@ uint64_t Engine::account(bool stop_at_quiet) {
             l1 += s.l1_fx[i];
         }
         st_.supersteps++;
-        st_.edges_scanned += total_edges_;
+        st_.edges_scanned += s.pushed ? s.push_edges : total_edges_;
+        if (s.pushed) st_.push_supersteps++;
         st_.last_changed = ch;
         if (algo_ == Algo::PR) {
             st_.last_dangling = fx_to_double(dg);
@@ -805,6 +855,41 @@ uint64_t Engine::account(bool stop_at_quiet) {
     return quiet;
 }
 
+// Out-edge copy for the push direction: offsets from the out-degrees and the
+// edges of the layout's CSC (renumbered like the layout), grouped by source.
+void Engine::build_out_edges() {
+    if (out_ready_) return;
+    const uint32_t V = (uint32_t)n_vertices_;
+    const uint64_t E = total_edges_;
+    d_out_ptr_ = (uint32_t*)dalloc(4 * pad4((size_t)V + 1));
+    d_out_dst_ = (uint32_t*)dalloc(4 * std::max<uint64_t>(E, 1));
+    d_out_w_ = weighted_ ? (uint32_t*)dalloc(4 * std::max<uint64_t>(E, 1)) : nullptr;
+    list_cap_ = (uint64_t)V + (E + kItemEdges - 1) / kItemEdges;
+    for (auto& l : d_list_) l = (uint2*)dalloc(sizeof(uint2) * std::max<uint64_t>(list_cap_, 1));
+    void* scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, 4 * out_edges_scratch_words(V));
+    if (e == cudaSuccess) {
+        uint32_t* cursor = (uint32_t*)scratch;
+        e = launch_out_edges(work_[0].in, V, d_outdeg_, d_out_ptr_, cursor, cursor + V + 1, d_out_dst_,
+                             weighted_ ? d_out_w_ : nullptr, stream_);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(stream_);
+    if (scratch) cudaFree(scratch);
+    cuda_check(e, "out-edges");
+    cuda_check(e2, "out-edges");
+    out_ready_ = true;
+}
+
+// The frontier the next superstep reads: one vertex, or all (kInf).
+void Engine::seed_frontier(uint32_t source_int) {
+    FrontierCfg f{};
+    f.list_out = d_list_[step_ & 1];
+    f.list_cap = list_cap_;
+    f.err = d_err_;
+    cuda_check(launch_seed_frontier((uint32_t)n_vertices_, source_int, d_out_ptr_, f, d_stats_ + (step_ % kStatRing),
+                                    stream_), "seed frontier");
+}
+
 void Engine::sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap, uint64_t* n_out, int* skipped) {
     if (!begun_ || step_ == 0) fail(GXP_E_STATE, "no superstep has run");
     if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
@@ -829,6 +914,56 @@ void Engine::sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap,
     cuda_check(cudaMemcpy(vals, d_gdq_vals_ + base, 4ull * n, cudaMemcpyDefault), "copy gdq values");
 }
 
+// The device-driven loop of the running min-label algorithm: a graph with
+// one WHILE node whose body is the superstep kernel (step read from d_ctl_)
+// followed by the control kernel that advances the step and sets the
+// condition. Built once per algorithm and graph; false if the driver cannot
+// build it (the run then drives the supersteps from the host).
+bool Engine::run_graph_ready() {
+    if (algo_ == Algo::PR || run_graph_failed_) return false;
+    cudaGraphExec_t& ge = run_graph_[algo_ == Algo::SSSP ? 0 : 1];
+    if (ge) return true;
+    if (!h_ctl_) cuda_check(cudaMallocHost(&h_ctl_, 2 * sizeof(RunCtl)), "pinned run control");
+    if (!h_ring_) cuda_check(cudaMallocHost(&h_ring_, sizeof(StepStats) * kStatRing), "pinned stats");
+    if (!d_ctl_) d_ctl_ = (RunCtl*)dalloc(sizeof(RunCtl));
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        SellArgs a = sell_args();
+        a.step_dev = &d_ctl_->step;
+        a.early_exit = 0u;   // the loop stops at the first quiet superstep
+        cudaError_t e1 = launch_superstep_sell(algo_, a, cs);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_run_control(d_ctl_, d_stats_, h, cs) : e1;
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(cs, &body);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ge) cudaGraphExecDestroy(ge);
+        ge = nullptr;
+        run_graph_failed_ = true;
+        return false;
+    }
+    return true;
+}
+
 uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max_steps) {
     begin(algo, source, damping);
     const gxp_msggen g = algo_ == Algo::SSSP ? GXP_GEN_RELAX : algo_ == Algo::CC ? GXP_GEN_LABEL : GXP_GEN_CONTRIB;
@@ -840,10 +975,41 @@ uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max
         account(false);
         return steps;
     }
-    // SSSP / CC: supersteps are enqueued in growing chunks and the host reads
-    // their changed counts once per chunk; the run ends at the first
-    // superstep that changed nothing (the count includes it)
-    // and the ones after a quiet superstep return at once on the device
+    // SSSP / CC on one partition: the loop runs on the device (a graph whose
+    // WHILE node repeats superstep + control until the first superstep that
+    // changes nothing, at most kRunChunk per launch); one host read per launch
+    if (n_parts_ == 1 && run_graph_ready()) {
+        const cudaGraphExec_t ge = run_graph_[algo_ == Algo::SSSP ? 0 : 1];
+        while (steps < max_steps) {
+            const uint32_t k = std::min<uint32_t>(kRunChunk, max_steps - steps);
+            h_ctl_[0] = RunCtl{step_, step_ + k, 1u, 0u};
+            cuda_check(cudaMemcpyAsync(d_ctl_, h_ctl_, sizeof(RunCtl), cudaMemcpyHostToDevice, stream_), "run control");
+            cuda_check(cudaEventRecord(ev_a_, stream_), "event");
+            cuda_check(cudaGraphLaunch(ge, stream_), "run graph");
+            cuda_check(cudaEventRecord(ev_b_, stream_), "event");
+            cuda_check(cudaMemcpyAsync(h_ctl_ + 1, d_ctl_, sizeof(RunCtl), cudaMemcpyDeviceToHost, stream_),
+                       "run control");
+            cuda_check(cudaMemcpyAsync(h_ring_, d_stats_, sizeof(StepStats) * kStatRing, cudaMemcpyDeviceToHost,
+                                       stream_), "read stats");
+            cuda_check(cudaStreamSynchronize(stream_), "run");
+            ring_host_.assign(h_ring_, h_ring_ + kStatRing);
+            const uint64_t done = h_ctl_[1].step;
+            if (done <= step_ || done > step_ + k) fail(GXP_E_CUDA, "device-driven run lost its step counter");
+            steps += (uint32_t)(done - step_);
+            step_ = done;
+            cur_ = (int)(step_ & 1u);
+            const uint64_t n_run = done - accounted_;
+            const uint64_t quiet = account(true, true);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) st_.last_superstep_ms = ms / (double)n_run;
+            if (quiet) return (uint32_t)quiet;
+        }
+        return steps;
+    }
+    // partitioned graphs: supersteps are enqueued in growing chunks and the
+    // host reads their changed counts once per chunk; the run ends at the
+    // first superstep that changed nothing (the count includes it) and the
+    // ones after a quiet superstep return at once on the device
     uint32_t chunk = 4;
     struct EarlyExit {
         bool& f;
@@ -902,6 +1068,11 @@ void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
         cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
     }
     cuda_check(launch_init_ghosts(algo_, n_ghost_total_, d_ghost_gid_, d_own_[cur_], d_ghost_, stream_), "refresh caches");
+    if (frontier_) {   // any value may have moved: every vertex is in the next frontier
+        cuda_check(cudaMemcpyAsync(d_own_[cur_ ^ 1], d_own_[cur_], 4ull * n_vertices_, cudaMemcpyDeviceToDevice,
+                                   stream_), "copy values");
+        seed_frontier(kInf);
+    }
     cuda_check(cudaStreamSynchronize(stream_), "set values");
 }
 

@@ -77,7 +77,8 @@ private:
     void build_sell();
     void build_caches();
     uint32_t* upload_u32(const std::vector<uint32_t>& h, size_t n_pad);
-    uint64_t account(bool stop_at_quiet);
+    // ring_copied: ring_host_ already holds the device ring (stream synchronized)
+    uint64_t account(bool stop_at_quiet, bool ring_copied = false);
     std::vector<StepStats> ring_host_;
     void check_device_error();
     void copy_in(void* dst, const void* src, size_t bytes);   // host or device src -> host dst
@@ -165,6 +166,27 @@ private:
     Algo algo_ = Algo::SSSP;
     uint32_t source_ = 0;
     uint32_t ppr_source_ = kInf;   // personalized PageRank: its source; else kInf
+    // push direction (min-label algorithms, one partition): out-edge copy and
+    // the two frontier lists (superstep t reads list t & 1, writes the other)
+    bool frontier_ = false;        // the running algorithm keeps frontier lists
+    bool out_ready_ = false;
+    uint32_t* d_out_ptr_ = nullptr;
+    uint32_t* d_out_dst_ = nullptr;
+    uint32_t* d_out_w_ = nullptr;
+    uint2* d_list_[2] = {nullptr, nullptr};
+    uint64_t list_cap_ = 0;
+    void build_out_edges();
+    void seed_frontier(uint32_t source_int);
+    // device-driven runs (min-label algorithms, one partition)
+    static constexpr uint32_t kRunChunk = 32;   // supersteps per graph launch (the stat ring holds 64)
+    cudaGraphExec_t run_graph_[2] = {nullptr, nullptr};   // SSSP, CC
+    bool run_graph_failed_ = false;
+    RunCtl* d_ctl_ = nullptr;
+    RunCtl* h_ctl_ = nullptr;      // pinned: [0] to the device, [1] back
+    StepStats* h_ring_ = nullptr;  // pinned copy of the stat ring
+    std::vector<uint32_t> h_old2new_;   // host copy of the renumbering (source ids)
+    bool run_graph_ready();
+    SellArgs sell_args() const;
     bool early_exit_ = false;      // inside gxp_run: supersteps after a quiet one return at once
     bool auto_tiles_ = false;      // tile / hub sizes chosen from the graph's size
     float damping_ = 0.85f;

@@ -100,8 +100,36 @@ struct StepStats {
     unsigned long long l1_fx[kStatLanes];         // sum |fx(r_new) - fx(r_old)|
     unsigned long long boundary_changed;          // pairs uploaded by the sync (all partitions)
     unsigned long long skipped;                   // 1 if the exchange was skipped
-    unsigned long long pad[6];
+    // frontier of the next superstep (min-label algorithms, single partition):
+    // items appended to its list (high 32 bits) and the out-edges of the
+    // vertices they cover (low 32 bits), advanced together by one atomic
+    unsigned long long list_ne;
+    unsigned long long pushed;                    // 1: the superstep ran in push direction,
+    unsigned long long push_edges;                //    relaxing this many out-edges
+    unsigned long long pad[3];
 };
+__host__ __device__ constexpr unsigned long long list_pack(uint32_t items, uint32_t edges) {
+    return ((unsigned long long)items << 32) | edges;
+}
+
+// Frontier lists: the vertices changed by a superstep, as work items of at
+// most kItemEdges out-edges each ({vertex, chunk}: out-edges [32 chunk,
+// 32 chunk + 32) of the vertex; a vertex without out-edges has one empty
+// item). Per list: at most n_vertices + ceil(n_edges / 32) items (below
+// 2^32, or the lists are not used); the out-edges of one list are at most
+// n_edges < 2^32, so the packed counter's halves never carry into each other.
+constexpr uint32_t kItemEdges = 32;
+struct FrontierCfg {
+    const uint2* list_in;        // this superstep's frontier (count: stats_in->list_ne >> 32)
+    uint2* list_out;             // the next one; nullptr = no frontier lists (pull only)
+    uint32_t direction;          // gxp_direction
+    uint32_t push_div;
+    uint64_t total_edges;
+    uint64_t list_cap;           // items each list holds
+    uint32_t* err;               // kErrBounds if a list would overflow (never, for valid graphs)
+};
+
+
 
 // Everything the superstep kernel touches.
 struct SuperstepArgs {
@@ -137,24 +165,33 @@ struct SellArgs {
     const HubPart* hubs;
     uint32_t n_hubs;
     const PartDev* parts;
-    const uint32_t* own_cur;
-    uint32_t* own_nxt;
+    // superstep t reads value buffer t & 1, stat slot t % kStatRing and
+    // frontier list t & 1; it writes buffer / list (t + 1) & 1 and slot t + 1,
+    // and clears slot t + 2
+    uint32_t* own[2];
+    float* rank[2];
+    StepStats* stats;            // [kStatRing]
+    uint2* lists[2];             // frontier lists (min-label algorithms, one partition) or nullptr
+    uint64_t step;               // t, unless
+    const uint64_t* step_dev;    // t lives in device memory (device-driven runs)
     const uint32_t* ghost;
-    const float* rank_cur;
-    float* rank_nxt;
     const uint32_t* outdeg;
     uint32_t* changed_bits;
     uint32_t* hub_val;           // [n_hubs] published partials (value bits)
     uint32_t* hub_arrive;        // [n_hubs] arrival counters, indexed by a row's first part
-    StepStats* stats_in;
-    StepStats* stats_out;
-    StepStats* stats_clear;
     uint32_t* err;
     uint32_t check_bounds;
     float damping;
     double inv_n;
     uint32_t ppr_source;         // PageRank: kInf; personalized PageRank: the source vertex
-    uint32_t skip_if_quiet;      // 1: return at once if the previous superstep changed nothing
+    uint32_t early_exit;         // 1: a superstep (t > 0) after a quiet one returns at once
+    // SSSP / CC on one partition: fc.list_out != nullptr turns the frontier
+    // lists on (the kernel points list_in / list_out at lists[]); the
+    // out-edge copy is what the push direction reads
+    FrontierCfg fc;
+    const uint32_t* out_ptr;     // [V + 1] out-edge offsets, internal ids
+    const uint32_t* out_dst;     // [E] destinations, grouped by source
+    const uint32_t* out_w;       // [E] weights, or nullptr (CC)
 };
 
 // Arguments of the batched multi-source SSSP superstep kernel (one edge block).
@@ -250,9 +287,36 @@ cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* g
 
 cudaError_t launch_superstep(Algo a, const SuperstepArgs& args, size_t smem_bytes, cudaStream_t s);
 cudaError_t launch_superstep_sell(Algo a, const SellArgs& args, cudaStream_t s);
+
+// Device-driven run: the step counter the superstep kernel reads
+// (SellArgs::step_dev) and the loop's bounds.
+struct RunCtl {
+    uint64_t step;          // supersteps done
+    uint64_t limit;         // the loop stops when step reaches it
+    uint32_t quiet_stop;    // 1: also stop after a superstep that changed nothing
+    uint32_t pad;
+};
+cudaError_t launch_run_control(RunCtl* ctl, const StepStats* ring, cudaGraphConditionalHandle h, cudaStream_t s);
 size_t superstep_smem_bytes(Algo a, uint32_t max_items);
 
 cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);
+
+// push direction (frontier.cu)
+struct RowSource;
+// out-edge copy of the CSC `in` (rows renumbered as the layout build does):
+// out_ptr = exclusive scan of outdeg (internal ids); cursor: n scratch words
+cudaError_t launch_out_edges(const RowSource& in, uint32_t n, const uint32_t* outdeg, uint32_t* out_ptr,
+                             uint32_t* cursor, uint32_t* scan_scratch, uint32_t* out_dst, uint32_t* out_w,
+                             cudaStream_t s);
+size_t out_edges_scratch_words(uint32_t n);
+// f.list_out <- items of vertex `source` (all vertices when source == kInf);
+// the counts go to stats->list_ne (zeroed here first)
+cudaError_t launch_seed_frontier(uint32_t n, uint32_t source, const uint32_t* out_ptr, const FrontierCfg& f,
+                                 StepStats* stats, cudaStream_t s);
+// exclusive scan of n u32 counts into out[0..n] (out[n] = total); scratch:
+// (n + 2047) / 2048 + 1 words (sell_build.cu)
+cudaError_t launch_exclusive_scan_u32(const uint32_t* x, uint32_t n, uint32_t* out, uint32_t* scratch,
+                                      cudaStream_t s);
 
 cudaError_t launch_msssp(const MsArgs& a, bool dry, uint32_t grid, cudaStream_t s);
 cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_t* sources, uint32_t n_sources,

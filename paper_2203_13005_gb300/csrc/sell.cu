@@ -1,5 +1,8 @@
 // Superstep kernel over the sliced-ELL layout: MSGGen + MSGMerge + MSGApply
 // (Section IV-A1's algorithm template) in pull form, one warp per work item.
+// For SSSP and CC on one partition the same grid runs the push direction
+// instead when the frontier is small (frontier.cuh); the choice is made on
+// the device from the previous superstep's frontier size.
 //
 //  * slice of 32 non-hub rows (the edge block of Section II-B, laid out
 //    column-major): lane i owns row i. For each of the slice's `width` edge
@@ -16,7 +19,9 @@
 //
 // Sums run in a fixed order, so fp32 PageRank is deterministic; PageRank's
 // global sums (dangling mass, L1 delta) are exact 64-bit fixed point.
-#include "gxp_internal.hpp"
+#include "frontier.cuh"
+
+#include <algorithm>
 
 namespace gxp {
 namespace {
@@ -87,16 +92,29 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
     constexpr int kU = Op::kUnroll;
     __shared__ unsigned long long s_acc[3];
     __shared__ uint32_t s_done;
+    __shared__ uint32_t s_ftot[kSellWarps], s_fedges[kSellWarps];   // frontier items, out-edges per warp
+    __shared__ unsigned long long s_fbase;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (blockIdx.x == 0 && a.stats_clear != nullptr) {
+    // superstep t reads value buffer t & 1 and stat slot t, writes the others
+    const uint64_t t = a.step_dev ? *a.step_dev : a.step;
+    const uint32_t* const own_cur = a.own[t & 1];
+    uint32_t* const own_nxt = a.own[(t + 1) & 1];
+    const float* const rank_cur = a.rank[t & 1];
+    float* const rank_nxt = a.rank[(t + 1) & 1];
+    const StepStats* const stats_in = a.stats + t % kStatRing;
+    StepStats* const stats_out = a.stats + (t + 1) % kStatRing;
+    FrontierCfg fc = a.fc;
+    fc.list_in = a.lists[t & 1];
+    if (fc.list_out) fc.list_out = a.lists[(t + 1) & 1];
+    if (blockIdx.x == 0) {
         // zero the ring slot two supersteps ahead (never read or written by this one)
-        unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats_clear);
+        unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats + (t + 2) % kStatRing);
         for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
     }
-    if (a.skip_if_quiet) {
+    if (a.early_exit && t > 0) {
         // min-label algorithms at a fixed point: nothing can change any more
-        unsigned long long c = a.stats_in->changed[lane] + a.stats_in->changed[lane + 32];
+        unsigned long long c = stats_in->changed[lane] + stats_in->changed[lane + 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
         if (c == 0ull) return;   // same for every thread of the grid
@@ -110,7 +128,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         // from the exact dangling-mass sum D of the current ranks: PageRank
         // spreads (1-d) + d*D evenly, (1-d)/N + d*D/N to every vertex;
         // personalized PageRank returns all of it to the source vertex
-        unsigned long long sd = a.stats_in->dangling_fx[lane] + a.stats_in->dangling_fx[lane + 32];
+        unsigned long long sd = stats_in->dangling_fx[lane] + stats_in->dangling_fx[lane + 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
         const double d = (double)a.damping;
@@ -131,21 +149,21 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         const uint32_t gid = P.v_begin + v;
         if constexpr (A == Algo::PR) {
             const float rn = fmaf(damping, m, gid == a.ppr_source ? base_src : base);
-            const float ro = a.rank_cur[gid];
+            const float ro = rank_cur[gid];
             const uint32_t od = a.outdeg[gid];
-            a.rank_nxt[gid] = rn;
+            rank_nxt[gid] = rn;
             const float c = od ? __fdiv_rn(rn, (float)od) : 0.0f;
             const uint32_t cb = __float_as_uint(c);
-            a.own_nxt[gid] = cb;
+            own_nxt[gid] = cb;
             const unsigned long long fn = fx_of(rn), fo = fx_of(ro);
             l1 += fn > fo ? fn - fo : fo - fn;
             if (od == 0u) dang += fn;
             // message changes are tracked only when a bitmap is wanted (partitions)
-            return a.changed_bits != nullptr && cb != a.own_cur[gid];
+            return a.changed_bits != nullptr && cb != own_cur[gid];
         } else {
-            const uint32_t old = a.own_cur[gid];
+            const uint32_t old = own_cur[gid];
             const uint32_t nw = min(old, (uint32_t)m);
-            a.own_nxt[gid] = nw;
+            own_nxt[gid] = nw;
             return nw != old;
         }
     };
@@ -157,11 +175,25 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
             ok = false;
             return 0u;
         }
-        return __ldg(u < P.n_own ? a.own_cur + P.v_begin + u : a.ghost + P.ghost_base + (u - P.n_own));
+        return __ldg(u < P.n_own ? own_cur + P.v_begin + u : a.ghost + P.ghost_base + (u - P.n_own));
     };
 
     const uint32_t gw = blockIdx.x * kSellWarps + (uint32_t)warp;
-    if (gw < a.n_hubs) {
+    bool f_has = false;   // pull direction with frontier lists: this lane's changed vertex
+    uint32_t f_v = 0;
+    bool pushed = false;
+    if constexpr (A != Algo::PR) {
+        if (push_chosen(fc, stats_in)) {   // same choice in every thread of the grid
+            const uint32_t c = push_superstep<Op::kWeighted>(fc, a.out_ptr, a.out_dst, a.out_w, own_cur,
+                                                             own_nxt, stats_in, stats_out, gw,
+                                                             (uint64_t)gridDim.x * kSellWarps, lane);
+            if (lane == 0) n_changed += c;
+            pushed = true;
+        }
+    }
+    if (pushed) {
+        // the frontier's out-edges were relaxed above
+    } else if (gw < a.n_hubs) {
         // ============================================================ hub part
         const HubPart hp = a.hubs[gw];
         const PartDev P = a.parts[hp.part];
@@ -206,11 +238,18 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
                 do_apply = true;
             }
         }
-        if (do_apply && lane == 0 && apply(P, hp.v, total)) {
+        const bool ch = do_apply && lane == 0 && apply(P, hp.v, total);
+        if (ch) {
             ++n_changed;
             if (a.changed_bits) {
                 const uint32_t g = P.v_begin + hp.v;
                 atomicOr(&a.changed_bits[g >> 5], 1u << (g & 31u));
+            }
+        }
+        if constexpr (A != Algo::PR) {
+            if (ch && fc.list_out) {   // the vertex joins the next frontier
+                f_has = true;
+                f_v = P.v_begin + hp.v;
             }
         }
     } else if (gw - a.n_hubs < a.n_slices) {
@@ -242,12 +281,48 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         const bool ch = row != kSellPad && apply(P, row, acc);
         const unsigned chm = __ballot_sync(kFull, ch);
         if (lane == 0) n_changed += __popc(chm);
+        if constexpr (A != Algo::PR) {
+            if (ch && fc.list_out) {
+                f_has = true;
+                f_v = P.v_begin + row;
+            }
+        }
         if (ch && a.changed_bits) {
             // one atomic per bitmap word touched by this warp
             const uint32_t g = P.v_begin + row;
             const unsigned grp = __match_any_sync(chm, g >> 5);
             const unsigned bits = __reduce_or_sync(grp, 1u << (g & 31u));
             if ((uint32_t)lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(&a.changed_bits[g >> 5], bits);
+        }
+    }
+
+    if constexpr (A != Algo::PR) {
+        if (fc.list_out && !pushed) {   // uniform over the grid
+            // the changed vertices join the next frontier: one atomic per CTA
+            // reserves the CTA's items, each warp writes its own
+            const uint32_t deg = f_has ? __ldg(a.outdeg + f_v) : 0u;
+            const uint32_t nit = f_has ? frontier_items(deg) : 0u;
+            const uint32_t incl = warp_inclusive_scan(nit, lane);
+            uint32_t edges = deg;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) edges += __shfl_xor_sync(kFull, edges, o);
+            if (lane == 31) {
+                s_ftot[warp] = incl;
+                s_fedges[warp] = edges;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t items = 0, e = 0;
+                for (int w = 0; w < kSellWarps; ++w) {
+                    const uint32_t t = s_ftot[w];
+                    s_ftot[w] = items;   // -> the warp's offset in the CTA's range
+                    items += t;
+                    e += s_fedges[w];
+                }
+                s_fbase = items ? atomicAdd(&stats_out->list_ne, list_pack(items, e)) >> 32 : 0ull;
+            }
+            __syncthreads();
+            if (__shfl_sync(kFull, incl, 31)) frontier_write(fc, s_fbase + s_ftot[warp], incl, nit, f_v, lane);
         }
     }
 
@@ -271,23 +346,49 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
             const unsigned long long x0 = atomicAdd(&s_acc[0], 0ull), x1 = atomicAdd(&s_acc[1], 0ull),
                                      x2 = atomicAdd(&s_acc[2], 0ull);
             const uint32_t ln = blockIdx.x % kStatLanes;
-            if (x0) atomicAdd(&a.stats_out->changed[ln], x0);
-            if (x1) atomicAdd(&a.stats_out->l1_fx[ln], x1);
-            if (x2) atomicAdd(&a.stats_out->dangling_fx[ln], x2);
+            if (x0) atomicAdd(&stats_out->changed[ln], x0);
+            if (x1) atomicAdd(&stats_out->l1_fx[ln], x1);
+            if (x2) atomicAdd(&stats_out->dangling_fx[ln], x2);
         }
     }
 }
 
 }  // namespace
 
+namespace {
+
+// Iteration control of a device-driven run (the body of a graph's WHILE
+// node, after each superstep): advance the step, and continue while the
+// step limit is not reached and, for the min-label algorithms, the superstep
+// changed something. The limit alone ends the loop, whatever the supersteps
+// compute.
+__global__ void __launch_bounds__(32) k_run_control(RunCtl* ctl, const StepStats* ring,
+                                                    cudaGraphConditionalHandle h) {
+    const int lane = threadIdx.x;
+    const uint64_t t = ctl->step + 1;   // supersteps done; slot t holds the last one's counts
+    const StepStats& st = ring[t % kStatRing];
+    unsigned long long c = st.changed[lane] + st.changed[lane + 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if (lane == 0) {
+        ctl->step = t;
+        const bool more = t < ctl->limit && (ctl->quiet_stop == 0u || c != 0ull);
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_run_control(RunCtl* ctl, const StepStats* ring, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_run_control<<<1, 32, 0, s>>>(ctl, ring, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_superstep_sell(Algo alg, const SellArgs& args, cudaStream_t s) {
     const uint64_t work = (uint64_t)args.n_hubs + args.n_slices;
-    if (work == 0) {
-        // nothing to compute, but the stat slot two supersteps ahead must still be cleared
-        if (args.stats_clear) return cudaMemsetAsync(args.stats_clear, 0, sizeof(StepStats), s);
-        return cudaSuccess;
-    }
-    const uint32_t grid = (uint32_t)((work + kSellWarps - 1) / kSellWarps);
+    // an empty layout still runs one block: it clears the stat slot two
+    // supersteps ahead (and the step may live in device memory)
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, (work + kSellWarps - 1) / kSellWarps);
     switch (alg) {
         case Algo::SSSP: k_sell<Algo::SSSP><<<grid, kSellBlock, 0, s>>>(args); break;
         case Algo::CC: k_sell<Algo::CC><<<grid, kSellBlock, 0, s>>>(args); break;

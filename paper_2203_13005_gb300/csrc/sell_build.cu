@@ -706,6 +706,16 @@ cudaError_t launch_relabel(const uint32_t* col_ptr, uint32_t n, uint32_t* new2ol
     return cudaGetLastError();
 }
 
+cudaError_t launch_exclusive_scan_u32(const uint32_t* x, uint32_t n, uint32_t* out, uint32_t* scratch,
+                                      cudaStream_t s) {
+    if (n == 0) return cudaMemsetAsync(out, 0, 4, s);
+    const uint32_t scan_blocks = (n + kScanChunk - 1) / kScanChunk;
+    k_scan_sums<<<scan_blocks, 256, 0, s>>>(x, n, scratch);
+    k_scan_top<<<1, 1024, 0, s>>>(scratch, scan_blocks);
+    k_scan_apply<<<scan_blocks, 256, 0, s>>>(x, n, scratch, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_permute_u32(const uint32_t* in, const uint32_t* map, uint32_t n, uint32_t* out, bool scatter,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;

@@ -180,6 +180,9 @@ SSSP_RMAT16 = Workload("sssp_rmat16", "rmat", 16, 1 << 20, 0x67700001, 1, 100)
 PAGERANK_RMAT22 = Workload("pagerank_rmat22", "rmat", 22, 1 << 26, 0x67700002)
 CC_ER24_P8 = Workload("cc_er24_8parts", "er", 24, 1 << 28, 0x67700003, parts=8)
 MSSSP_RMAT24 = Workload("msssp64_rmat24", "rmat", 24, 1 << 28, 0x67700004, 1, 255)
+# the SSSP recipe at the PageRank graph's size: where a pull sweep costs
+# about a millisecond and the sparse supersteps are worth pushing
+SSSP_RMAT22 = Workload("sssp_rmat22", "rmat", 22, 1 << 26, 0x67700006, 1, 100)
 SERVE_SEED = 0x67700005
 # served graphs: R-MAT scales 18/20/22/24, edge factor 16, w ~ U{1..255};
 # seeds 0x67700018, 0x67700020, 0x67700022, 0x67700024 (the scale in hex digits)
