@@ -695,7 +695,9 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
                "init values");
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
-    frontier_ = a != Algo::PR && n_parts_ == 1 && cfg_.direction != GXP_DIR_PULL;
+    // (the packed frontier counter needs lists of fewer than 2^32 items)
+    frontier_ = a != Algo::PR && n_parts_ == 1 && cfg_.direction != GXP_DIR_PULL &&
+                (uint64_t)V + (total_edges_ + kItemEdges - 1) / kItemEdges < (1ull << 32);
     if (frontier_) {
         build_out_edges();
         // both value buffers start equal: the push superstep lowers the next
@@ -867,10 +869,9 @@ void Engine::build_out_edges() {
     list_cap_ = (uint64_t)V + (E + kItemEdges - 1) / kItemEdges;
     for (auto& l : d_list_) l = (uint2*)dalloc(sizeof(uint2) * std::max<uint64_t>(list_cap_, 1));
     void* scratch = nullptr;
-    cudaError_t e = cudaMalloc(&scratch, 4 * out_edges_scratch_words(V));
+    cudaError_t e = cudaMalloc(&scratch, 4 * out_edges_scratch_words(V, E));
     if (e == cudaSuccess) {
-        uint32_t* cursor = (uint32_t*)scratch;
-        e = launch_out_edges(work_[0].in, V, d_outdeg_, d_out_ptr_, cursor, cursor + V + 1, d_out_dst_,
+        e = launch_out_edges(work_[0].in, V, E, d_outdeg_, d_out_ptr_, (uint32_t*)scratch, d_out_dst_,
                              weighted_ ? d_out_w_ : nullptr, stream_);
     }
     cudaError_t e2 = cudaStreamSynchronize(stream_);

@@ -304,11 +304,12 @@ cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s
 // push direction (frontier.cu)
 struct RowSource;
 // out-edge copy of the CSC `in` (rows renumbered as the layout build does):
-// out_ptr = exclusive scan of outdeg (internal ids); cursor: n scratch words
-cudaError_t launch_out_edges(const RowSource& in, uint32_t n, const uint32_t* outdeg, uint32_t* out_ptr,
-                             uint32_t* cursor, uint32_t* scan_scratch, uint32_t* out_dst, uint32_t* out_w,
+// out_ptr = exclusive scan of outdeg (internal ids); scratch holds
+// out_edges_scratch_words(n, n_edges) words
+cudaError_t launch_out_edges(const RowSource& in, uint32_t n, uint64_t n_edges, const uint32_t* outdeg,
+                             uint32_t* out_ptr, uint32_t* scratch, uint32_t* out_dst, uint32_t* out_w,
                              cudaStream_t s);
-size_t out_edges_scratch_words(uint32_t n);
+size_t out_edges_scratch_words(uint32_t n, uint64_t n_edges);
 // f.list_out <- items of vertex `source` (all vertices when source == kInf);
 // the counts go to stats->list_ne (zeroed here first)
 cudaError_t launch_seed_frontier(uint32_t n, uint32_t source, const uint32_t* out_ptr, const FrontierCfg& f,
