@@ -9,8 +9,9 @@ Section III-B in numpy.
 
 Pins (what holds this oracle to something other than itself) live in
 ``tests/test_oracle_pins.py``: SciPy's Dijkstra and connected components,
-hand-built graphs, closed forms for PageRank, dense linear solves, and brute
-force for Lemma 1.
+hand-built graphs, closed forms for PageRank and for mode-label propagation
+on cliques, stars, paths and oscillating pairs, dense linear solves, and
+brute force for Lemma 1.
 """
 from __future__ import annotations
 
@@ -62,6 +63,10 @@ def _load():
         lib.orc_cc_step.argtypes = [u64, u64, p, p, p, p, p]
         lib.orc_cc.restype = i64
         lib.orc_cc.argtypes = [u64, u64, p, p, u32, p, p]
+        lib.orc_lp_step.restype = u64
+        lib.orc_lp_step.argtypes = [u64, u64, p, p, p, p, p]
+        lib.orc_lp.restype = i64
+        lib.orc_lp.argtypes = [u64, u64, p, p, u32, p, p]
         lib.orc_pr_step.restype = dbl
         lib.orc_pr_step.argtypes = [u64, u64, p, p, p, dbl, p, p, p]
         lib.orc_pagerank.restype = C.c_int
@@ -119,6 +124,30 @@ def cc_step(n, src, dst, l_in):
     l_out = np.empty(n, dtype=np.uint32)
     msg = np.empty(n, dtype=np.uint32)
     c = _load().orc_cc_step(n, len(src), _p(src), _p(dst), _p(l_in), _p(l_out), _p(msg))
+    return l_out, int(c)
+
+
+LP_MAX_STEPS = 15   # Section V-A caps LP at 15 iterations
+
+
+def lp(n, src, dst, max_steps=LP_MAX_STEPS):
+    """Synchronous mode-label propagation from l_0[v] = v until a superstep
+    changes nothing or max_steps. Returns (labels u32[n], supersteps, changed[])."""
+    src, dst = _u32(src), _u32(dst)
+    labels = np.empty(n, dtype=np.uint32)
+    cap = max(1, max_steps)
+    changed = np.zeros(cap, dtype=np.uint64)
+    steps = _load().orc_lp(n, len(src), _p(src), _p(dst), max_steps, _p(labels), _p(changed))
+    if steps < 0:
+        raise MemoryError("oracle lp allocation failed")
+    return labels, int(steps), changed[:steps].copy()
+
+
+def lp_step(n, src, dst, l_in):
+    src, dst, l_in = _u32(src), _u32(dst), _u32(l_in)
+    l_out = np.empty(n, dtype=np.uint32)
+    pairs = np.empty(max(1, len(src)), dtype=np.uint64)
+    c = _load().orc_lp_step(n, len(src), _p(src), _p(dst), _p(l_in), _p(l_out), _p(pairs))
     return l_out, int(c)
 
 

@@ -23,6 +23,12 @@
  *         r_{t+1}[v] = (1-d)/N + d*(sum_{(u,v)} r_t[u]/outdeg(u) + D_t/N),
  *         fixed number of supersteps, fp64.
  *   PPR   r_0 = e_s, r_{t+1} = (1-d) e_s + d*(A^T D^-1 r_t + D_t e_s), fp64.
+ *   LP    (label propagation read as synchronous mode-label propagation, the
+ *         paper's LP workload, capped at 15 supersteps in Section V-A)
+ *         l_0[v]=v; v's new label is the label carried by the most in-edges
+ *         (u,v) (message l[u]), ties to the smallest label; a vertex without
+ *         in-edges keeps its label. Stop after a superstep that changes
+ *         nothing, or after max_steps.
  * Multi-edges count in out-degrees and in merges; self-loops are kept.
  */
 #include <stdint.h>
@@ -118,6 +124,68 @@ int64_t orc_cc(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
     }
     if (cur != labels) memcpy(labels, cur, n * sizeof(uint32_t));
     free(other); free(msg);
+    return steps;
+}
+
+/* ------------------------------------------------------------------ LP ---- */
+
+static int orc_cmp_u64(const void* a, const void* b) {
+    const uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/*
+ * One synchronous mode-label superstep: l_out from l_in. MSGGen sends l_in[u]
+ * along every edge (u,v); MSGMerge takes the mode of v's messages (the
+ * (v, label) pairs are sorted, so equal labels of v are adjacent and labels
+ * ascend: the first run of the largest length is the smallest label among
+ * the most frequent); MSGApply sets it, or keeps l_in[v] without messages.
+ * Returns #changed.
+ */
+uint64_t orc_lp_step(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                     const uint32_t* l_in, uint32_t* l_out, uint64_t* pairs /* scratch, m entries */) {
+    for (uint64_t e = 0; e < m; ++e)                               /* MSGGen */
+        pairs[e] = ((uint64_t)dst[e] << 32) | (uint64_t)l_in[src[e]];
+    qsort(pairs, (size_t)m, sizeof(uint64_t), orc_cmp_u64);
+    for (uint64_t v = 0; v < n; ++v) l_out[v] = l_in[v];          /* no messages: keep */
+    uint64_t i = 0;
+    while (i < m) {                                                /* MSGMerge(mode) + MSGApply */
+        const uint64_t v = pairs[i] >> 32;
+        uint64_t best_count = 0;
+        uint32_t best_label = 0;
+        while (i < m && (pairs[i] >> 32) == v) {
+            uint64_t k = i;
+            while (k < m && pairs[k] == pairs[i]) ++k;
+            if (k - i > best_count) {                              /* strict: ties keep the smaller label */
+                best_count = k - i;
+                best_label = (uint32_t)pairs[i];
+            }
+            i = k;
+        }
+        l_out[v] = best_label;
+    }
+    uint64_t changed = 0;
+    for (uint64_t v = 0; v < n; ++v) changed += (l_out[v] != l_in[v]);
+    return changed;
+}
+
+int64_t orc_lp(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+               uint32_t max_steps, uint32_t* labels, uint64_t* changed_per_step) {
+    uint32_t* other = (uint32_t*)malloc(n * sizeof(uint32_t) + 4);
+    uint64_t* pairs = (uint64_t*)malloc(m * sizeof(uint64_t) + 8);
+    if (!other || !pairs) { free(other); free(pairs); return -1; }
+    for (uint64_t v = 0; v < n; ++v) labels[v] = (uint32_t)v;
+    uint32_t* cur = labels; uint32_t* nxt = other;
+    int64_t steps = 0;
+    for (uint32_t t = 0; t < max_steps; ++t) {
+        const uint64_t c = orc_lp_step(n, m, src, dst, cur, nxt, pairs);
+        if (changed_per_step) changed_per_step[t] = c;
+        ++steps;
+        uint32_t* tmp = cur; cur = nxt; nxt = tmp;
+        if (c == 0) break;
+    }
+    if (cur != labels) memcpy(labels, cur, n * sizeof(uint32_t));
+    free(other); free(pairs);
     return steps;
 }
 

@@ -6,6 +6,10 @@
 * PageRank / PPR: closed forms (directed cycle, undirected star, in-star with a
   dangling centre), two-scalar recurrences for exactly 20 supersteps, and the
   fixed point from a dense linear solve.
+* LP (mode-label propagation): closed-form traces on a clique, an oscillating
+  pair under the 15-superstep cap, a directed in-star, a directed path
+  (Jacobi order), a majority that is not the minimum (multi-edges count), a
+  self-loop, and an undirected star.
 Each family is chosen so a dropped term, a wrong sign/index or a transposed
 operand in the oracle fails at least one test.
 """
@@ -336,3 +340,121 @@ def test_ppr_fixed_point_linear_solve(seed):
     r = oracle.ppr(n, src, dst, s, D, 400)
     assert np.allclose(r, want, rtol=1e-11, atol=1e-15)
     assert abs(r.sum() - 1) < 1e-12
+
+
+# ------------------------------------------------------------------------ LP
+
+def _undirected(pairs):
+    a = np.array([p[0] for p in pairs], np.uint32)
+    b = np.array([p[1] for p in pairs], np.uint32)
+    return np.concatenate([a, b]), np.concatenate([b, a])
+
+
+@pytest.mark.parametrize("k", [4, 7])
+def test_lp_clique_trace(k):
+    # K_k on ids 10..10+k-1 inside 30 vertices. Superstep 1: every neighbour
+    # label occurs once, so the minimum wins: vertex 10 takes 11, the others
+    # take 10. Superstep 2: vertex 10 sees k-1 tens, the others see one 11 and
+    # k-2 >= 2 tens: all take 10. Superstep 3 changes nothing.
+    n, base = 30, 10
+    src, dst = _undirected([(base + i, base + j) for i in range(k) for j in range(i + 1, k)])
+    l1, c1 = oracle.lp_step(n, src, dst, np.arange(n, dtype=np.uint32))
+    exp1 = np.arange(n, dtype=np.uint32)
+    exp1[base] = base + 1
+    exp1[base + 1:base + k] = base
+    assert np.array_equal(l1, exp1) and c1 == k
+    labels, steps, changed = oracle.lp(n, src, dst)
+    exp = np.arange(n, dtype=np.uint32)
+    exp[base:base + k] = base
+    assert np.array_equal(labels, exp)
+    assert steps == 3 and list(changed) == [k, 1, 0]
+
+
+def test_lp_pair_oscillates_to_the_cap():
+    # two vertices joined both ways swap labels every superstep: never quiet
+    src, dst = _undirected([(0, 1)])
+    for cap in (1, 2, 15):
+        labels, steps, changed = oracle.lp(3, src, dst, max_steps=cap)
+        assert steps == cap and list(changed) == [2] * cap
+        assert list(labels) == ([1, 0, 2] if cap % 2 else [0, 1, 2])
+
+
+def test_lp_in_star_reads_in_edges():
+    # leaves 1..5 -> centre 0: the centre sees five distinct labels and takes
+    # the smallest (1); the leaves have no in-edges and keep theirs
+    src = np.arange(1, 6, dtype=np.uint32)
+    dst = np.zeros(5, np.uint32)
+    labels, steps, changed = oracle.lp(6, src, dst)
+    assert list(labels) == [1, 1, 2, 3, 4, 5]
+    assert steps == 2 and list(changed) == [1, 0]
+
+
+def test_lp_path_is_jacobi():
+    # 0 -> 1 -> 2 -> 3: superstep t moves label 0 one hop (an in-place update
+    # would carry it to the end in one superstep)
+    src = np.array([0, 1, 2], np.uint32)
+    dst = np.array([1, 2, 3], np.uint32)
+    l1, _ = oracle.lp_step(4, src, dst, np.arange(4, dtype=np.uint32))
+    assert list(l1) == [0, 0, 1, 2]
+    labels, steps, changed = oracle.lp(4, src, dst)
+    assert list(labels) == [0, 0, 0, 0]
+    assert steps == 4 and list(changed) == [3, 2, 1, 0]
+
+
+def test_lp_majority_beats_minimum():
+    # vertex 9 receives 5 twice (a multi-edge) and 3 once: the mode is 5
+    src = np.array([5, 5, 3], np.uint32)
+    dst = np.array([9, 9, 9], np.uint32)
+    l1, c1 = oracle.lp_step(10, src, dst, np.arange(10, dtype=np.uint32))
+    assert l1[9] == 5 and c1 == 1
+    # with one edge from 5, 5 and 3 tie and the smaller label wins
+    l1, _ = oracle.lp_step(10, src[1:], dst[1:], np.arange(10, dtype=np.uint32))
+    assert l1[9] == 3
+
+
+def test_lp_self_loop_counts():
+    # 7 -> 7 twice and 2 -> 7: the own label arrives twice and wins; with one
+    # self-loop the tie goes to the smaller label 2
+    l1, _ = oracle.lp_step(8, np.array([7, 7, 2], np.uint32), np.array([7, 7, 7], np.uint32),
+                           np.arange(8, dtype=np.uint32))
+    assert l1[7] == 7
+    l1, _ = oracle.lp_step(8, np.array([7, 2], np.uint32), np.array([7, 7], np.uint32),
+                           np.arange(8, dtype=np.uint32))
+    assert l1[7] == 2
+
+
+@pytest.mark.parametrize("k", [3, 6])
+def test_lp_undirected_star_trace(k):
+    # centre 0, leaves 1..k: the leaves take 0 and the centre the smallest
+    # leaf label 1; then the leaves take 1 and the centre sees k zeros
+    # (takes 0); the two labels swap between centre and leaves from then on
+    src, dst = _undirected([(0, i) for i in range(1, k + 1)])
+    n = k + 1
+    labels, steps, changed = oracle.lp(n, src, dst, max_steps=15)
+    assert steps == 15
+    assert list(changed) == [k + 1] + [k + 1] * 14
+    # after an odd number of supersteps: centre 1, leaves 0
+    assert labels[0] == 1 and np.all(labels[1:] == 0)
+    labels, _, _ = oracle.lp(n, src, dst, max_steps=4)
+    assert labels[0] == 0 and np.all(labels[1:] == 1)
+
+
+def test_lp_result_labels_come_from_in_neighbours():
+    # invariant on a random graph: every new label is the old one (no
+    # in-edges) or the label of an in-neighbour, and no other label reaches
+    # the vertex more often
+    rng = np.random.default_rng(4)
+    n = 300
+    src = rng.integers(0, n, 900, dtype=np.uint32)
+    dst = rng.integers(0, n, 900, dtype=np.uint32)
+    l0 = rng.integers(0, 20, n, dtype=np.uint32)
+    l1, _ = oracle.lp_step(n, src, dst, l0)
+    for v in range(n):
+        msgs = l0[src[dst == v]]
+        if len(msgs) == 0:
+            assert l1[v] == l0[v]
+            continue
+        vals, cnt = np.unique(msgs, return_counts=True)
+        assert l1[v] in vals
+        assert cnt[vals == l1[v]][0] == cnt.max()
+        assert l1[v] == vals[cnt == cnt.max()].min()
