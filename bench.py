@@ -351,6 +351,69 @@ def run_cc(args):
     ctx.close()
 
 
+def run_lp(args):
+    """Label propagation (mode merge, ties to the smallest label, at most 15
+    supersteps as in the paper's LP runs) on the Erdős–Rényi graph of the CC
+    workload (2^24 vertices, 2^28 directed edges) in 8 partitions with sync
+    caching and skipping. GTEPS = supersteps x edges / run time; the roofline
+    counts 8 B per edge (source id, gathered label) and 40 B per row (its
+    descriptor, old and new label) over the run's supersteps."""
+    import torch
+    from paper_2203_13005_gb300 import gxp
+    wl = synth.CC_ER24_P8 if args.lp_scale == 24 else synth.CC_ER24_P8.scaled(args.lp_scale)
+    src, dst, _ = wl.edges()
+    n, m = wl.n_vertices, wl.n_edges
+    parts = args.lp_parts
+    ctx = gxp.Context(0)
+    ctx.create_graph(n, parts)
+    ctx.load_coo(src, dst)
+    del src, dst
+    cap = 15
+    times = []
+    steps = 0
+    with ClockSampler(0) as clk:
+        for r in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = ctx.run(gxp.GXP_ALGO_LP, max_steps=cap)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    st = ctx.stats()
+    sec = min(times[1:]) if len(times) > 1 else times[0]
+    # per-superstep device time (events around each superstep incl. its sync)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    ctx.begin(gxp.GXP_ALGO_LP)
+    g, mm, a = gxp.TEMPLATES[gxp.GXP_ALGO_LP]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for b, e in evs:
+        b.record(stream)
+        ctx.lib.gxp_superstep(ctx.h, gxp.GXP_ALGO_LP, g, mm, a, None)
+        e.record(stream)
+    torch.cuda.synchronize()
+    step_us = [b.elapsed_time(e) * 1e3 for b, e in evs]
+    k_us = statistics.mean(step_us)
+    bytes_step = 8 * m + 40 * n
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": steps * m / sec / 1e9, "unit": "GTEPS", "n_gpus": 1,
+        "steps": len(times) - 1, "warmup": 1, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"lp_er{wl.scale}_{parts}parts", "vertices": n, "edges": m, "partitions": parts,
+                   "max_supersteps": cap, "step": "one LP run (to a quiet superstep or the cap)",
+                   "superstep_us": [round(x, 1) for x in step_us]},
+        "supersteps": steps, "syncs_done": st["syncs_done"], "syncs_skipped": st["syncs_skipped"],
+        "sync_pairs": st["sync_pairs"],
+        "roofline": {"bound": "hbm", "achieved": bytes_step / (k_us * 1e-6) / 1e9, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": bytes_step / (k_us * 1e-6) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"], "kernel": "k_lp_small + k_lp_chunks + k_lp_hubs (+ sync)",
+                     "avg_superstep_us": k_us, "algorithmic_bytes_per_superstep": bytes_step},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
@@ -578,9 +641,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default=WL.name,
                     choices=[WL.name, synth.SSSP_RMAT16.name, synth.SSSP_RMAT22.name, synth.MSSSP_RMAT24.name,
-                             synth.CC_ER24_P8.name,
+                             synth.CC_ER24_P8.name, "lp_er24_8parts",
                              "serve"],
                     help="extra workloads print their own line; the default is the headline")
+    ap.add_argument("--lp-parts", type=int, default=8, help="lp_er24_8parts: partitions (1 = one, renumbered)")
+    ap.add_argument("--lp-scale", type=int, default=24, help="lp_er24_8parts: log2 vertices (smaller for profiling)")
     ap.add_argument("--direction", default="auto", choices=sorted(DIRECTIONS),
                     help="sssp_rmat16: direction of the supersteps")
     ap.add_argument("--push-div", type=int, default=0, help="sssp_rmat16: auto pushes while frontier work x div <= E")
@@ -606,6 +671,8 @@ def main():
     if args.workload == synth.CC_ER24_P8.name:
         run_cc(args)
         return
+    if args.workload == "lp_er24_8parts":
+        return run_lp(args)
     if args.workload in (synth.SSSP_RMAT16.name, synth.SSSP_RMAT22.name):
         run_sssp(args)
         return

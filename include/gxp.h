@@ -58,8 +58,13 @@ typedef enum gxp_algo {
     GXP_ALGO_SSSP = 0,      /* Bellman-Ford shortest paths (Section V-A) */
     GXP_ALGO_CC = 1,        /* min-label propagation = weakly connected components */
     GXP_ALGO_PAGERANK = 2,  /* PageRank with dangling-mass redistribution */
-    GXP_ALGO_PPR = 3        /* personalized PageRank from `source`: PageRank whose teleport and
+    GXP_ALGO_PPR = 3,       /* personalized PageRank from `source`: PageRank whose teleport and
                                dangling mass return to the source (r_0 = e_source) */
+    GXP_ALGO_LP = 4         /* label propagation (Section V-A's LP): l_0[v] = v; each superstep a
+                               vertex takes the label most of its in-edges carry, ties to the
+                               smallest label; vertices without in-edges keep theirs. Synchronous
+                               (Jacobi); it need not converge (the paper caps it at 15 supersteps:
+                               pass max_steps = 15 to gxp_run) */
 } gxp_algo;
 
 /* The three template functions of Section IV-A1, as built-in operators. */
@@ -71,13 +76,15 @@ typedef enum gxp_msggen {
 
 typedef enum gxp_merge {
     GXP_MERGE_MIN = 0,      /* uint32 minimum, exact */
-    GXP_MERGE_SUM = 1       /* fp32 sum in a fixed order (deterministic) */
+    GXP_MERGE_SUM = 1,      /* fp32 sum in a fixed order (deterministic) */
+    GXP_MERGE_MODE = 2      /* the most frequent uint32 message, ties to the smallest, exact */
 } gxp_merge;
 
 typedef enum gxp_apply {
     GXP_APPLY_MIN = 0,      /* x' = min(x, m); changed if x' != x */
-    GXP_APPLY_PAGERANK = 1  /* r' = (1-d)/N + d (m + D/N), D = dangling mass; personalized
+    GXP_APPLY_PAGERANK = 1, /* r' = (1-d)/N + d (m + D/N), D = dangling mass; personalized
                                PageRank: r' = d m, plus (1-d) + d D at the source */
+    GXP_APPLY_SET = 2       /* x' = m if the vertex received messages, else x; changed if x' != x */
 } gxp_apply;
 
 typedef enum gxp_format {
@@ -191,16 +198,18 @@ GXP_API gxp_status gxp_load_partition(gxp_ctx* ctx, uint32_t part, gxp_format fm
 /* ------------------------------------------------------- vertex values -- */
 
 /* Start an algorithm: set every partition's vertex values to its initial
- * state — SSSP: d[source] = 0, else 0xFFFFFFFF; CC: l[v] = v; PageRank:
- * r[v] = 1/N; personalized PageRank: r = e_source — and reset the superstep
- * counters. `source` is ignored for CC and PageRank. damping is used by
+ * state — SSSP: d[source] = 0, else 0xFFFFFFFF; CC and LP: l[v] = v;
+ * PageRank: r[v] = 1/N; personalized PageRank: r = e_source — and reset the
+ * superstep counters. `source` is ignored for CC, LP and PageRank. LP builds
+ * its row lists (in-degree classes; hub rows get hash tables of 2^k >= 2 x
+ * in-degree slots) on first use. damping is used by
  * PageRank/PPR (e.g. 0.85). PPR runs the PageRank template (CONTRIB, SUM,
  * PAGERANK) with gxp_superstep(GXP_ALGO_PPR, ...). Builds the
  * partition caches (ghost/mirror tables) on first use. */
 GXP_API gxp_status gxp_begin(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping);
 
 /* Copy the current values of the vertices owned by `part` (in local order,
- * n = owned count) to `out`: uint32 for SSSP/CC, fp32 ranks for PageRank.
+ * n = owned count) to `out`: uint32 for SSSP/CC/LP, fp32 ranks for PageRank.
  * part = UINT32_MAX copies all partitions in global id order (n = n_vertices). */
 GXP_API gxp_status gxp_get_values(gxp_ctx* ctx, uint32_t part, void* out, uint64_t n);
 
@@ -219,7 +228,8 @@ GXP_API gxp_status gxp_set_values(gxp_ctx* ctx, uint32_t part, const void* in, u
  * boundary vertices (lazy uploading, Algorithm 3) into the caches of the
  * others, and the exchange is skipped when there are none anywhere
  * (Section III-B3). Supported templates: SSSP = (RELAX, MIN, MIN),
- * CC = (LABEL, MIN, MIN), PageRank = (CONTRIB, SUM, PAGERANK); others return
+ * CC = (LABEL, MIN, MIN), PageRank = (CONTRIB, SUM, PAGERANK),
+ * LP = (LABEL, MODE, SET); others return
  * GXP_E_UNSUPPORTED. `algo` must match gxp_begin. If n_changed is non-NULL
  * the call waits for the device and stores the number of vertices whose
  * value changed; otherwise it returns once the work is enqueued. */

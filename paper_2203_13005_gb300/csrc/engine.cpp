@@ -95,6 +95,7 @@ void Engine::free_graph_device() {
     }
     d_ctl_ = nullptr;
     h_old2new_.clear();
+    lp_ = LpLists{};
     for (void* p : graph_allocs_) cudaFree(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
@@ -669,6 +670,7 @@ static Algo to_algo(gxp_algo a) {
         case GXP_ALGO_CC: return Algo::CC;
         case GXP_ALGO_PAGERANK: return Algo::PR;
         case GXP_ALGO_PPR: return Algo::PR;   // PageRank with the teleport returning to one source
+        case GXP_ALGO_LP: return Algo::LP;
         default: fail(GXP_E_INVAL, "unknown algorithm");
     }
 }
@@ -679,7 +681,7 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     const bool personalized = algo == GXP_ALGO_PPR;
     if ((a == Algo::SSSP || personalized) && source >= n_vertices_) fail(GXP_E_INVAL, "source out of range");
     if (a == Algo::PR && !(damping >= 0.0f && damping < 1.0f)) fail(GXP_E_INVAL, "damping must be in [0, 1)");
-    if (a != Algo::PR && n_parts_ > 1 && cfg_.direction == GXP_DIR_PUSH)
+    if ((a == Algo::SSSP || a == Algo::CC) && n_parts_ > 1 && cfg_.direction == GXP_DIR_PUSH)
         fail(GXP_E_UNSUPPORTED, "push direction is implemented for single-partition graphs");
     if (!finalized_) finalize();
     if (a == Algo::SSSP && !weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights on every partition");
@@ -696,7 +698,12 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
     // (the packed frontier counter needs lists of fewer than 2^32 items)
-    frontier_ = a != Algo::PR && n_parts_ == 1 && cfg_.direction != GXP_DIR_PULL &&
+    if (a == Algo::LP) {
+        build_lp();
+        // rows without in-edges are never written: both buffers hold their labels
+        cuda_check(cudaMemcpyAsync(d_own_[1], d_own_[0], 4ull * V, cudaMemcpyDeviceToDevice, stream_), "copy values");
+    }
+    frontier_ = (a == Algo::SSSP || a == Algo::CC) && n_parts_ == 1 && cfg_.direction != GXP_DIR_PULL &&
                 (uint64_t)V + (total_edges_ + kItemEdges - 1) / kItemEdges < (1ull << 32);
     if (frontier_) {
         build_out_edges();
@@ -765,12 +772,37 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         fail(GXP_E_INVAL, "algorithm differs from the one begun");
     const bool ok = (algo_ == Algo::SSSP && g == GXP_GEN_RELAX && m == GXP_MERGE_MIN && ap == GXP_APPLY_MIN) ||
                     (algo_ == Algo::CC && g == GXP_GEN_LABEL && m == GXP_MERGE_MIN && ap == GXP_APPLY_MIN) ||
-                    (algo_ == Algo::PR && g == GXP_GEN_CONTRIB && m == GXP_MERGE_SUM && ap == GXP_APPLY_PAGERANK);
+                    (algo_ == Algo::PR && g == GXP_GEN_CONTRIB && m == GXP_MERGE_SUM && ap == GXP_APPLY_PAGERANK) ||
+                    (algo_ == Algo::LP && g == GXP_GEN_LABEL && m == GXP_MERGE_MODE && ap == GXP_APPLY_SET);
     if (!ok) fail(GXP_E_UNSUPPORTED, "unsupported (msggen, merge, apply) template for this algorithm");
     const int nx = cur_ ^ 1;
-    const SellArgs a = sell_args();
     cuda_check(cudaEventRecord(ev_a_, stream_), "event");
-    cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
+    if (algo_ == Algo::LP) {
+        LpArgs l{};
+        l.parts = lp_.d_parts;
+        l.windows = lp_.d_windows;
+        l.n_windows = lp_.n_windows;
+        l.row_g = lp_.d_row_g;
+        l.chunks = lp_.d_chunks;
+        l.n_chunks = lp_.n_chunks;
+        l.hubs = lp_.d_hubs;
+        l.n_hubs = lp_.n_hubs;
+        l.keys = lp_.d_keys;
+        l.counts = lp_.d_counts;
+        l.own_cur = d_own_[cur_];
+        l.own_nxt = d_own_[nx];
+        l.ghost = d_ghost_;
+        l.changed_bits = n_parts_ > 1 ? d_changed_ : nullptr;
+        l.stats_in = d_stats_ + step_ % kStatRing;
+        l.stats_out = d_stats_ + (step_ + 1) % kStatRing;
+        l.stats_clear = d_stats_ + (step_ + 2) % kStatRing;
+        l.skip_if_quiet = (early_exit_ && step_ > 0) ? 1u : 0u;
+        l.narrow_labels = n_vertices_ <= (1ull << 27) ? 1u : 0u;   // labels are vertex ids
+        cuda_check(launch_lp_superstep(l, stream_), "label propagation superstep");
+    } else {
+        const SellArgs a = sell_args();
+        cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
+    }
     if (n_parts_ > 1) {
         SyncArgs s{};
         s.parts = d_parts_;
@@ -891,6 +923,81 @@ void Engine::seed_frontier(uint32_t source_int) {
                                     stream_), "seed frontier");
 }
 
+// Row lists of label propagation, by in-degree class (host-built once per
+// graph from the partitions' offsets): 1..kLpSmall in-edges (packed into
+// warp windows of adjacent edges, in CSC order), up to kLpChunk, and hub rows
+// cut into chunks of kLpChunk with a hash table each.
+void Engine::build_lp() {
+    if (lp_.ready) return;
+    std::vector<LpPart> parts(n_parts_);
+    std::vector<LpRow> chunks;
+    std::vector<LpWindow> windows;
+    std::vector<uint32_t> row_g;
+    std::vector<LpHub> hubs;
+    uint64_t table_slots = 0;
+    auto add_row = [&](uint32_t g, uint32_t p, uint32_t e0, uint32_t deg) {
+        if (deg == 0) return;
+        if (deg <= kLpSmall) {
+            // joins the open window if its edges follow on and fit, else opens one
+            LpWindow* w = windows.empty() ? nullptr : &windows.back();
+            const uint32_t wn = w ? (w->n_part & 63u) : 0u;
+            if (!w || (w->n_part >> 6) != p || w->e0 + wn != e0 || wn + deg > 32u) {
+                windows.push_back(LpWindow{e0, (uint32_t)row_g.size(), 0u, p << 6});
+                w = &windows.back();
+            }
+            const uint32_t at = w->n_part & 63u;
+            w->starts |= 1u << at;
+            w->n_part += deg;
+            row_g.push_back(g);
+        } else if (deg <= kLpChunk) {
+            chunks.push_back(LpRow{g, p, e0, deg, kInf, {0, 0, 0}});
+        } else {
+            uint32_t lg = 1;
+            while ((1ull << lg) < 2ull * deg) ++lg;
+            const uint32_t h = (uint32_t)hubs.size();
+            hubs.push_back(LpHub{g, lg, table_slots});
+            table_slots += 1ull << lg;
+            for (uint32_t c = 0; c < deg; c += kLpChunk)
+                chunks.push_back(LpRow{g, p, e0 + c, std::min(kLpChunk, deg - c), h, {0, 0, 0}});
+        }
+    };
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        HostPart& hp = parts_[p];
+        std::vector<uint32_t> cp(hp.n_own + 1);
+        cuda_check(cudaMemcpy(cp.data(), hp.d_col_ptr, 4ull * (hp.n_own + 1), cudaMemcpyDeviceToHost), "row offsets");
+        const uint32_t* src = hp.d_src;
+        if (relabeled_) {   // sources in internal ids, once: no renumbering lookup per edge and superstep
+            uint32_t* rs = (uint32_t*)dalloc(4 * std::max<uint64_t>(hp.n_edges(), 1));
+            cuda_check(launch_permute_u32(d_old2new_, hp.d_src, (uint32_t)hp.n_edges(), rs, false, stream_),
+                       "renumber sources");
+            src = rs;
+        }
+        parts[p] = LpPart{src, nullptr, hp.v_begin, hp.n_own, hp.ghost_base, 0};
+        for (uint32_t l = 0; l < hp.n_own; ++l) {   // input row order
+            const uint32_t g = relabeled_ ? h_old2new_[l] : hp.v_begin + l;
+            add_row(g, p, cp[l], cp[l + 1] - cp[l]);
+        }
+    }
+    auto upload = [&](const void* h, size_t bytes) {
+        void* d = dalloc(std::max<size_t>(bytes, 16));
+        if (bytes) cuda_check(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice), "upload label propagation lists");
+        return d;
+    };
+    lp_.d_parts = (LpPart*)upload(parts.data(), sizeof(LpPart) * parts.size());
+    lp_.d_windows = (LpWindow*)upload(windows.data(), sizeof(LpWindow) * windows.size());
+    lp_.d_row_g = (uint32_t*)upload(row_g.data(), 4 * row_g.size());
+    lp_.d_chunks = (LpRow*)upload(chunks.data(), sizeof(LpRow) * chunks.size());
+    lp_.d_hubs = (LpHub*)upload(hubs.data(), sizeof(LpHub) * hubs.size());
+    lp_.n_windows = (uint32_t)windows.size();
+    lp_.n_chunks = (uint32_t)chunks.size();
+    lp_.n_hubs = (uint32_t)hubs.size();
+    lp_.d_keys = (uint32_t*)dalloc(4 * std::max<uint64_t>(table_slots, 1));
+    lp_.d_counts = (uint32_t*)dalloc(4 * std::max<uint64_t>(table_slots, 1));
+    cuda_check(cudaMemsetAsync(lp_.d_keys, 0xFF, 4 * std::max<uint64_t>(table_slots, 1), stream_), "memset");
+    cuda_check(cudaMemsetAsync(lp_.d_counts, 0, 4 * std::max<uint64_t>(table_slots, 1), stream_), "memset");
+    lp_.ready = true;
+}
+
 void Engine::sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap, uint64_t* n_out, int* skipped) {
     if (!begun_ || step_ == 0) fail(GXP_E_STATE, "no superstep has run");
     if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
@@ -921,7 +1028,7 @@ void Engine::sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap,
 // condition. Built once per algorithm and graph; false if the driver cannot
 // build it (the run then drives the supersteps from the host).
 bool Engine::run_graph_ready() {
-    if (algo_ == Algo::PR || run_graph_failed_) return false;
+    if (algo_ == Algo::PR || algo_ == Algo::LP || run_graph_failed_) return false;
     cudaGraphExec_t& ge = run_graph_[algo_ == Algo::SSSP ? 0 : 1];
     if (ge) return true;
     if (!h_ctl_) cuda_check(cudaMallocHost(&h_ctl_, 2 * sizeof(RunCtl)), "pinned run control");
@@ -967,9 +1074,9 @@ bool Engine::run_graph_ready() {
 
 uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max_steps) {
     begin(algo, source, damping);
-    const gxp_msggen g = algo_ == Algo::SSSP ? GXP_GEN_RELAX : algo_ == Algo::CC ? GXP_GEN_LABEL : GXP_GEN_CONTRIB;
-    const gxp_merge m = algo_ == Algo::PR ? GXP_MERGE_SUM : GXP_MERGE_MIN;
-    const gxp_apply ap = algo_ == Algo::PR ? GXP_APPLY_PAGERANK : GXP_APPLY_MIN;
+    const gxp_msggen g = algo_ == Algo::SSSP ? GXP_GEN_RELAX : algo_ == Algo::PR ? GXP_GEN_CONTRIB : GXP_GEN_LABEL;
+    const gxp_merge m = algo_ == Algo::PR ? GXP_MERGE_SUM : algo_ == Algo::LP ? GXP_MERGE_MODE : GXP_MERGE_MIN;
+    const gxp_apply ap = algo_ == Algo::PR ? GXP_APPLY_PAGERANK : algo_ == Algo::LP ? GXP_APPLY_SET : GXP_APPLY_MIN;
     uint32_t steps = 0;
     if (algo_ == Algo::PR) {
         for (; steps < max_steps; ++steps) superstep(algo, g, m, ap, false);
@@ -979,7 +1086,7 @@ uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max
     // SSSP / CC on one partition: the loop runs on the device (a graph whose
     // WHILE node repeats superstep + control until the first superstep that
     // changes nothing, at most kRunChunk per launch); one host read per launch
-    if (n_parts_ == 1 && run_graph_ready()) {
+    if (n_parts_ == 1 && algo_ != Algo::LP && run_graph_ready()) {
         const cudaGraphExec_t ge = run_graph_[algo_ == Algo::SSSP ? 0 : 1];
         while (steps < max_steps) {
             const uint32_t k = std::min<uint32_t>(kRunChunk, max_steps - steps);
@@ -1051,7 +1158,7 @@ void Engine::get_values(uint32_t part, void* out, uint64_t n) {
 
 void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
     if (!begun_) fail(GXP_E_STATE, "gxp_begin must come first");
-    if (algo_ == Algo::PR) fail(GXP_E_UNSUPPORTED, "set_values is implemented for SSSP and CC");
+    if (algo_ == Algo::PR) fail(GXP_E_UNSUPPORTED, "set_values is implemented for SSSP, CC and LP");
     if (!in) fail(GXP_E_INVAL, "null input");
     uint64_t off = 0, cnt = n_vertices_;
     if (part != 0xFFFFFFFFu) {
@@ -1069,6 +1176,9 @@ void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
         cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
     }
     cuda_check(launch_init_ghosts(algo_, n_ghost_total_, d_ghost_gid_, d_own_[cur_], d_ghost_, stream_), "refresh caches");
+    if (algo_ == Algo::LP)   // rows without in-edges are read from either buffer
+        cuda_check(cudaMemcpyAsync(d_own_[cur_ ^ 1], d_own_[cur_], 4ull * n_vertices_, cudaMemcpyDeviceToDevice,
+                                   stream_), "copy values");
     if (frontier_) {   // any value may have moved: every vertex is in the next frontier
         cuda_check(cudaMemcpyAsync(d_own_[cur_ ^ 1], d_own_[cur_], 4ull * n_vertices_, cudaMemcpyDeviceToDevice,
                                    stream_), "copy values");

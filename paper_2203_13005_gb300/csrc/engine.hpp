@@ -177,6 +177,19 @@ private:
     uint64_t list_cap_ = 0;
     void build_out_edges();
     void seed_frontier(uint32_t source_int);
+    // label propagation: rows by in-degree class, hub hash tables
+    struct LpLists {
+        bool ready = false;
+        LpPart* d_parts = nullptr;
+        LpWindow* d_windows = nullptr;
+        uint32_t* d_row_g = nullptr;
+        LpRow* d_chunks = nullptr;
+        LpHub* d_hubs = nullptr;
+        uint32_t n_windows = 0, n_chunks = 0, n_hubs = 0;
+        uint32_t* d_keys = nullptr;
+        uint32_t* d_counts = nullptr;
+    } lp_;
+    void build_lp();
     // device-driven runs (min-label algorithms, one partition)
     static constexpr uint32_t kRunChunk = 32;   // supersteps per graph launch (the stat ring holds 64)
     cudaGraphExec_t run_graph_[2] = {nullptr, nullptr};   // SSSP, CC

@@ -143,8 +143,8 @@ __global__ void k_init_values(int algo, uint32_t ppr_source, uint32_t n, uint32_
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (algo == (int)Algo::SSSP) {
             own[v] = (v == source) ? 0u : kInf;
-        } else if (algo == (int)Algo::CC) {
-            own[v] = label_of ? label_of[v] : v;   // CC labels are input ids
+        } else if (algo == (int)Algo::CC || algo == (int)Algo::LP) {
+            own[v] = label_of ? label_of[v] : v;   // CC / LP labels are input ids
         } else {
             // PageRank: r_0 = 1/N everywhere; personalized PageRank: r_0 = e_source
             const float r0 = ppr_source == kInf ? (float)(1.0 / (double)n) : (v == ppr_source ? 1.0f : 0.0f);

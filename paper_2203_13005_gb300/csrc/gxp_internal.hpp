@@ -29,7 +29,7 @@ constexpr uint32_t kErrTimeout = 2u;
 // an fp32 value x in [0, 2] is held as round(x * 2^60) in a uint64.
 constexpr int kFxShift = 60;
 
-enum class Algo : int { SSSP = 0, CC = 1, PR = 2 };
+enum class Algo : int { SSSP = 0, CC = 1, PR = 2, LP = 3 };
 
 // One edge block ("tile") paired with its vertex block (Section II-B): the
 // in-edges [e0, e0+ne) of local destinations [v0, v0+nv) of one partition.
@@ -243,6 +243,62 @@ struct PprArgs {
     uint64_t active_mask;            // slots holding a query
     uint64_t finish_mask;            // slots whose last superstep this is
 };
+
+// Mode-label propagation (lp.cu). Rows are listed by in-degree class:
+// 1..32 in-edges (packed into warp windows), up to kLpChunk (a CTA per row), more (a
+// hub: chunks of kLpChunk counted into a hash table of its own, then one CTA
+// takes the mode). Rows without in-edges keep their labels and are not listed.
+constexpr uint32_t kLpSmall = 32;
+constexpr uint32_t kLpChunk = 4096;
+struct LpPart {                 // where a row's in-edges and their labels are
+    const uint32_t* src;        // CSC sources (local ids, or input ids with src_map)
+    const uint32_t* src_map;    // single renumbered partition: input id -> value index
+    uint32_t v_begin, n_own, ghost_base, pad;
+};
+struct LpRow {                  // a row, or a chunk of a hub row
+    uint32_t g;                 // value index (global internal id)
+    uint32_t part;
+    uint32_t e0;                // first in-edge (partition CSC index)
+    uint32_t n;                 // in-edges
+    uint32_t hub;               // hub index for a hub chunk, else kInf
+    uint32_t pad[3];
+};
+// Consecutive rows of 1..32 in-edges whose edges are adjacent, packed into
+// one warp's 32 lanes: lane k reads edge e0 + k; bit k of `starts` marks
+// the lanes where a row begins (the rows' value indices are row_g[first ..]).
+struct LpWindow {
+    uint32_t e0;
+    uint32_t first;
+    uint32_t starts;
+    uint32_t n_part;            // edges (low 6 bits) | partition << 6
+};
+struct LpHub {
+    uint32_t g;
+    uint32_t log2_size;         // table slots = 2^log2_size >= 2 in-degree
+    uint64_t table;             // first slot
+};
+struct LpArgs {
+    const LpPart* parts;
+    const LpWindow* windows;    // rows of 1..kLpSmall in-edges
+    uint32_t n_windows;
+    const uint32_t* row_g;      // their value indices
+    const LpRow* chunks;        // kLpSmall < in-edges <= kLpChunk (hub = kInf), and hub chunks
+    uint32_t n_chunks;
+    const LpHub* hubs;
+    uint32_t n_hubs;
+    uint32_t* keys;             // hub tables: label per slot (kInf = empty) ...
+    uint32_t* counts;           // ... and its count; left empty after each superstep
+    const uint32_t* own_cur;
+    uint32_t* own_nxt;
+    const uint32_t* ghost;
+    uint32_t* changed_bits;     // partitions: bitmap of changed vertices, or nullptr
+    const StepStats* stats_in;
+    StepStats* stats_out;
+    StepStats* stats_clear;
+    uint32_t skip_if_quiet;     // 1: return at once if the previous superstep changed nothing
+    uint32_t narrow_labels;     // 1: labels < 2^27 (32-bit (row, label) keys suffice)
+};
+cudaError_t launch_lp_superstep(const LpArgs& a, cudaStream_t s);
 
 // Arguments of the two sync kernels (changed ∩ boundary -> gdq -> caches).
 struct SyncArgs {

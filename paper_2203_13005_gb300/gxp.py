@@ -21,10 +21,10 @@ from . import build as _build
 GXP_OK, GXP_E_INVAL, GXP_E_NOMEM, GXP_E_CUDA, GXP_E_TIMEOUT = 0, 1, 2, 3, 4
 GXP_E_BOUNDS, GXP_E_STATE, GXP_E_UNSUPPORTED, GXP_E_BUSY = 5, 6, 7, 8
 # algorithms and template operators
-GXP_ALGO_SSSP, GXP_ALGO_CC, GXP_ALGO_PAGERANK, GXP_ALGO_PPR = 0, 1, 2, 3
+GXP_ALGO_SSSP, GXP_ALGO_CC, GXP_ALGO_PAGERANK, GXP_ALGO_PPR, GXP_ALGO_LP = 0, 1, 2, 3, 4
 GXP_GEN_RELAX, GXP_GEN_LABEL, GXP_GEN_CONTRIB = 0, 1, 2
-GXP_MERGE_MIN, GXP_MERGE_SUM = 0, 1
-GXP_APPLY_MIN, GXP_APPLY_PAGERANK = 0, 1
+GXP_MERGE_MIN, GXP_MERGE_SUM, GXP_MERGE_MODE = 0, 1, 2
+GXP_APPLY_MIN, GXP_APPLY_PAGERANK, GXP_APPLY_SET = 0, 1, 2
 GXP_FMT_COO, GXP_FMT_CSC, GXP_FMT_CSR = 0, 1, 2
 ALL_PARTS = 0xFFFFFFFF
 INF = 0xFFFFFFFF
@@ -34,6 +34,7 @@ TEMPLATES = {
     GXP_ALGO_CC: (GXP_GEN_LABEL, GXP_MERGE_MIN, GXP_APPLY_MIN),
     GXP_ALGO_PAGERANK: (GXP_GEN_CONTRIB, GXP_MERGE_SUM, GXP_APPLY_PAGERANK),
     GXP_ALGO_PPR: (GXP_GEN_CONTRIB, GXP_MERGE_SUM, GXP_APPLY_PAGERANK),
+    GXP_ALGO_LP: (GXP_GEN_LABEL, GXP_MERGE_MODE, GXP_APPLY_SET),
 }
 # serving
 GXP_QUERY_SSSP, GXP_QUERY_PPR = 0, 1
