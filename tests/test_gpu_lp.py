@@ -125,3 +125,37 @@ def test_template_checked():
         assert ei.value.code == gxp.GXP_E_UNSUPPORTED
         c.superstep()
         assert list(c.values()) == [0, 0]
+
+
+@pytest.mark.slow
+def test_wide_labels():
+    # more than 2^27 vertices: the (row, label) keys no longer fit 32 bits;
+    # cliques, a star and a hub among the ids above 2^27
+    n = (1 << 27) + 64
+    base = 1 << 27
+    rng = np.random.default_rng(8)
+    s, d = [], []
+    for c0 in (base, base + 20):
+        for i in range(8):
+            for j in range(8):
+                if i != j:
+                    s.append(c0 + i)
+                    d.append(c0 + j)
+    for leaf in range(base + 40, base + 50):
+        s += [leaf, base + 39]
+        d += [base + 39, leaf]
+    hub_src = rng.integers(base, n, 5000)
+    s += list(hub_src)
+    d += [base + 63] * len(hub_src)
+    src, dst = np.array(s, np.uint32), np.array(d, np.uint32)
+    with gxp.Context(0) as c:
+        c.create_graph(n, 1)
+        c.load_coo(src, dst)
+        c.begin(gxp.GXP_ALGO_LP)
+        lab = np.arange(n, dtype=np.uint32)
+        for t in range(4):
+            ref, ch_ref = oracle.lp_step(n, src, dst, lab)
+            assert c.superstep() == ch_ref, f"superstep {t + 1}"
+            got = c.values()
+            assert np.array_equal(got[base:], ref[base:]) and np.array_equal(got[:base], ref[:base])
+            lab = ref
