@@ -116,6 +116,40 @@ void gxs_er(uint64_t n, uint64_t m, uint64_t seed, uint32_t* src, uint32_t* dst)
     }
 }
 
+/*
+ * Clustered graph (a planted-partition model): the n vertices are cut into k
+ * contiguous blocks [n c / k, n (c+1) / k), the same cut as the default
+ * partitioning into k partitions. Pair i draws, for attempts j = 0..15 (five
+ * values 5(16i+j) .. 5(16i+j)+4): its block c = below(v0, k), whether it
+ * crosses to another block (unit(v1) < p_cross; the other block is
+ * (c + 1 + below(v2, k-1)) mod k), and its ends u = lo(c) + below(v3, size(c))
+ * and v = lo(c') + below(v4, size(c')); it keeps the first attempt with
+ * u != v (else v = (u + 1) mod n, as for gxs_er). Each pair is stored in both
+ * directions. Requires n >= 2k.
+ */
+void gxs_clustered(uint64_t n, uint32_t k, uint64_t m, double p_cross, uint64_t seed, uint32_t* src,
+                   uint32_t* dst) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)m; ++i) {
+        uint32_t u = 0, v = 0;
+        int ok = 0;
+        for (uint64_t j = 0; j < 16 && !ok; ++j) {
+            const uint64_t b = 5ULL * (16ULL * (uint64_t)i + j);
+            const uint32_t c = gxs_below(gxs_u64(seed, b), k);
+            const double x = (double)(gxs_u64(seed, b + 1) >> 11) * (1.0 / 9007199254740992.0);
+            const uint32_t c2 = (k > 1 && x < p_cross) ? (c + 1u + gxs_below(gxs_u64(seed, b + 2), k - 1u)) % k : c;
+            const uint64_t lo = n * c / k, hi = n * (c + 1) / k;
+            const uint64_t lo2 = n * c2 / k, hi2 = n * (c2 + 1) / k;
+            u = (uint32_t)(lo + gxs_below(gxs_u64(seed, b + 3), (uint32_t)(hi - lo)));
+            v = (uint32_t)(lo2 + gxs_below(gxs_u64(seed, b + 4), (uint32_t)(hi2 - lo2)));
+            ok = (u != v);
+        }
+        if (!ok) v = (uint32_t)((u + 1ULL) % n);
+        src[2 * i] = u;     dst[2 * i] = v;
+        src[2 * i + 1] = v; dst[2 * i + 1] = u;
+    }
+}
+
 /* Uniform integer weights in [lo, hi]: w[i] = lo + below(value i, hi-lo+1). */
 void gxs_weights(uint64_t n, uint32_t lo, uint32_t hi, uint64_t seed, uint32_t* w) {
     const uint32_t k = hi - lo + 1u;

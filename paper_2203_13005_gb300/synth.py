@@ -36,6 +36,7 @@ def _load():
         lib.gxs_fill_unit.argtypes = [u64, u64, u64, p]
         lib.gxs_rmat.argtypes = [u32, u64, dbl, dbl, dbl, u64, p, p]
         lib.gxs_er.argtypes = [u64, u64, u64, p, p]
+        lib.gxs_clustered.argtypes = [u64, u32, u64, dbl, u64, p, p]
         lib.gxs_weights.argtypes = [u64, u32, u32, u64, p]
         lib.gxs_sample.restype = u32
         lib.gxs_sample.argtypes = [u64, p, u32, u64, p, p]
@@ -85,6 +86,18 @@ def erdos_renyi(n: int, m_pairs: int, seed: int):
     src = np.empty(2 * m_pairs, dtype=np.uint32)
     dst = np.empty(2 * m_pairs, dtype=np.uint32)
     _load().gxs_er(n, m_pairs, seed & (2**64 - 1), _ptr(src), _ptr(dst))
+    return src, dst
+
+
+def clustered(n: int, blocks: int, m_pairs: int, p_cross: float, seed: int):
+    """Planted-partition pairs in `blocks` contiguous id blocks (the default
+    partition cut), a fraction p_cross of them joining two different blocks,
+    stored in both directions: 2*m_pairs directed edges."""
+    if blocks < 1 or n < 2 * blocks:
+        raise ValueError("clustered graph needs n >= 2 * blocks")
+    src = np.empty(2 * m_pairs, dtype=np.uint32)
+    dst = np.empty(2 * m_pairs, dtype=np.uint32)
+    _load().gxs_clustered(n, blocks, m_pairs, float(p_cross), seed & (2**64 - 1), _ptr(src), _ptr(dst))
     return src, dst
 
 
@@ -146,13 +159,14 @@ def omp_threads() -> int:
 class Workload:
     """A seeded graph workload: its name says what it is and how big."""
     name: str
-    kind: str            # "rmat" or "er"
+    kind: str            # "rmat", "er" or "clustered"
     scale: int           # log2 of the vertex count
     n_edges: int         # directed edges (ER: twice the pairs)
     seed: int
     w_lo: int = 0        # weights drawn in [w_lo, w_hi] when w_hi > 0
     w_hi: int = 0
     parts: int = 1       # contiguous dst-range partitions
+    p_cross: float = 0.0 # clustered: fraction of pairs joining two blocks (blocks = parts)
 
     @property
     def n_vertices(self) -> int:
@@ -163,6 +177,8 @@ class Workload:
             src, dst = rmat(self.scale, self.n_edges, self.seed)
         elif self.kind == "er":
             src, dst = erdos_renyi(self.n_vertices, self.n_edges // 2, self.seed)
+        elif self.kind == "clustered":
+            src, dst = clustered(self.n_vertices, self.parts, self.n_edges // 2, self.p_cross, self.seed)
         else:
             raise ValueError(self.kind)
         w = weights(self.n_edges, self.w_lo, self.w_hi, self.seed) if self.w_hi else None
@@ -179,6 +195,11 @@ class Workload:
 SSSP_RMAT16 = Workload("sssp_rmat16", "rmat", 16, 1 << 20, 0x67700001, 1, 100)
 PAGERANK_RMAT22 = Workload("pagerank_rmat22", "rmat", 22, 1 << 26, 0x67700002)
 CC_ER24_P8 = Workload("cc_er24_8parts", "er", 24, 1 << 28, 0x67700003, parts=8)
+# the same size, but 8 communities on the 8 partitions with one pair in
+# 100,000 crossing between them, weighted: the graph on which sync skipping
+# triggers (SSSP, as in the paper's skipping experiment)
+SSSP_CLUSTERED24_P8 = Workload("sssp_clustered24_8parts", "clustered", 24, 1 << 28, 0x67700007, 1, 100, parts=8,
+                               p_cross=1e-5)
 MSSSP_RMAT24 = Workload("msssp64_rmat24", "rmat", 24, 1 << 28, 0x67700004, 1, 255)
 # the SSSP recipe at the PageRank graph's size: where a pull sweep costs
 # about a millisecond and the sparse supersteps are worth pushing

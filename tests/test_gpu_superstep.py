@@ -135,6 +135,36 @@ def test_cc_partitions_sync_trace(parts, bounds, tile, hub):
             assert st["syncs_done"] + st["syncs_skipped"] == steps_ref
 
 
+@pytest.mark.parametrize("p_cross", [1e-3, 1e-4])
+def test_sssp_clustered_graph_skips_syncs(p_cross):
+    # communities on the partitions with few pairs between them: the
+    # supersteps that change no boundary vertex skip their exchange, and the
+    # uploads and skip flags follow the sync oracle superstep for superstep
+    import dataclasses
+    wl = dataclasses.replace(synth.SSSP_CLUSTERED24_P8.scaled(14), p_cross=p_cross)
+    src, dst, w = wl.edges()
+    n = wl.n_vertices
+    b = [n * p // wl.parts for p in range(wl.parts + 1)]
+    d_ref, steps_ref, trace = osync.min_label_sync_trace(n, src, dst, b, "sssp", w=w, source=0)
+    assert sum(s for _, s in trace) >= 2   # skipping triggers on this graph
+    with _ctx(n, wl.parts, None) as c:
+        c.load_coo(src, dst, w)
+        c.begin(gxp.GXP_ALGO_SSSP, 0)
+        for t in range(steps_ref):
+            c.superstep()
+            uploads, skipped = trace[t]
+            for p in range(wl.parts):
+                ids, vals, sk = c.sync(p)
+                assert sk == skipped, (t, p)
+                assert np.array_equal(ids, uploads[p][0]), (t, p)
+                assert np.array_equal(vals, uploads[p][1]), (t, p)
+        assert np.array_equal(c.values(), d_ref)
+        assert c.run(gxp.GXP_ALGO_SSSP, 0) == steps_ref
+        st = c.stats()
+        assert st["syncs_skipped"] == sum(s for _, s in trace)
+        assert st["syncs_done"] + st["syncs_skipped"] == steps_ref
+
+
 def test_cc_disconnected_partitions_always_skip():
     a = [(u, v) for u in range(4) for v in range(4) if u != v]
     e = np.array(a + [(u + 4, v + 4) for u, v in a], dtype=np.uint32)

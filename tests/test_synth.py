@@ -97,3 +97,26 @@ def test_workload_sizes():
     assert synth.MSSSP_RMAT24.n_vertices == 16777216 and synth.MSSSP_RMAT24.w_hi == 255
     small = w.scaled(8)
     assert small.n_vertices == 256 and small.n_edges == 4096
+
+
+def test_clustered_blocks_and_crossing_fraction():
+    n, k, m, pc = 4000, 8, 50000, 0.01
+    src, dst = synth.clustered(n, k, m, pc, 0x1234)
+    assert len(src) == 2 * m
+    # pairs are stored in both directions, without self-loops
+    assert np.array_equal(src[0::2], dst[1::2]) and np.array_equal(dst[0::2], src[1::2])
+    assert np.all(src != dst) and src.max() < n
+    block = lambda x: (x.astype(np.int64) * k) // n   # the default partition cut
+    cross = (block(src) != block(dst)).mean()
+    assert abs(cross - pc) < 0.003
+    # every block is used, about evenly
+    counts = np.bincount(block(src[0::2]), minlength=k)
+    assert counts.min() > 0.8 * m / k
+    # counter-based: the same seed gives the same graph, another seed another
+    s2, d2 = synth.clustered(n, k, m, pc, 0x1234)
+    assert np.array_equal(src, s2) and np.array_equal(dst, d2)
+    s3, _ = synth.clustered(n, k, m, pc, 0x1235)
+    assert not np.array_equal(src, s3)
+    # no crossing at all when p_cross = 0
+    s0, d0 = synth.clustered(n, k, 5000, 0.0, 7)
+    assert np.all(block(s0) == block(d0))
