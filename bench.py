@@ -272,21 +272,30 @@ def run_sssp(args):
     k_us = statistics.mean(superstep_us(cp))
     cp.close()
     bytes_sweep = 12 * m + 12 * n + n // 4   # src + w + gathered value per edge; col_ptr, d read, d write, bitmap
-    # end to end: COO from host memory -> load -> run -> distances back
-    out = np.empty(n, dtype=np.uint32)
+    # end to end through the public API with host buffers: weighted CSC from
+    # pinned host memory -> load (device build) -> run -> distances back into
+    # pinned host memory
+    order = np.argsort(dst, kind="stable")
+    col_ptr = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+    np.cumsum(np.bincount(dst, minlength=n), out=col_ptr.numpy()[1:])
+    csc_src = torch.from_numpy(np.ascontiguousarray(src[order]).view(np.int32)).pin_memory()
+    csc_w = torch.from_numpy(np.ascontiguousarray(w[order]).view(np.int32)).pin_memory()
+    del order
+    out = torch.empty(n, dtype=torch.int32).pin_memory()
     e2e = []
+    c2 = gxp.Context(0, direction=direction, push_div=args.push_div)
+    c2.set_stream(stream.cuda_stream)
     for i in range(4):
         torch.cuda.synchronize()
         c0 = time.perf_counter()
-        c2 = gxp.Context(0, direction=direction, push_div=args.push_div)
         c2.create_graph(n, 1)
-        c2.load_coo(src, dst, w)
+        c2.load_partition(0, gxp.GXP_FMT_CSC, m, col_ptr, csc_src, csc_w)
         c2.run(gxp.GXP_ALGO_SSSP, 0)
         c2.values(out=out)
         torch.cuda.synchronize()
         if i:
             e2e.append(time.perf_counter() - c0)
-        c2.close()
+    c2.close()
     e2e_s = statistics.median(e2e)
     peaks = measured_peaks()
     line = {
@@ -307,7 +316,7 @@ def run_sssp(args):
                      "unit": "GB/s", "frac": bytes_sweep / (k_us * 1e-6) / 1e9 / peaks["hbm_gbs"], "traffic": None,
                      "peak_source": peaks["source"], "kernel": "k_sell<SSSP>", "avg_launch_us": k_us,
                      "algorithmic_bytes_per_launch": bytes_sweep},
-        "e2e": {"value": steps * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 12 * m,
+        "e2e": {"value": steps * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 8 * (n + 1) + 8 * m,
                 "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_s * 1e3},
         "clocks": clk.summary(),
     }
@@ -324,18 +333,19 @@ def run_cc(args):
     wl = synth.CC_ER24_P8
     src, dst, _ = wl.edges()
     n, m = wl.n_vertices, wl.n_edges
-    ctx = gxp.Context(0)
+    ctx = gxp.Context(0, cache_slots=args.cache_slots)
     ctx.create_graph(n, wl.parts)
     ctx.load_coo(src, dst)
     del src, dst
     times = []
     steps = 0
-    for r in range(max(2, args.steps)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        steps = ctx.run(gxp.GXP_ALGO_CC)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
+    with ClockSampler(0) as clk:
+        for r in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = ctx.run(gxp.GXP_ALGO_CC)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
     st = ctx.stats()
     sec = min(times[1:]) if len(times) > 1 else times[0]
     line = {
@@ -343,9 +353,11 @@ def run_cc(args):
         "steps": len(times) - 1, "warmup": 1, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl.name, "vertices": n, "edges": m, "partitions": wl.parts,
-                   "step": "one run to convergence incl. per-superstep host checks"},
+                   "cache_slots": args.cache_slots,
+                   "step": "one run to convergence incl. per-chunk host checks"},
         "supersteps": steps, "syncs_done": st["syncs_done"], "syncs_skipped": st["syncs_skipped"],
-        "sync_pairs": st["sync_pairs"], "last_superstep_ms": st["last_superstep_ms"],
+        "sync_pairs": st["sync_pairs"], "cache_downloads": st["cache_downloads"],
+        "last_superstep_ms": st["last_superstep_ms"], "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -684,6 +696,8 @@ def main():
                              synth.CC_ER24_P8.name, "lp_er24_8parts", synth.SSSP_CLUSTERED24_P8.name,
                              "serve"],
                     help="extra workloads print their own line; the default is the headline")
+    ap.add_argument("--cache-slots", type=int, default=0,
+                    help="cc_er24_8parts: cached remote vertices per partition (0 = all, 4294967295 = none)")
     ap.add_argument("--lp-parts", type=int, default=8, help="lp_er24_8parts: partitions (1 = one, renumbered)")
     ap.add_argument("--lp-scale", type=int, default=24, help="lp_er24_8parts: log2 vertices (smaller for profiling)")
     ap.add_argument("--direction", default="auto", choices=sorted(DIRECTIONS),

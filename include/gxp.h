@@ -117,8 +117,19 @@ typedef struct gxp_config {
                                    Graphs of several partitions always pull. */
     uint32_t push_div;          /* GXP_DIR_AUTO pushes a superstep when (frontier out-edges +
                                    frontier items) * push_div <= the graph's edges; 0 = 8 */
-    uint32_t reserved[4];
+    uint32_t cache_slots;       /* synchronization caching (Section III-B2) with a budget: remote
+                                   vertices each partition keeps cached between supersteps.
+                                   0 = all of them; GXP_CACHE_NONE = none. The kept ones are those
+                                   read by the most in-edges (the steady state of the LRU weight,
+                                   which rises with use and decays per iteration, when every
+                                   superstep reads every in-edge); cached copies are refreshed by
+                                   the lazy upload of changed boundary vertices, the others are
+                                   downloaded again from their owners after every superstep
+                                   (gxp_stats.cache_downloads). Values are the same either way. */
+    uint32_t reserved[3];
 } gxp_config;
+
+#define GXP_CACHE_NONE 0xFFFFFFFFu
 
 /* Direction of the min-label supersteps (SSSP, CC). Both give the same values
  * and the same changed sets after every superstep (Jacobi order):
@@ -153,7 +164,9 @@ typedef struct gxp_stats {
     double   last_superstep_ms;     /* device time of the last superstep incl. its sync */
     uint64_t device_bytes;          /* device memory held by the context */
     uint64_t push_supersteps;       /* of the supersteps, those run in push direction */
-    uint64_t reserved[5];
+    uint64_t cache_downloads;       /* remote values downloaded because they were not cached
+                                       (gxp_config.cache_slots), summed over supersteps */
+    uint64_t reserved[4];
 } gxp_stats;
 
 /* ------------------------------------------------------------ lifecycle -- */

@@ -96,6 +96,8 @@ void Engine::free_graph_device() {
     d_ctl_ = nullptr;
     h_old2new_.clear();
     lp_ = LpLists{};
+    d_pull_list_ = d_download_list_ = nullptr;
+    n_pull_ = n_download_ = 0;
     for (void* p : graph_allocs_) cudaFree(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
@@ -658,6 +660,35 @@ void Engine::build_caches() {
     cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * words, stream_), "memset");
     cuda_check(cudaMemsetAsync(d_part_counts_, 0, 4 * n_parts_, stream_), "memset");
     cuda_check(cudaMemsetAsync(d_done_ctr_, 0, 4, stream_), "memset");
+    // caching under a budget: each partition keeps the cache_slots copies
+    // read by the most in-edges (ties: lower id); the rest are downloaded
+    // again after every superstep
+    d_pull_list_ = d_download_list_ = nullptr;
+    n_pull_ = n_download_ = 0;
+    if (cfg_.cache_slots != 0) {
+        std::vector<uint32_t> pull, download;
+        for (auto& hp : parts_) {
+            const uint32_t G = (uint32_t)hp.ghost_gid.size();
+            const uint32_t keep = cfg_.cache_slots == GXP_CACHE_NONE ? 0u : std::min(G, cfg_.cache_slots);
+            std::vector<uint32_t> reads(G, 0), order(G);
+            for (uint32_t u : hp.src)
+                if (u >= hp.n_own) ++reads[u - hp.n_own];
+            for (uint32_t i = 0; i < G; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return reads[x] > reads[y]; });
+            std::vector<uint8_t> kept(G, 0);
+            for (uint32_t i = 0; i < keep; ++i) kept[order[i]] = 1;
+            for (uint32_t i = 0; i < G; ++i) (kept[i] ? pull : download).push_back(hp.ghost_base + i);
+        }
+        n_pull_ = (uint32_t)pull.size();
+        n_download_ = (uint32_t)download.size();
+        d_pull_list_ = (uint32_t*)dalloc(4 * std::max<size_t>(pull.size(), 1));
+        d_download_list_ = (uint32_t*)dalloc(4 * std::max<size_t>(download.size(), 1));
+        if (!pull.empty())
+            cuda_check(cudaMemcpy(d_pull_list_, pull.data(), 4 * pull.size(), cudaMemcpyHostToDevice), "upload");
+        if (!download.empty())
+            cuda_check(cudaMemcpy(d_download_list_, download.data(), 4 * download.size(), cudaMemcpyHostToDevice),
+                       "upload");
+    }
     // the host copies must outlive the async uploads
     cuda_check(cudaStreamSynchronize(stream_), "upload caches");
 }
@@ -813,6 +844,8 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         s.ghost_gid = d_ghost_gid_;
         s.n_ghost = n_ghost_total_;
         s.ghost = d_ghost_;
+        s.pull_list = d_pull_list_;
+        s.n_pull = d_pull_list_ ? n_pull_ : n_ghost_total_;
         s.gdq_ids = d_gdq_ids_;
         s.gdq_vals = d_gdq_vals_;
         s.gdq_base = d_gdq_base_;
@@ -823,6 +856,9 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         s.blocks_x = sync_blocks_x_;
         s.stats_out = d_stats_ + (step_ + 1) % kStatRing;
         cuda_check(launch_sync(s, max_words_, stream_), "sync kernels");
+        if (n_download_)
+            cuda_check(launch_download(d_download_list_, n_download_, d_ghost_gid_, d_own_[nx], d_ghost_, stream_),
+                       "download uncached copies");
         cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)n_vertices_ + 31) / 32 + 2), stream_), "memset");
     }
     cuda_check(cudaEventRecord(ev_b_, stream_), "event");
@@ -865,6 +901,7 @@ uint64_t Engine::account(bool stop_at_quiet, bool ring_copied) {
             st_.last_l1_delta = fx_to_double(l1);
         }
         if (n_parts_ > 1) {
+            st_.cache_downloads += n_download_;
             st_.last_boundary_changed = s.boundary_changed;
             st_.sync_pairs += s.boundary_changed;
             if (s.skipped) st_.syncs_skipped++;

@@ -132,6 +132,9 @@ private:
     uint64_t* d_gdq_base_ = nullptr;
     uint32_t *d_block_counts_ = nullptr, *d_block_offsets_ = nullptr, *d_part_counts_ = nullptr;
     uint32_t* d_done_ctr_ = nullptr;
+    uint32_t* d_pull_list_ = nullptr;       // cache budget: the kept copies, or nullptr = all
+    uint32_t* d_download_list_ = nullptr;   // and the ones downloaded every superstep
+    uint32_t n_pull_ = 0, n_download_ = 0;
     uint32_t sync_blocks_x_ = 0, max_words_ = 0;
     StepStats* d_stats_ = nullptr;
     uint32_t* d_err_ = nullptr;

@@ -282,11 +282,23 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
 // new value. Each partition's cache list is sorted by global id, so a thread
 // per cached copy reads the changed bits and the owners' values in
 // ascending order and writes the cache sequentially.
+// With a cache budget only the kept copies (pull_list) are refreshed here.
 __global__ void k_sync_pull(const SyncArgs a) {
     if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_ghost; g += gridDim.x * blockDim.x) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_pull; i += gridDim.x * blockDim.x) {
+        const uint32_t g = a.pull_list ? a.pull_list[i] : i;
         const uint32_t gid = a.ghost_gid[g];
         if ((a.changed_bits[gid >> 5] >> (gid & 31u)) & 1u) a.ghost[g] = a.own_val[gid];
+    }
+}
+
+// Copies a partition does not keep cached: downloaded again from their
+// owners after every superstep, exchange skipped or not.
+__global__ void k_download(const uint32_t* __restrict__ list, uint32_t n, const uint32_t* __restrict__ gid,
+                           const uint32_t* __restrict__ own, uint32_t* __restrict__ ghost) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t g = list[i];
+        ghost[g] = own[gid[g]];
     }
 }
 
@@ -353,8 +365,15 @@ cudaError_t launch_sync(const SyncArgs& a, uint32_t, cudaStream_t s) {
     dim3 grid(a.blocks_x, a.n_parts);
     k_sync_count<<<grid, kSyncBlock, 0, s>>>(a);
     k_sync_write<<<grid, kSyncBlock, 0, s>>>(a);
-    if (a.n_ghost)
-        k_sync_pull<<<std::min<uint32_t>((a.n_ghost + 255) / 256, 152u * 16), 256, 0, s>>>(a);
+    if (a.n_pull)
+        k_sync_pull<<<std::min<uint32_t>((a.n_pull + 255) / 256, 152u * 16), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_download(const uint32_t* list, uint32_t n, const uint32_t* ghost_gid, const uint32_t* own_val,
+                            uint32_t* ghost, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_download<<<std::min<uint32_t>((n + 255) / 256, 152u * 16), 256, 0, s>>>(list, n, ghost_gid, own_val, ghost);
     return cudaGetLastError();
 }
 

@@ -310,6 +310,8 @@ struct SyncArgs {
     const uint32_t* ghost_gid;        // [n_ghost] global id of each cached copy (sorted per partition)
     uint32_t n_ghost;                 // cached copies over all partitions
     uint32_t* ghost;                  // [n_ghost] caches to update
+    const uint32_t* pull_list;        // the cached copies (ghost indices, ascending), or nullptr = all
+    uint32_t n_pull;
     uint32_t* gdq_ids;                // [sum of boundary counts]
     uint32_t* gdq_vals;
     const uint64_t* gdq_base;         // [n_parts] offset of each partition's gdq
@@ -356,6 +358,10 @@ cudaError_t launch_run_control(RunCtl* ctl, const StepStats* ring, cudaGraphCond
 size_t superstep_smem_bytes(Algo a, uint32_t max_items);
 
 cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);
+// copies not kept in a partition's cache: ghost[i] = own_val[ghost_gid[i]]
+// for every ghost index i of list[0 .. n)
+cudaError_t launch_download(const uint32_t* list, uint32_t n, const uint32_t* ghost_gid, const uint32_t* own_val,
+                            uint32_t* ghost, cudaStream_t s);
 
 // push direction (frontier.cu)
 struct RowSource;

@@ -40,13 +40,14 @@ TEMPLATES = {
 GXP_QUERY_SSSP, GXP_QUERY_PPR = 0, 1
 GXP_QUERY_QUEUED, GXP_QUERY_RUNNING, GXP_QUERY_DONE, GXP_QUERY_FAILED = 0, 1, 2, 3
 GXP_DIR_AUTO, GXP_DIR_PULL, GXP_DIR_PUSH = 0, 1, 2
+GXP_CACHE_NONE = 0xFFFFFFFF
 
 
 class gxp_config(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("tile_items", C.c_uint32), ("hub_items", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("check_bounds", C.c_uint32), ("max_slots", C.c_uint32),
                 ("pipeline_depth", C.c_uint32), ("keep_ids", C.c_uint32), ("direction", C.c_uint32),
-                ("push_div", C.c_uint32), ("reserved", C.c_uint32 * 4)]
+                ("push_div", C.c_uint32), ("cache_slots", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class gxp_stats(C.Structure):
@@ -54,7 +55,8 @@ class gxp_stats(C.Structure):
                 ("last_boundary_changed", C.c_uint64), ("syncs_done", C.c_uint64),
                 ("syncs_skipped", C.c_uint64), ("sync_pairs", C.c_uint64), ("last_l1_delta", C.c_double),
                 ("last_dangling", C.c_double), ("last_superstep_ms", C.c_double),
-                ("device_bytes", C.c_uint64), ("push_supersteps", C.c_uint64), ("reserved", C.c_uint64 * 5)]
+                ("device_bytes", C.c_uint64), ("push_supersteps", C.c_uint64), ("cache_downloads", C.c_uint64),
+                ("reserved", C.c_uint64 * 4)]
 
 
 # (name, restype, argtypes) of every exported symbol
@@ -168,12 +170,12 @@ class Context:
 
     def __init__(self, device: int = 0, tile_items: int = 0, hub_items: int = 0,
                  check_bounds: bool = False, timeout_ns: int = 0, mem_budget: int = 0, keep_ids: bool = False,
-                 direction: int = GXP_DIR_AUTO, push_div: int = 0):
+                 direction: int = GXP_DIR_AUTO, push_div: int = 0, cache_slots: int = 0):
         self.lib = load()
         cfg = gxp_config()
         self.lib.gxp_config_default(C.byref(cfg))
         cfg.tile_items, cfg.hub_items, cfg.keep_ids = tile_items, hub_items, int(keep_ids)
-        cfg.direction, cfg.push_div = direction, push_div
+        cfg.direction, cfg.push_div, cfg.cache_slots = direction, push_div, cache_slots
         cfg.check_bounds, cfg.timeout_ns, cfg.mem_budget = int(check_bounds), timeout_ns, mem_budget
         h = C.c_void_p()
         rc = self.lib.gxp_init(device, C.byref(cfg), C.byref(h))
