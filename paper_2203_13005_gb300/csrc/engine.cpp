@@ -814,10 +814,16 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         l.windows = lp_.d_windows;
         l.n_windows = lp_.n_windows;
         l.row_g = lp_.d_row_g;
+        l.warp_rows = lp_.d_warp_rows;
+        l.n_warp_rows = lp_.n_warp_rows;
         l.chunks = lp_.d_chunks;
         l.n_chunks = lp_.n_chunks;
         l.hubs = lp_.d_hubs;
         l.n_hubs = lp_.n_hubs;
+        l.segments = lp_.d_segments;
+        l.n_segments = lp_.n_segments;
+        l.hub_best = lp_.d_hub_best;
+        l.seg_used = lp_.d_seg_used;
         l.keys = lp_.d_keys;
         l.counts = lp_.d_counts;
         l.own_cur = d_own_[cur_];
@@ -963,14 +969,15 @@ void Engine::seed_frontier(uint32_t source_int) {
 // Row lists of label propagation, by in-degree class (host-built once per
 // graph from the partitions' offsets): 1..kLpSmall in-edges (packed into
 // warp windows of adjacent edges, in CSC order), up to kLpChunk, and hub rows
-// cut into chunks of kLpChunk with a hash table each.
+// cut into chunks of kLpChunk with a hash table each, cut into segments.
 void Engine::build_lp() {
     if (lp_.ready) return;
     std::vector<LpPart> parts(n_parts_);
-    std::vector<LpRow> chunks;
+    std::vector<LpRow> chunks, warp_rows;
     std::vector<LpWindow> windows;
     std::vector<uint32_t> row_g;
     std::vector<LpHub> hubs;
+    std::vector<LpSegment> segments;
     uint64_t table_slots = 0;
     auto add_row = [&](uint32_t g, uint32_t p, uint32_t e0, uint32_t deg) {
         if (deg == 0) return;
@@ -986,13 +993,18 @@ void Engine::build_lp() {
             w->starts |= 1u << at;
             w->n_part += deg;
             row_g.push_back(g);
+        } else if (deg <= kLpWarpRow) {
+            warp_rows.push_back(LpRow{g, p, e0, deg, kInf, {0, 0, 0}});
         } else if (deg <= kLpChunk) {
             chunks.push_back(LpRow{g, p, e0, deg, kInf, {0, 0, 0}});
         } else {
             uint32_t lg = 1;
             while ((1ull << lg) < 2ull * deg) ++lg;
             const uint32_t h = (uint32_t)hubs.size();
-            hubs.push_back(LpHub{g, lg, table_slots});
+            hubs.push_back(LpHub{g, lg, table_slots, (uint32_t)segments.size(), 0});
+            for (uint64_t s0 = 0; s0 < (1ull << lg); s0 += kLpSegment)
+                segments.push_back(LpSegment{h, (uint32_t)std::min<uint64_t>(kLpSegment, (1ull << lg) - s0),
+                                             table_slots + s0});
             table_slots += 1ull << lg;
             for (uint32_t c = 0; c < deg; c += kLpChunk)
                 chunks.push_back(LpRow{g, p, e0 + c, std::min(kLpChunk, deg - c), h, {0, 0, 0}});
@@ -1024,10 +1036,18 @@ void Engine::build_lp() {
     lp_.d_windows = (LpWindow*)upload(windows.data(), sizeof(LpWindow) * windows.size());
     lp_.d_row_g = (uint32_t*)upload(row_g.data(), 4 * row_g.size());
     lp_.d_chunks = (LpRow*)upload(chunks.data(), sizeof(LpRow) * chunks.size());
+    lp_.d_warp_rows = (LpRow*)upload(warp_rows.data(), sizeof(LpRow) * warp_rows.size());
+    lp_.n_warp_rows = (uint32_t)warp_rows.size();
     lp_.d_hubs = (LpHub*)upload(hubs.data(), sizeof(LpHub) * hubs.size());
     lp_.n_windows = (uint32_t)windows.size();
     lp_.n_chunks = (uint32_t)chunks.size();
     lp_.n_hubs = (uint32_t)hubs.size();
+    lp_.d_segments = (LpSegment*)upload(segments.data(), sizeof(LpSegment) * segments.size());
+    lp_.n_segments = (uint32_t)segments.size();
+    lp_.d_seg_used = (uint32_t*)dalloc(4 * std::max<size_t>(segments.size(), 1));
+    cuda_check(cudaMemsetAsync(lp_.d_seg_used, 0, 4 * std::max<size_t>(segments.size(), 1), stream_), "memset");
+    lp_.d_hub_best = (unsigned long long*)dalloc(8 * std::max<size_t>(hubs.size(), 1));
+    cuda_check(cudaMemsetAsync(lp_.d_hub_best, 0, 8 * std::max<size_t>(hubs.size(), 1), stream_), "memset");
     lp_.d_keys = (uint32_t*)dalloc(4 * std::max<uint64_t>(table_slots, 1));
     lp_.d_counts = (uint32_t*)dalloc(4 * std::max<uint64_t>(table_slots, 1));
     cuda_check(cudaMemsetAsync(lp_.d_keys, 0xFF, 4 * std::max<uint64_t>(table_slots, 1), stream_), "memset");

@@ -187,8 +187,13 @@ private:
         LpWindow* d_windows = nullptr;
         uint32_t* d_row_g = nullptr;
         LpRow* d_chunks = nullptr;
+        LpRow* d_warp_rows = nullptr;
+        uint32_t n_warp_rows = 0;
         LpHub* d_hubs = nullptr;
-        uint32_t n_windows = 0, n_chunks = 0, n_hubs = 0;
+        LpSegment* d_segments = nullptr;
+        unsigned long long* d_hub_best = nullptr;
+        uint32_t* d_seg_used = nullptr;
+        uint32_t n_windows = 0, n_chunks = 0, n_hubs = 0, n_segments = 0;
         uint32_t* d_keys = nullptr;
         uint32_t* d_counts = nullptr;
     } lp_;

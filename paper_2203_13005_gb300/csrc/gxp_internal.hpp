@@ -245,11 +245,16 @@ struct PprArgs {
 };
 
 // Mode-label propagation (lp.cu). Rows are listed by in-degree class:
-// 1..32 in-edges (packed into warp windows), up to kLpChunk (a CTA per row), more (a
-// hub: chunks of kLpChunk counted into a hash table of its own, then one CTA
-// takes the mode). Rows without in-edges keep their labels and are not listed.
+// 1..32 in-edges (packed into warp windows), up to kLpWarpRow (a warp per
+// row) and up to kLpChunk (a CTA per row), both counting in shared-memory
+// hash tables, more (a hub: chunks of kLpChunk
+// counted the same way and added into a global hash table of its own, which
+// segments of kLpSegment slots then reduce). Rows without in-edges keep their
+// labels and are not listed.
 constexpr uint32_t kLpSmall = 32;
-constexpr uint32_t kLpChunk = 4096;
+constexpr uint32_t kLpWarpRow = 256;   // rows up to this many in-edges: a warp each
+constexpr uint32_t kLpChunk = 2048;
+constexpr uint32_t kLpSegment = 4096;
 struct LpPart {                 // where a row's in-edges and their labels are
     const uint32_t* src;        // CSC sources (local ids, or input ids with src_map)
     const uint32_t* src_map;    // single renumbered partition: input id -> value index
@@ -276,18 +281,31 @@ struct LpHub {
     uint32_t g;
     uint32_t log2_size;         // table slots = 2^log2_size >= 2 in-degree
     uint64_t table;             // first slot
+    uint32_t seg0;              // its first segment (segment i covers slots [i kLpSegment, ...) of the table)
+    uint32_t pad;
+};
+struct LpSegment {              // kLpSegment slots (or fewer) of one hub's table
+    uint32_t hub;
+    uint32_t n;
+    uint64_t slot0;
 };
 struct LpArgs {
     const LpPart* parts;
     const LpWindow* windows;    // rows of 1..kLpSmall in-edges
     uint32_t n_windows;
     const uint32_t* row_g;      // their value indices
-    const LpRow* chunks;        // kLpSmall < in-edges <= kLpChunk (hub = kInf), and hub chunks
+    const LpRow* warp_rows;     // kLpSmall < in-edges <= kLpWarpRow
+    uint32_t n_warp_rows;
+    const LpRow* chunks;        // kLpWarpRow < in-edges <= kLpChunk (hub = kInf), and hub chunks
     uint32_t n_chunks;
     const LpHub* hubs;
     uint32_t n_hubs;
+    const LpSegment* segments;  // the hub tables cut into segments
+    uint32_t n_segments;
     uint32_t* keys;             // hub tables: label per slot (kInf = empty) ...
     uint32_t* counts;           // ... and its count; left empty after each superstep
+    unsigned long long* hub_best;   // [n_hubs] best (count, -label) over the segments; zeroed after use
+    uint32_t* seg_used;             // [n_segments] 1 once a label took a slot of the segment; cleared after use
     const uint32_t* own_cur;
     uint32_t* own_nxt;
     const uint32_t* ghost;

@@ -11,12 +11,17 @@
 //    (largest count, then smallest label with it) give the row's mode. No
 //    sort (sorting each row in its lane cost about 2,000 instructions per 32
 //    rows, every lane waiting on the longest row);
-//  * rows with 33..4096 in-edges: a CTA per row gathers the labels into
-//    shared memory, sorts them (bitonic), finds each run's start with a
-//    block max-scan of run starts, and reduces (count, -label) at run ends;
-//  * hub rows (more in-edges): each chunk of 4096 is sorted the same way and
-//    its runs are added into the hub's hash table (open addressing, at most
-//    half full); a CTA per hub then reduces its table and empties it.
+//  * rows with 33..256 in-edges: a warp per row, 257..2048: a CTA per row;
+//    both count the labels in a shared-memory hash table (2^k >= 2 in-degree
+//    slots, open addressing; equal labels of a warp added once) and reduce
+//    (count, -label) over it (sorting each row with a bitonic network in a
+//    CTA, up to 78 barriers a row, ran 3x slower on R-MAT);
+//  * hub rows (more in-edges): each chunk of 2048 is counted the same way
+//    and its counts are added into the hub's global hash table; segments of
+//    4096 slots that a label entered this superstep, spread over all CTAs,
+//    reduce the tables into a 64-bit maximum per hub and empty them (once
+//    labels settle, most segments stay empty and are skipped), and a thread
+//    per hub applies.
 #include "frontier.cuh"
 
 #include <algorithm>
@@ -140,125 +145,185 @@ __global__ void __launch_bounds__(kLpBlock) k_lp_windows(const LpArgs a) {
     if (lane == 0) lp_count(a, n_changed, w0);
 }
 
-// add `count` occurrences of `label` to a hub's table (open addressing with
-// linear probing; the table is at most half full, so a slot is always found)
-__device__ __forceinline__ void lp_table_add(uint32_t* keys, uint32_t* counts, uint32_t log2_size, uint32_t label,
-                                             uint32_t count) {
+// add `count` occurrences of `label` to a hash table of 2^log2_size slots
+// (open addressing with linear probing; the table holds at most half as many
+// labels as slots, so a slot is always found). Works on global and on shared
+// memory tables.
+__device__ __forceinline__ uint32_t lp_table_add(uint32_t* keys, uint32_t* counts, uint32_t log2_size,
+                                                 uint32_t label, uint32_t count) {
     const uint32_t mask = (1u << log2_size) - 1u;
     uint32_t slot = (label * 0x9E3779B1u) >> (32u - log2_size);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const uint32_t k = atomicCAS(keys + slot, kInf, label);
         if (k == kInf || k == label) {
             atomicAdd(counts + slot, count);
-            return;
+            return slot;
         }
         slot = (slot + 1u) & mask;
     }
+    return 0u;
 }
 
-__global__ void __launch_bounds__(kLpBlock) k_lp_chunks(const LpArgs a) {
-    __shared__ uint32_t lab[kLpChunk];
-    __shared__ uint32_t s_warp[kLpWarps];
-    __shared__ unsigned long long s_best[kLpWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    unsigned long long b = 0ull;
+    for (int w = 0; w < kLpWarps; ++w) b = max(b, s_red[w]);
+    return b;
+}
+
+// Rows of 33..256 in-edges, a warp each (8 rows in flight per CTA): the
+// warp counts the row's labels in its own shared-memory hash table (2^k >=
+// 2n slots, at most 512), takes the largest (count, -label) over the table
+// with a warp reduction and empties it.
+__global__ void __launch_bounds__(kLpBlock) k_lp_warp_rows(const LpArgs a) {
+    __shared__ uint32_t t_key[kLpWarps][2 * kLpWarpRow], t_cnt[kLpWarps][2 * kLpWarpRow];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lp_quiet(a, lane)) return;
+    uint32_t* keys = t_key[warp];
+    uint32_t* cnts = t_cnt[warp];
+    for (uint32_t i = (uint32_t)lane; i < 2 * kLpWarpRow; i += 32u) {
+        keys[i] = kInf;
+        cnts[i] = 0u;
+    }
+    __syncwarp();
+    const uint64_t w0 = ((uint64_t)blockIdx.x * kLpBlock + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * kLpBlock) >> 5;
+    uint32_t n_changed = 0;
+    for (uint64_t ri = w0; ri < a.n_warp_rows; ri += nw) {
+        const LpRow r = a.warp_rows[ri];
+        const LpPart P = a.parts[r.part];
+        const uint32_t n = r.n;
+        uint32_t lg = 1;
+        while ((1u << lg) < 2u * n) ++lg;
+        for (uint32_t i0 = 0; i0 < n; i0 += 32u * kGatherUnroll) {
+            uint32_t sv[kGatherUnroll], lab[kGatherUnroll];
+#pragma unroll
+            for (int q = 0; q < kGatherUnroll; ++q) {
+                const uint32_t i = i0 + 32u * q + (uint32_t)lane;
+                sv[q] = i < n ? __ldg(P.src + r.e0 + i) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < kGatherUnroll; ++q) {
+                const uint32_t i = i0 + 32u * q + (uint32_t)lane;
+                lab[q] = i < n ? lp_label(a, P, sv[q]) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < kGatherUnroll; ++q) {
+                const bool has = i0 + 32u * q + (uint32_t)lane < n;
+                const unsigned act = __ballot_sync(kFull, has);
+                if (has) {
+                    const unsigned grp = __match_any_sync(act, lab[q]);
+                    if (lane == __ffs(grp) - 1) lp_table_add(keys, cnts, lg, lab[q], (uint32_t)__popc(grp));
+                }
+            }
+        }
+        __syncwarp();
+        unsigned long long best = 0ull;
+        for (uint32_t i = (uint32_t)lane; i < (1u << lg); i += 32u) {
+            const uint32_t k = keys[i];
+            if (k != kInf) {
+                best = max(best, mode_key(cnts[i], k));
+                keys[i] = kInf;
+                cnts[i] = 0u;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(kFull, best, o));
+        if (lane == 0 && lp_apply(a, r.g, ~(uint32_t)best)) ++n_changed;
+        __syncwarp();
+    }
+    if (lane == 0) lp_count(a, n_changed, w0);
+}
+
+// Rows of 257..2048 in-edges (hub = kInf) and chunks of 2048 of hub rows: the
+// CTA counts the labels in a shared-memory hash table (2^k >= 2n slots),
+// then takes the mode (a row) or adds its counts into the hub's table.
+__global__ void __launch_bounds__(kLpBlock) k_lp_rows(const LpArgs a) {
+    __shared__ uint32_t t_key[2 * kLpChunk], t_cnt[2 * kLpChunk];
+    __shared__ unsigned long long s_red[kLpWarps];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (lp_quiet(a, lane)) return;
+    for (uint32_t i = (uint32_t)tid; i < 2 * kLpChunk; i += kLpBlock) {
+        t_key[i] = kInf;
+        t_cnt[i] = 0u;
+    }
+    __syncthreads();
     uint32_t n_changed = 0;
     for (uint64_t c = blockIdx.x; c < a.n_chunks; c += gridDim.x) {
         const LpRow r = a.chunks[c];
         const LpPart P = a.parts[r.part];
         const uint32_t n = r.n;
-        uint32_t np2 = 2;
-        while (np2 < n) np2 <<= 1;
-        for (uint32_t i0 = 0; i0 < np2; i0 += (uint32_t)kLpBlock * kGatherUnroll) {
-            uint32_t s[kGatherUnroll];
+        uint32_t lg = 1;
+        while ((1u << lg) < 2u * n) ++lg;
+        const uint32_t size = 1u << lg;
+        for (uint32_t i0 = 0; i0 < n; i0 += (uint32_t)kLpBlock * kGatherUnroll) {
+            uint32_t sv[kGatherUnroll], lab[kGatherUnroll];
 #pragma unroll
             for (int q = 0; q < kGatherUnroll; ++q) {
                 const uint32_t i = i0 + (uint32_t)q * kLpBlock + (uint32_t)tid;
-                s[q] = i < n ? __ldg(P.src + r.e0 + i) : 0u;
+                sv[q] = i < n ? __ldg(P.src + r.e0 + i) : 0u;
             }
 #pragma unroll
             for (int q = 0; q < kGatherUnroll; ++q) {
                 const uint32_t i = i0 + (uint32_t)q * kLpBlock + (uint32_t)tid;
-                if (i < np2) lab[i] = i < n ? lp_label(a, P, s[q]) : kInf;   // padding sorts last
+                lab[q] = i < n ? lp_label(a, P, sv[q]) : 0u;
             }
-        }
-        __syncthreads();
-        for (uint32_t k = 2; k <= np2; k <<= 1) {   // bitonic sort, ascending
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = (uint32_t)tid; i < np2; i += kLpBlock) {
-                    const uint32_t l = i ^ j;
-                    if (l > i) {
-                        const uint32_t x = lab[i], y = lab[l];
-                        if ((x > y) == ((i & k) == 0u)) {
-                            lab[i] = y;
-                            lab[l] = x;
-                        }
-                    }
+            // lanes with the same label add once (labels repeat as they settle:
+            // one slot's atomics would otherwise serialize)
+#pragma unroll
+            for (int q = 0; q < kGatherUnroll; ++q) {
+                const bool has = i0 + (uint32_t)q * kLpBlock + (uint32_t)tid < n;
+                const unsigned act = __ballot_sync(kFull, has);
+                if (has) {
+                    const unsigned grp = __match_any_sync(act, lab[q]);
+                    if (lane == __ffs(grp) - 1) lp_table_add(t_key, t_cnt, lg, lab[q], (uint32_t)__popc(grp));
                 }
-                __syncthreads();
             }
         }
-        // thread t owns lab[lo, hi); a run starts where the label changes
-        const uint32_t per = (n + kLpBlock - 1) / kLpBlock;
-        const uint32_t lo = min(n, (uint32_t)tid * per), hi = min(n, lo + per);
-        uint32_t last_start = 0;   // 0 is always a start: the identity of the max-scan
-        for (uint32_t i = lo; i < hi; ++i)
-            if (i == 0 || lab[i] != lab[i - 1]) last_start = i;
-        // exclusive max-scan of the segments' last starts over the block
-        uint32_t incl = last_start;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl = max(incl, y);
-        }
-        if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
-        uint32_t before = __shfl_up_sync(kFull, incl, 1);
-        if (lane == 0) before = 0;
-        for (int w = 0; w < warp; ++w) before = max(before, s_warp[w]);
-        // walk the segment: at each run end, its length from the run's start
-        uint32_t start = before;
+        // read the counts and empty the table for the next row
         unsigned long long best = 0ull;
-        for (uint32_t i = lo; i < hi; ++i) {
-            if (i == 0 || lab[i] != lab[i - 1]) start = i;
-            if (i + 1 == n || lab[i + 1] != lab[i]) {
-                const uint32_t len = i - start + 1;
-                if (r.hub != kInf) {
-                    const LpHub H = a.hubs[r.hub];
-                    lp_table_add(a.keys + H.table, a.counts + H.table, H.log2_size, lab[i], len);
+        for (uint32_t i = (uint32_t)tid; i < size; i += kLpBlock) {
+            const uint32_t k = t_key[i];
+            if (k != kInf) {
+                const uint32_t cnt = t_cnt[i];
+                if (r.hub == kInf) {
+                    best = max(best, mode_key(cnt, k));
                 } else {
-                    best = max(best, mode_key(len, lab[i]));
+                    const LpHub H = a.hubs[r.hub];
+                    const uint32_t slot = lp_table_add(a.keys + H.table, a.counts + H.table, H.log2_size, k, cnt);
+                    a.seg_used[H.seg0 + slot / kLpSegment] = 1u;   // same value from every writer
                 }
+                t_key[i] = kInf;
+                t_cnt[i] = 0u;
             }
         }
         if (r.hub == kInf) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(kFull, best, o));
-            if (lane == 0) s_best[warp] = best;
-            __syncthreads();
-            if (tid == 0) {
-                unsigned long long b = 0ull;
-                for (int w = 0; w < kLpWarps; ++w) b = max(b, s_best[w]);
-                if (lp_apply(a, r.g, ~(uint32_t)b)) ++n_changed;
-            }
+            best = block_max(best, s_red);
+            if (tid == 0 && lp_apply(a, r.g, ~(uint32_t)best)) ++n_changed;
         }
-        __syncthreads();   // lab[] and the shared arrays are reused by the next row
+        __syncthreads();   // the table and s_red are reused by the next row
     }
     if (tid == 0) lp_count(a, n_changed, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kLpBlock) k_lp_hubs(const LpArgs a) {
-    __shared__ unsigned long long s_best[kLpWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// hub tables, a segment per CTA: the best (count, -label) of the segment
+// goes into the hub's 64-bit maximum, and the segment is emptied
+__global__ void __launch_bounds__(kLpBlock) k_lp_segments(const LpArgs a) {
+    __shared__ unsigned long long s_red[kLpWarps];
+    const int tid = threadIdx.x, lane = tid & 31;
     if (lp_quiet(a, lane)) return;
-    uint32_t n_changed = 0;
-    for (uint32_t h = blockIdx.x; h < a.n_hubs; h += gridDim.x) {
-        const LpHub H = a.hubs[h];
-        const uint64_t size = 1ull << H.log2_size;
-        uint32_t* keys = a.keys + H.table;
-        uint32_t* counts = a.counts + H.table;
+    for (uint32_t sg = blockIdx.x; sg < a.n_segments; sg += gridDim.x) {
+        if (!a.seg_used[sg]) continue;   // no label took a slot here this superstep (uniform in the CTA)
+        const LpSegment S = a.segments[sg];
+        uint32_t* keys = a.keys + S.slot0;
+        uint32_t* counts = a.counts + S.slot0;
         unsigned long long best = 0ull;
-        for (uint64_t i = (uint64_t)tid; i < size; i += kLpBlock) {
+        for (uint32_t i = (uint32_t)tid; i < S.n; i += kLpBlock) {
             const uint32_t k = keys[i];
             if (k != kInf) {
                 best = max(best, mode_key(counts[i], k));
@@ -266,18 +331,28 @@ __global__ void __launch_bounds__(kLpBlock) k_lp_hubs(const LpArgs a) {
                 counts[i] = 0u;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(kFull, best, o));
-        if (lane == 0) s_best[warp] = best;
-        __syncthreads();
+        best = block_max(best, s_red);
         if (tid == 0) {
-            unsigned long long b = 0ull;
-            for (int w = 0; w < kLpWarps; ++w) b = max(b, s_best[w]);
-            if (lp_apply(a, H.g, ~(uint32_t)b)) ++n_changed;
+            if (best) atomicMax(a.hub_best + S.hub, best);
+            a.seg_used[sg] = 0u;
         }
         __syncthreads();
     }
-    if (tid == 0) lp_count(a, n_changed, blockIdx.x + 17u);
+}
+
+// a thread per hub: apply the mode its segments agreed on
+__global__ void k_lp_hubs(const LpArgs a) {
+    const int lane = threadIdx.x & 31;
+    if (lp_quiet(a, lane)) return;
+    uint32_t n_changed = 0;
+    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < a.n_hubs; h += gridDim.x * blockDim.x) {
+        const unsigned long long best = a.hub_best[h];
+        a.hub_best[h] = 0ull;
+        if (lp_apply(a, a.hubs[h].g, ~(uint32_t)best)) ++n_changed;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_changed += __shfl_xor_sync(kFull, n_changed, o);
+    if (lane == 0) lp_count(a, n_changed, blockIdx.x * 8u + (threadIdx.x >> 5) + 17u);
 }
 
 }  // namespace
@@ -287,9 +362,12 @@ cudaError_t launch_lp_superstep(const LpArgs& a, cudaStream_t s) {
         (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((a.n_windows + 8 * kWinUnroll - 1) / (8 * kWinUnroll),
                                                            152ull * 16));
     k_lp_windows<<<g_win, kLpBlock, 0, s>>>(a);   // also clears the stat slot two supersteps ahead
-    if (a.n_chunks)
-        k_lp_chunks<<<(uint32_t)std::min<uint64_t>(a.n_chunks, 152ull * 8), kLpBlock, 0, s>>>(a);
-    if (a.n_hubs) k_lp_hubs<<<(uint32_t)std::min<uint64_t>(a.n_hubs, 152ull * 8), kLpBlock, 0, s>>>(a);
+    if (a.n_warp_rows)
+        k_lp_warp_rows<<<(uint32_t)std::min<uint64_t>((a.n_warp_rows + 7) / 8, 152ull * 8), kLpBlock, 0, s>>>(a);
+    if (a.n_chunks) k_lp_rows<<<(uint32_t)std::min<uint64_t>(a.n_chunks, 152ull * 4), kLpBlock, 0, s>>>(a);
+    if (a.n_segments)
+        k_lp_segments<<<(uint32_t)std::min<uint64_t>(a.n_segments, 152ull * 8), kLpBlock, 0, s>>>(a);
+    if (a.n_hubs) k_lp_hubs<<<(uint32_t)std::min<uint64_t>((a.n_hubs + 255) / 256, 152ull * 4), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

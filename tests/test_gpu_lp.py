@@ -1,7 +1,7 @@
 """Label propagation (mode merge, Jacobi, 15-superstep cap) through the C-ABI
 against the oracle: labels and changed counts after every superstep, on one
 partition (renumbered or not) and on several, with rows in every in-degree
-class (1..32, 33..4096, hub rows cut into chunks of 4096 with a hash table),
+class (1..32, 33..256, 257..2048, hub rows cut into chunks of 2048 with a hash table),
 ties, multi-edges, self-loops and graphs that never settle."""
 import numpy as np
 import pytest
@@ -15,14 +15,15 @@ CAP = oracle.LP_MAX_STEPS
 
 
 def _mixed_graph(seed, n=12000):
-    """Symmetric R-MAT core plus rows of 32, 33, 4096, 4097 and 9000 in-edges
+    """Symmetric R-MAT core plus rows of 32, 33, 256, 257, 2048, 2049, 4097 and 9000 in-edges
     (sources drawn from a few hundred vertices: repeated labels early) and
     multi-edges / self-loops."""
     rng = np.random.default_rng(seed)
     s, d = synth.rmat(13, 8 << 13, seed)
     s, d = np.concatenate([s, d]), np.concatenate([d, s])
     extra_s, extra_d = [], []
-    for v, k in ((9000, 32), (9001, 33), (9002, 4096), (9003, 4097), (9004, 9000)):
+    for v, k in ((9000, 32), (9001, 33), (9002, 2048), (9003, 2049), (9004, 9000), (9005, 4097), (9006, 256),
+                 (9007, 257)):
         extra_s.append(rng.integers(0, 400, k, dtype=np.uint32))
         extra_d.append(np.full(k, v, np.uint32))
     extra_s.append(np.array([9100, 9100, 9101], np.uint32))   # self-loops, multi-edge
