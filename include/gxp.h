@@ -218,7 +218,8 @@ GXP_API gxp_status gxp_load_partition(gxp_ctx* ctx, uint32_t part, gxp_format fm
  * in-degree slots) on first use. damping is used by
  * PageRank/PPR (e.g. 0.85). PPR runs the PageRank template (CONTRIB, SUM,
  * PAGERANK) with gxp_superstep(GXP_ALGO_PPR, ...). Builds the
- * partition caches (ghost/mirror tables) on first use. */
+ * partition caches (cached copies of remote sources, boundary set) on first
+ * use. */
 GXP_API gxp_status gxp_begin(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping);
 
 /* Copy the current values of the vertices owned by `part` (in local order,
@@ -260,9 +261,14 @@ GXP_API gxp_status gxp_sync(gxp_ctx* ctx, uint32_t part, uint32_t* ids, void* va
                             uint64_t cap, uint64_t* n_out, int* skipped);
 
 /* Iteration control (Section II-C2): run supersteps until one changes no
- * vertex (SSSP, CC) or exactly max_steps of them (PageRank). Starts with
+ * vertex (SSSP, CC, LP) or max_steps of them (always max_steps for
+ * PageRank; LP need not settle: the paper caps it at 15). Starts with
  * gxp_begin(algo, source, damping). *steps_done (nullable) counts supersteps
- * run, including the final one that changed nothing. */
+ * run, including the final one that changed nothing. SSSP and CC on one
+ * partition run the loop on the device (a CUDA graph whose conditional
+ * node repeats superstep + stop test, up to 32 supersteps per launch, one
+ * host synchronization per launch); the others enqueue supersteps in
+ * chunks and read their changed counts once per chunk. */
 GXP_API gxp_status gxp_run(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping,
                            uint32_t max_steps, uint32_t* steps_done);
 

@@ -617,8 +617,9 @@ void Engine::finalize() {
     finalized_ = true;
 }
 
-// Mirror table (where each owned vertex is cached), boundary bitmap and
-// global-data-queue layout for the sync of Algorithm 3.
+// Boundary bitmap (vertices another partition caches), global-data-queue
+// layout for the sync of Algorithm 3, and under a cache budget the kept and
+// downloaded copies.
 void Engine::build_caches() {
     const uint32_t V = (uint32_t)n_vertices_;
     const size_t words = ((size_t)V + 31) / 32 + 2;
