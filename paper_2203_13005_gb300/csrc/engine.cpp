@@ -1000,7 +1000,7 @@ void Engine::build_lp() {
             chunks.push_back(LpRow{g, p, e0, deg, kInf, {0, 0, 0}});
         } else {
             uint32_t lg = 1;
-            while ((1ull << lg) < 2ull * deg) ++lg;
+            while ((1ull << lg) < 2ull * deg && lg < 32) ++lg;   // 2^32 slots hold any in-degree's labels
             const uint32_t h = (uint32_t)hubs.size();
             hubs.push_back(LpHub{g, lg, table_slots, (uint32_t)segments.size(), 0});
             for (uint64_t s0 = 0; s0 < (1ull << lg); s0 += kLpSegment)

@@ -146,14 +146,14 @@ __global__ void __launch_bounds__(kLpBlock) k_lp_windows(const LpArgs a) {
 }
 
 // add `count` occurrences of `label` to a hash table of 2^log2_size slots
-// (open addressing with linear probing; the table holds at most half as many
-// labels as slots, so a slot is always found). Works on global and on shared
-// memory tables.
+// (open addressing with linear probing; a table of 2^k >= 2 n slots, or 2^32,
+// has a free slot for every distinct label, so one is always found). Works
+// on global and on shared memory tables.
 __device__ __forceinline__ uint32_t lp_table_add(uint32_t* keys, uint32_t* counts, uint32_t log2_size,
                                                  uint32_t label, uint32_t count) {
-    const uint32_t mask = (1u << log2_size) - 1u;
+    const uint32_t mask = log2_size >= 32u ? 0xFFFFFFFFu : (1u << log2_size) - 1u;
     uint32_t slot = (label * 0x9E3779B1u) >> (32u - log2_size);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
         const uint32_t k = atomicCAS(keys + slot, kInf, label);
         if (k == kInf || k == label) {
             atomicAdd(counts + slot, count);
