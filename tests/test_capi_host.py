@@ -76,3 +76,38 @@ def test_init_without_gpu_reports_error():
     with pytest.raises(gxp.GxpError) as ei:
         gxp.Context(0)
     assert ei.value.code in (gxp.GXP_E_CUDA, gxp.GXP_E_INVAL)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # every struct of the ABI: the C compiler's size and field offsets equal
+    # the ctypes binding's
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [gxp.gxp_config, gxp.gxp_stats, gxp.gxp_batch_opts, gxp.gxp_batch_report, gxp.gxp_serve_opts,
+               gxp.gxp_query_info, gxp.gxp_serve_report]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gxp.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = ln.split()
+        got[(name, field)] = int(val)
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == C.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
