@@ -1022,7 +1022,7 @@ void Engine::build_lp() {
                        "renumber sources");
             src = rs;
         }
-        parts[p] = LpPart{src, nullptr, hp.v_begin, hp.n_own, hp.ghost_base, 0};
+        parts[p] = LpPart{src, hp.v_begin, hp.n_own, hp.ghost_base, 0};
         for (uint32_t l = 0; l < hp.n_own; ++l) {   // input row order
             const uint32_t g = relabeled_ ? h_old2new_[l] : hp.v_begin + l;
             add_row(g, p, cp[l], cp[l + 1] - cp[l]);

@@ -256,8 +256,7 @@ constexpr uint32_t kLpWarpRow = 256;   // rows up to this many in-edges: a warp 
 constexpr uint32_t kLpChunk = 2048;
 constexpr uint32_t kLpSegment = 4096;
 struct LpPart {                 // where a row's in-edges and their labels are
-    const uint32_t* src;        // CSC sources (local ids, or input ids with src_map)
-    const uint32_t* src_map;    // single renumbered partition: input id -> value index
+    const uint32_t* src;        // CSC sources as local ids (a renumbered partition's, renumbered once)
     uint32_t v_begin, n_own, ghost_base, pad;
 };
 struct LpRow {                  // a row, or a chunk of a hub row

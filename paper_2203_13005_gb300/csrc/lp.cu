@@ -36,7 +36,6 @@ constexpr int kGatherUnroll = 4;
 
 // the label of in-edge source s of partition P (previous superstep)
 __device__ __forceinline__ uint32_t lp_label(const LpArgs& a, const LpPart& P, uint32_t s) {
-    if (P.src_map) return __ldg(a.own_cur + __ldg(P.src_map + s));
     return s < P.n_own ? __ldg(a.own_cur + P.v_begin + s) : __ldg(a.ghost + P.ghost_base + (s - P.n_own));
 }
 
