@@ -812,6 +812,7 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
     if (algo_ == Algo::LP) {
         LpArgs l{};
         l.parts = lp_.d_parts;
+        l.n_parts = n_parts_;
         l.windows = lp_.d_windows;
         l.n_windows = lp_.n_windows;
         l.row_g = lp_.d_row_g;

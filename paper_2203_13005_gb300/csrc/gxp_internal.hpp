@@ -290,6 +290,7 @@ struct LpSegment {              // kLpSegment slots (or fewer) of one hub's tabl
 };
 struct LpArgs {
     const LpPart* parts;
+    uint32_t n_parts;           // 1: no cached copies (sources are indices into own_cur)
     const LpWindow* windows;    // rows of 1..kLpSmall in-edges
     uint32_t n_windows;
     const uint32_t* row_g;      // their value indices

@@ -70,6 +70,9 @@ __device__ __forceinline__ unsigned long long mode_key(uint32_t count, uint32_t 
 
 constexpr int kWinUnroll = 4;   // windows a warp has in flight
 
+// kOnePart: one partition (no cached copies): every source is a local
+// index into the label array, read without the partition descriptor
+template <bool kOnePart>
 __global__ void __launch_bounds__(kLpBlock) k_lp_windows(const LpArgs a) {
     const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && a.stats_clear != nullptr) {
@@ -98,14 +101,16 @@ __global__ void __launch_bounds__(kLpBlock) k_lp_windows(const LpArgs a) {
             has[q] = (uint32_t)lane < (W[q].n_part & 63u);
             lead[q] = has[q] && ((W[q].starts >> lane) & 1u);
         }
+        const uint32_t* src0 = kOnePart ? a.parts[0].src : nullptr;
 #pragma unroll
         for (int q = 0; q < kWinUnroll; ++q) {
-            src[q] = has[q] ? __ldg(P[q]->src + W[q].e0 + lane) : 0u;
+            src[q] = has[q] ? __ldg((kOnePart ? src0 : P[q]->src) + W[q].e0 + lane) : 0u;
             g[q] = lead[q] ? __ldg(a.row_g + W[q].first + (uint32_t)__popc(W[q].starts & upto) - 1u) : 0u;
         }
 #pragma unroll
         for (int q = 0; q < kWinUnroll; ++q) {
-            label[q] = has[q] ? lp_label(a, *P[q], src[q]) : 0u;
+            if constexpr (kOnePart) label[q] = has[q] ? __ldg(a.own_cur + src[q]) : 0u;
+            else label[q] = has[q] ? lp_label(a, *P[q], src[q]) : 0u;
             old[q] = lead[q] ? a.own_cur[g[q]] : 0u;
         }
 #pragma unroll
@@ -360,7 +365,8 @@ cudaError_t launch_lp_superstep(const LpArgs& a, cudaStream_t s) {
     const uint32_t g_win =
         (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((a.n_windows + 8 * kWinUnroll - 1) / (8 * kWinUnroll),
                                                            152ull * 16));
-    k_lp_windows<<<g_win, kLpBlock, 0, s>>>(a);   // also clears the stat slot two supersteps ahead
+    if (a.n_parts == 1) k_lp_windows<true><<<g_win, kLpBlock, 0, s>>>(a);   // also clears the stat slot
+    else k_lp_windows<false><<<g_win, kLpBlock, 0, s>>>(a);                 // two supersteps ahead
     if (a.n_warp_rows)
         k_lp_warp_rows<<<(uint32_t)std::min<uint64_t>((a.n_warp_rows + 7) / 8, 152ull * 8), kLpBlock, 0, s>>>(a);
     if (a.n_chunks) k_lp_rows<<<(uint32_t)std::min<uint64_t>(a.n_chunks, 152ull * 4), kLpBlock, 0, s>>>(a);
