@@ -412,9 +412,17 @@ def run_lp(args):
     descriptor, old and new label) over the run's supersteps."""
     import torch
     from paper_2203_13005_gb300 import gxp
-    wl = synth.CC_ER24_P8 if args.lp_scale == 24 else synth.CC_ER24_P8.scaled(args.lp_scale)
-    src, dst, _ = wl.edges()
-    n, m = wl.n_vertices, wl.n_edges
+    if args.lp_graph == "rmat":
+        # a power-law graph: the PageRank R-MAT recipe at --lp-scale, stored
+        # in both directions (rows of every in-degree class, hub rows included)
+        wl = synth.PAGERANK_RMAT22.scaled(args.lp_scale)
+        s0, d0, _ = wl.edges()
+        src, dst = np.concatenate([s0, d0]), np.concatenate([d0, s0])
+        del s0, d0
+    else:
+        wl = synth.CC_ER24_P8 if args.lp_scale == 24 else synth.CC_ER24_P8.scaled(args.lp_scale)
+        src, dst, _ = wl.edges()
+    n, m = wl.n_vertices, len(src)
     parts = args.lp_parts
     ctx = gxp.Context(0)
     ctx.create_graph(n, parts)
@@ -451,7 +459,8 @@ def run_lp(args):
         "metric": METRIC, "value": steps * m / sec / 1e9, "unit": "GTEPS", "n_gpus": 1,
         "steps": len(times) - 1, "warmup": 1, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"lp_er{wl.scale}_{parts}parts", "vertices": n, "edges": m, "partitions": parts,
+        "config": {"workload": f"lp_{args.lp_graph}{wl.scale}_{parts}parts", "vertices": n, "edges": m,
+                   "partitions": parts,
                    "max_supersteps": cap, "step": "one LP run (to a quiet superstep or the cap)",
                    "superstep_us": [round(x, 1) for x in step_us]},
         "supersteps": steps, "syncs_done": st["syncs_done"], "syncs_skipped": st["syncs_skipped"],
@@ -700,6 +709,8 @@ def main():
                     help="cc_er24_8parts: cached remote vertices per partition (0 = all, 4294967295 = none)")
     ap.add_argument("--lp-parts", type=int, default=8, help="lp_er24_8parts: partitions (1 = one, renumbered)")
     ap.add_argument("--lp-scale", type=int, default=24, help="lp_er24_8parts: log2 vertices (smaller for profiling)")
+    ap.add_argument("--lp-graph", default="er", choices=["er", "rmat"],
+                    help="lp_er24_8parts: the ER graph, or symmetric R-MAT (power-law) at --lp-scale")
     ap.add_argument("--direction", default="auto", choices=sorted(DIRECTIONS),
                     help="sssp_rmat16: direction of the supersteps")
     ap.add_argument("--push-div", type=int, default=0, help="sssp_rmat16: auto pushes while frontier work x div <= E")
