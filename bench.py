@@ -164,9 +164,10 @@ def run_reference(args, world, rank):
 
 
 def cpu_baseline(src, dst, n, m):
-    """Oracle PageRank on this host: a bounded sample of 3 full-graph supersteps."""
+    """Oracle PageRank on this host: one whole step of the workload (its 20
+    full-graph supersteps, about 10 s of single-threaded CPU work)."""
     import oracle
-    k = 3
+    k = ITERS
     t0 = time.perf_counter()
     oracle.pagerank(n, src, dst, DAMPING, k)
     dt = time.perf_counter() - t0
