@@ -97,6 +97,19 @@ def test_workload_sizes():
     assert synth.MSSSP_RMAT24.n_vertices == 16777216 and synth.MSSSP_RMAT24.w_hi == 255
     small = w.scaled(8)
     assert small.n_vertices == 256 and small.n_edges == 4096
+    s22 = synth.SSSP_RMAT22
+    assert (s22.n_vertices, s22.n_edges, s22.w_lo, s22.w_hi, s22.seed) == (4194304, 67108864, 1, 100, 0x67700006)
+    cl = synth.SSSP_CLUSTERED24_P8
+    assert (cl.kind, cl.n_vertices, cl.n_edges, cl.parts, cl.p_cross, cl.w_hi) == (
+        "clustered", 16777216, 268435456, 8, 1e-5, 100)
+    cls = cl.scaled(12)   # the recipe at another size keeps its kind, blocks and crossing rate
+    assert (cls.kind, cls.n_vertices, cls.n_edges, cls.parts, cls.p_cross) == ("clustered", 4096, 65536, 8, 1e-5)
+    src, dst, wts = cls.edges()
+    assert len(src) == len(wts) == 65536 and wts.min() >= 1 and wts.max() <= 100
+    # every workload has its own seed
+    seeds = [x.seed for x in (synth.SSSP_RMAT16, synth.PAGERANK_RMAT22, synth.CC_ER24_P8, synth.MSSSP_RMAT24,
+                              synth.SSSP_RMAT22, synth.SSSP_CLUSTERED24_P8)] + [g.seed for g in synth.SERVE_GRAPHS]
+    assert len(set(seeds)) == len(seeds)
 
 
 def test_clustered_blocks_and_crossing_fraction():
