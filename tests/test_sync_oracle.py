@@ -77,3 +77,73 @@ def test_sssp_trace():
     d2, steps2, _ = oracle.sssp(n, src, dst, w, 0)
     assert np.array_equal(d, d2) and steps == steps2
     assert trace[-1][1]  # nothing changes in the last superstep, so nothing to sync
+
+
+# ---------------------------------------------------------------- LRU cache
+
+def _golden_lru():
+    path = __file__.replace("test_sync_oracle.py", "golden/lru_trace_6v.txt")
+    kv = {}
+    for ln in open(path):
+        ln = ln.strip()
+        if not ln or ln.startswith("#"):
+            continue
+        k, v = ln.split(":", 1)
+        kv[k.strip()] = v.strip()
+    edges = [tuple(int(x) for x in e.split()) for e in kv["edges"].split(",")]
+    after = []
+    t = 1
+    while f"after {t}" in kv:
+        row = []
+        for part in kv[f"after {t}"].split(";"):
+            ids, d = part.strip().split("|")
+            row.append(([int(x) for x in ids.split()[1:]], int(d)))
+        after.append(row)
+        t += 1
+    return (np.array([e[0] for e in edges], np.uint32), np.array([e[1] for e in edges], np.uint32),
+            [int(x) for x in kv["bounds"].split()], int(kv["capacity"]),
+            [int(x) for x in kv["before"].split()], after)
+
+
+def test_lru_hand_trace():
+    src, dst, bounds, cap, before, after = _golden_lru()
+    lab, steps, trace0, trace = sync.lru_trace(6, src, dst, bounds, cap)
+    assert lab.tolist() == [0] * 6 and steps == 4
+    assert trace0 == before
+    assert [[(k, d) for k, d in row] for row in trace] == after
+
+
+def test_lru_weight_rule():
+    # decay by half, rise by reads when used, saturate at W_MAX; evict lowest, ties evict higher id
+    kept, w, d = sync.lru_boundary({7, 9}, {7: 10, 9: 3}, [9, 11], {7: 1, 9: 4, 11: 5}, 2)
+    # 7: 10//2 = 5; 9: 3//2 + 4 = 5; 11 enters with 5 -> all tie at 5: keep 7, 9 (lower ids)
+    assert kept == {7, 9} and w == {7: 5, 9: 5} and d == 1
+    kept, w, d = sync.lru_boundary(set(), {}, [1, 2], {1: 70000, 2: 3}, 1)
+    assert kept == {1} and w == {1: sync.W_MAX} and d == 2
+    kept, w, d = sync.lru_boundary({1}, {1: sync.W_MAX}, [1], {1: 70000}, 1)
+    assert w == {1: sync.W_MAX} and d == 0
+    # capacity 0: every use downloads, nothing is kept
+    kept, w, d = sync.lru_boundary(set(), {}, [4, 5], {4: 1, 5: 1}, 0)
+    assert kept == set() and d == 2
+
+
+def test_lru_unbounded_downloads_each_copy_once_and_invariants():
+    wl = synth.CC_ER24_P8.scaled(10)
+    src, dst, _ = wl.edges()
+    n = wl.n_vertices
+    bounds = [n * p // 4 for p in range(5)]
+    ghosts = sync.reads_per_copy(n, src, dst, bounds)
+    big = max(len(g) for g, _ in ghosts)
+    lab, steps, trace0, trace = sync.lru_trace(n, src, dst, bounds, big)
+    ref, rsteps, _ = oracle.cc(n, src, dst)
+    assert np.array_equal(lab, ref) and steps == rsteps
+    # room for every copy: each is downloaded once, at its first use (superstep 1, CC)
+    assert trace0 == [len(g) for g, _ in ghosts]
+    assert all(d == 0 for row in trace for _, d in row)
+    for cap in (1, 7, 50):
+        _, _, t0, tr = sync.lru_trace(n, src, dst, bounds, cap)
+        for p, (g, _) in enumerate(ghosts):
+            assert t0[p] == len(g)
+            for row in tr:
+                kept, d = row[p]
+                assert len(kept) <= cap and set(kept) <= set(g.tolist())
