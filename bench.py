@@ -163,6 +163,13 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(src, dst, n, m):
     """Oracle PageRank on this host: one whole step of the workload (its 20
     full-graph supersteps, about 10 s of single-threaded CPU work)."""
@@ -171,8 +178,24 @@ def cpu_baseline(src, dst, n, m):
     t0 = time.perf_counter()
     oracle.pagerank(n, src, dst, DAMPING, k)
     dt = time.perf_counter() - t0
-    return {"value": k * m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+    return {"value": k * m / dt / 1e9, "unit": "GTEPS", "cores": 1, "host_cores": host_cores(), "kind": "oracle",
             "sample": f"{k} fp64 supersteps of {WL.name} (single thread, incl. its out-degree pass)"}
+
+
+def cpu_all_cores_pagerank(src, dst, n, m):
+    """The same 20 PageRank supersteps (fp64, pulled by destination over a CSC)
+    on every host core with OpenMP: a parallel CPU baseline, not the oracle.
+    The CSC is built before the timed region."""
+    from oracle import cpu_baselines as cb
+    cores = cb.set_threads(host_cores())
+    col_ptr, csrc, _ = cb.csc(n, src, dst)
+    outdeg = np.bincount(src, minlength=n).astype(np.uint32)
+    t0 = time.perf_counter()
+    cb.pagerank_pull(n, col_ptr, csrc, outdeg, DAMPING, ITERS)
+    dt = time.perf_counter() - t0
+    return {"value": ITERS * m / dt / 1e9, "unit": "GTEPS", "cores": cores, "host_cores": host_cores(),
+            "kind": "openmp pull by destination (fp64)",
+            "sample": f"{ITERS} supersteps of {WL.name}, CSC built outside the timed region"}
 
 
 def run_msssp(args):
@@ -299,6 +322,7 @@ def run_sssp(args):
     c2.close()
     e2e_s = statistics.median(e2e)
     peaks = measured_peaks()
+    cpu = {} if args.no_cpu_baseline else cpu_sssp_baselines(wl, src, dst, w, n, m)
     line = {
         "metric": METRIC, "value": steps * m / (ms * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": reps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -319,10 +343,82 @@ def run_sssp(args):
                      "algorithmic_bytes_per_launch": bytes_sweep},
         "e2e": {"value": steps * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 8 * (n + 1) + 8 * m,
                 "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": reps * steps,
         "clocks": clk.summary(),
     }
+    line.update(cpu)
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def cpu_sssp_baselines(wl, src, dst, w, n, m) -> dict:
+    """SSSP from vertex 0 on the host: the oracle's Jacobi run (one core), the
+    same supersteps pulled by destination on every core (OpenMP), and a
+    binary-heap Dijkstra (one core). Each is checked against the oracle's
+    distances; the CSC / CSR are built before the timed regions."""
+    import oracle
+    from oracle import cpu_baselines as cb
+    t0 = time.perf_counter()
+    d_ref, steps, _ = oracle.sssp(n, src, dst, w, 0)
+    t_orc = time.perf_counter() - t0
+    cores = cb.set_threads(host_cores())
+    cp, cs, cw = cb.csc(n, src, dst, w)
+    d0 = np.full(n, 0xFFFFFFFF, np.uint32)
+    d0[0] = 0
+    t0 = time.perf_counter()
+    d_all, steps_all = cb.minlabel_pull(n, cp, cs, cw, d0)
+    t_all = time.perf_counter() - t0
+    rp, rd, rw = cb.csr(n, src, dst, w)
+    t0 = time.perf_counter()
+    d_dij = cb.dijkstra(n, rp, rd, rw, 0)
+    t_dij = time.perf_counter() - t0
+    if not (np.array_equal(d_all, d_ref) and np.array_equal(d_dij, d_ref) and steps_all == steps):
+        raise RuntimeError("a CPU baseline disagrees with the oracle")
+    hc = host_cores()
+    return {
+        "cpu_baseline": {"value": steps * m / t_orc / 1e9, "unit": "GTEPS", "cores": 1, "host_cores": hc,
+                         "kind": "oracle", "sample": f"one whole run of {wl.name} ({steps} Jacobi supersteps)"},
+        "cpu_baseline_all_cores": {"value": steps * m / t_all / 1e9, "unit": "GTEPS", "cores": cores,
+                                   "host_cores": hc, "kind": "openmp pull by destination",
+                                   "sample": f"one whole run of {wl.name}, CSC built outside the timed region"},
+        "cpu_baseline_dijkstra": {"value": m / t_dij / 1e9, "unit": "GTEPS (edges / run time)", "cores": 1,
+                                  "host_cores": hc, "kind": "binary-heap Dijkstra", "ms": t_dij * 1e3,
+                                  "sample": f"source 0 of {wl.name}, CSR built outside the timed region"},
+    }
+
+
+def cpu_cc_baselines(wl, src, dst, n, m) -> dict:
+    """Connected components on the host: one superstep of the oracle (one core,
+    a bounded sample of the run), one superstep pulled by destination on every
+    core, and the whole answer by union-find (one core)."""
+    import oracle
+    from oracle import cpu_baselines as cb
+    lab0 = np.arange(n, dtype=np.uint32)
+    t0 = time.perf_counter()
+    l1, _ = oracle.cc_step(n, src, dst, lab0)
+    t_orc = time.perf_counter() - t0
+    cores = cb.set_threads(host_cores())
+    cp, cs, _ = cb.csc(n, src, dst)
+    t0 = time.perf_counter()
+    l1_all, _ = cb.minlabel_pull(n, cp, cs, None, lab0, max_steps=1)
+    t_all = time.perf_counter() - t0
+    del cp, cs
+    t0 = time.perf_counter()
+    uf = cb.union_find(n, src, dst)
+    t_uf = time.perf_counter() - t0
+    if not np.array_equal(l1_all, l1):
+        raise RuntimeError("the all-cores superstep disagrees with the oracle")
+    hc = host_cores()
+    return {
+        "cpu_baseline": {"value": m / t_orc / 1e9, "unit": "GTEPS", "cores": 1, "host_cores": hc, "kind": "oracle",
+                         "sample": f"the first superstep of {wl.name} (all edges)"},
+        "cpu_baseline_all_cores": {"value": m / t_all / 1e9, "unit": "GTEPS", "cores": cores, "host_cores": hc,
+                                   "kind": "openmp pull by destination",
+                                   "sample": f"the first superstep of {wl.name}, CSC built outside the timed region"},
+        "cpu_baseline_union_find": {"value": m / t_uf / 1e9, "unit": "GTEPS (edges / run time)", "cores": 1,
+                                    "host_cores": hc, "kind": "union-find (path halving)", "ms": t_uf * 1e3,
+                                    "sample": f"all components of {wl.name}"},
+    }, uf
 
 
 def run_cc(args):
@@ -334,6 +430,7 @@ def run_cc(args):
     wl = synth.CC_ER24_P8
     src, dst, _ = wl.edges()
     n, m = wl.n_vertices, wl.n_edges
+    cpu, uf = ({}, None) if args.no_cpu_baseline else cpu_cc_baselines(wl, src, dst, n, m)
     ctx = gxp.Context(0, cache_slots=args.cache_slots)
     ctx.create_graph(n, wl.parts)
     ctx.load_coo(src, dst)
@@ -348,18 +445,40 @@ def run_cc(args):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
     st = ctx.stats()
+    if uf is not None and not np.array_equal(ctx.values(), uf):
+        raise RuntimeError("GPU components differ from union-find")
     sec = min(times[1:]) if len(times) > 1 else times[0]
+    # the superstep kernel alone (k_sell<CC>, events around it on the context's
+    # stream) and the whole superstep with its exchange, superstep by superstep
+    ctx.begin(gxp.GXP_ALGO_CC)
+    k_ms, s_ms = [], []
+    for _ in range(steps):
+        ctx.superstep()
+        sx = ctx.stats()
+        k_ms.append(sx["last_kernel_ms"])
+        s_ms.append(sx["last_superstep_ms"])
+    k_us = statistics.mean(k_ms) * 1e3
+    bytes_sweep = 8 * m + 12 * n + n // 4   # source id + gathered label per edge; col_ptr, old, new, bitmap
+    peaks = measured_peaks()
     line = {
         "metric": METRIC, "value": steps * m / sec / 1e9, "unit": "GTEPS", "n_gpus": 1,
         "steps": len(times) - 1, "warmup": 1, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl.name, "vertices": n, "edges": m, "partitions": wl.parts,
                    "cache_slots": args.cache_slots,
-                   "step": "one run to convergence incl. per-chunk host checks"},
+                   "step": "one run to convergence incl. per-chunk host checks",
+                   "l2": "inputs larger than L2: 1 GiB of edge indices per superstep vs 129 MB L2"},
         "supersteps": steps, "syncs_done": st["syncs_done"], "syncs_skipped": st["syncs_skipped"],
         "sync_pairs": st["sync_pairs"], "cache_downloads": st["cache_downloads"],
-        "last_superstep_ms": st["last_superstep_ms"], "clocks": clk.summary(),
+        "superstep_kernel_us": [round(x * 1e3, 1) for x in k_ms],
+        "superstep_with_sync_us": [round(x * 1e3, 1) for x in s_ms],
+        "roofline": {"bound": "hbm", "achieved": bytes_sweep / (k_us * 1e-6) / 1e9, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": bytes_sweep / (k_us * 1e-6) / 1e9 / peaks["hbm_gbs"],
+                     "traffic": None, "peak_source": peaks["source"], "kernel": "k_sell<CC>",
+                     "avg_launch_us": k_us, "algorithmic_bytes_per_launch": bytes_sweep},
+        "gpu_launches": None, "clocks": clk.summary(),
     }
+    line.update(cpu)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -761,9 +880,10 @@ def main():
 
     src, dst, _ = WL.edges()
     n, m = WL.n_vertices, WL.n_edges
-    base = None
+    base = base_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(src, dst, n, m)
+        base_all = cpu_all_cores_pagerank(src, dst, n, m)
 
     stream = torch.cuda.Stream(device=dev)
     ctx = gxp.Context(local)
@@ -864,6 +984,7 @@ def main():
         }
         if base is not None:
             line["cpu_baseline"] = base
+            line["cpu_baseline_all_cores"] = base_all
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:

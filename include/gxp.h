@@ -18,8 +18,8 @@
  * - Errors raised asynchronously on the GPU (a CUDA fault, a device-side
  *   bounds check, a device wait that ran out of time) are returned by the
  *   next call that synchronizes with the device. After GXP_E_CUDA,
- *   GXP_E_TIMEOUT or GXP_E_BOUNDS the context is poisoned: later calls return
- *   GXP_E_STATE until gxp_destroy().
+ *   GXP_E_TIMEOUT, GXP_E_BOUNDS or GXP_E_LOST the context is poisoned: later
+ *   calls return GXP_E_STATE until gxp_destroy().
  * - Pointers: unless a flag says otherwise, array arguments may be host or
  *   device pointers (the library copies through unified addressing). Input
  *   arrays are copied; the caller keeps ownership and may free them when the
@@ -51,8 +51,36 @@ typedef enum gxp_status {
     GXP_E_BOUNDS = 5,       /* a device-side bounds check found an out-of-range index */
     GXP_E_STATE = 6,        /* call out of order, or context poisoned by an earlier error */
     GXP_E_UNSUPPORTED = 7,  /* valid but not implemented combination */
-    GXP_E_BUSY = 8          /* no free query slot / queue full (serving) */
+    GXP_E_BUSY = 8,         /* no free query slot / queue full (serving) */
+    GXP_E_LOST = 9          /* an exchange between partitions did not arrive: the superstep's
+                               delivery mark was missing when its stats were read (the lazy
+                               upload of Section III-B2 lost a message); poisons the context */
 } gxp_status;
+
+/* Host-side fault injection (gxp_config.fault, or the GXP_FAULT environment
+ * variable "kind[:n][,kind[:n]...]" with kinds alloc, h2d, sync, timeout).
+ * None makes the GPU fault, trap or hang: each fails one host-side event on
+ * purpose so that the error paths can be tested.
+ *  - ALLOC:     the fault_at-th device allocation of the context fails as an
+ *               out-of-memory would: the call returns GXP_E_NOMEM and the
+ *               context stays usable (the graph must be loaded again).
+ *  - H2D:       the fault_at-th host-to-device copy is not enqueued: the call
+ *               returns GXP_E_CUDA and the context is poisoned.
+ *  - SYNC_DROP: the fault_at-th exchange between partitions is dropped (its
+ *               kernels are not launched); the next read of the superstep
+ *               statistics finds its delivery mark missing: GXP_E_LOST, and
+ *               the context is poisoned.
+ *  - TIMEOUT:   every bounded device-side wait gives up at once (it then
+ *               waits for its own copies in flight): GXP_E_TIMEOUT. Only the
+ *               kernel of gxp_superstep_min_noalloc waits on the device, and
+ *               it reads the GXP_FAULT variable ("timeout") on every call. */
+typedef enum gxp_fault {
+    GXP_FAULT_NONE = 0,
+    GXP_FAULT_ALLOC = 1,
+    GXP_FAULT_H2D = 2,
+    GXP_FAULT_SYNC_DROP = 3,
+    GXP_FAULT_TIMEOUT = 4
+} gxp_fault;
 
 typedef enum gxp_algo {
     GXP_ALGO_SSSP = 0,      /* Bellman-Ford shortest paths (Section V-A) */
@@ -112,21 +140,27 @@ typedef struct gxp_config {
                                    decreasing in-degree, so the most gathered values share cache
                                    lines (values, sources and labels are mapped back: results
                                    are in input ids); 1: keep the input order */
-    uint32_t direction;         /* gxp_direction of SSSP / CC supersteps on a single partition:
-                                   GXP_DIR_AUTO (0, default), GXP_DIR_PULL or GXP_DIR_PUSH.
-                                   Graphs of several partitions always pull. */
+    uint32_t direction;         /* gxp_direction of SSSP / CC supersteps: GXP_DIR_AUTO (0,
+                                   default), GXP_DIR_PULL or GXP_DIR_PUSH. With several
+                                   partitions a push relaxes, in each partition, the in-edges
+                                   from its own changed vertices and from its cached copies of
+                                   changed remote vertices (delivered by the exchange). */
     uint32_t push_div;          /* GXP_DIR_AUTO pushes a superstep when (frontier out-edges +
                                    frontier items) * push_div <= the graph's edges; 0 = 8 */
     uint32_t cache_slots;       /* synchronization caching (Section III-B2) with a budget: remote
-                                   vertices each partition keeps cached between supersteps.
-                                   0 = all of them; GXP_CACHE_NONE = none. The kept ones are those
-                                   read by the most in-edges (the steady state of the LRU weight,
-                                   which rises with use and decays per iteration, when every
-                                   superstep reads every in-edge); cached copies are refreshed by
-                                   the lazy upload of changed boundary vertices, the others are
-                                   downloaded again from their owners after every superstep
-                                   (gxp_stats.cache_downloads). Values are the same either way. */
-    uint32_t reserved[3];
+                                   copies each partition keeps cached between supersteps.
+                                   0 = all of them; GXP_CACHE_NONE = none. With a budget the cache
+                                   is LRU-weighted (see gxp_cache_get): a copy enters when a
+                                   superstep uses it, its weight decays by half per superstep and
+                                   rises with its reads, the lowest weights are evicted. Cached
+                                   copies are refreshed by the lazy upload of changed boundary
+                                   vertices; a used copy that is not cached is downloaded from its
+                                   owner (gxp_stats.cache_downloads). Values are the same either
+                                   way. */
+    uint32_t fault;             /* gxp_fault injected into this context; 0 = none (GXP_FAULT may
+                                   still name one) */
+    uint32_t fault_at;          /* which event of that kind fails, from 1; 0 = the first */
+    uint32_t reserved[1];
 } gxp_config;
 
 #define GXP_CACHE_NONE 0xFFFFFFFFu
@@ -166,7 +200,10 @@ typedef struct gxp_stats {
     uint64_t push_supersteps;       /* of the supersteps, those run in push direction */
     uint64_t cache_downloads;       /* remote values downloaded because they were not cached
                                        (gxp_config.cache_slots), summed over supersteps */
-    uint64_t reserved[4];
+    double   last_kernel_ms;        /* device time of the last superstep's compute kernel alone
+                                       (MSGGen + MSGMerge + MSGApply, without its sync); gxp_run's
+                                       device-driven loop: the average superstep */
+    uint64_t reserved[3];
 } gxp_stats;
 
 /* ------------------------------------------------------------ lifecycle -- */
@@ -260,6 +297,21 @@ GXP_API gxp_status gxp_superstep(gxp_ctx* ctx, gxp_algo algo, gxp_msggen msggen,
 GXP_API gxp_status gxp_sync(gxp_ctx* ctx, uint32_t part, uint32_t* ids, void* vals,
                             uint64_t cap, uint64_t* n_out, int* skipped);
 
+/* The copies partition `part` holds in its cache now (Section III-B2,
+ * LRU-based caching): their vertex ids, ascending, into ids[0 .. *n_out)
+ * (host or device pointer). Without a budget (gxp_config.cache_slots = 0)
+ * every remote source of the partition's in-edges is cached. With a budget
+ * the cache starts empty at gxp_begin and, at every superstep boundary, the
+ * copies the coming superstep uses (its frontier: vertices changed in the
+ * superstep before; every vertex, or the source, before the first) enter it,
+ * each copy's weight W <- min(65535, floor(W / 2) * cached + reads * used)
+ * (reads: the partition's in-edges from that vertex), and the lowest weights
+ * are evicted down to cache_slots, ties evicting the higher id. A used copy
+ * that was not cached counts in gxp_stats.cache_downloads.
+ * Errors: GXP_E_STATE (no graph loaded), GXP_E_INVAL (part out of range,
+ * n_out NULL, or cap below the count, which *n_out then holds). */
+GXP_API gxp_status gxp_cache_get(gxp_ctx* ctx, uint32_t part, uint32_t* ids, uint64_t cap, uint64_t* n_out);
+
 /* Iteration control (Section II-C2): run supersteps until one changes no
  * vertex (SSSP, CC, LP) or max_steps of them (always max_steps for
  * PageRank; LP need not settle: the paper caps it at 15). Starts with
@@ -286,7 +338,10 @@ typedef struct gxp_batch_opts {
                                 from measured coefficients, then a local sweep (autotuner) */
     uint32_t use_graph;      /* 1: replay each superstep from a captured CUDA graph */
     uint32_t max_steps;      /* 0 = run to convergence */
-    uint32_t reserved[6];
+    const char* tune_cache;  /* path of the autotuner's JSON cache, or NULL: with block_edges = 0
+                                a record for this graph shape and GPU (gxp_tune_cache_get) is
+                                used instead of measuring, and a new measurement is stored */
+    uint32_t reserved[4];
 } gxp_batch_opts;
 
 typedef struct gxp_batch_report {
@@ -299,8 +354,30 @@ typedef struct gxp_batch_report {
     double   model_ms;       /* the pipeline-time equation's estimate at the chosen block size */
     double   sweep_best_ms;  /* measured superstep time at the chosen block size (autotuner) */
     uint64_t edges_per_superstep;
-    uint64_t reserved[6];
+    uint64_t tune_from_cache;   /* 1: the coefficients and block size came from the tune cache */
+    uint64_t reserved[5];
 } gxp_batch_report;
+
+/* One autotuner record (Section III-A): the per-edge download, compute and
+ * upload costs k1, k2, k3 and the per-block cost a (ms), Lemma 1's continuous
+ * optimum, the block size the local sweep chose and its measured superstep
+ * time. */
+typedef struct gxp_tune_record {
+    double k1, k2, k3, a;
+    double model_block_edges;
+    double block_edges;
+    double sweep_best_ms;
+} gxp_tune_record;
+
+/* The autotuner's cache file (JSON: one member per key). The key the batch
+ * engine uses is "sssp_batch V=<vertices> E=<edges> deg=<floor(log2(E/V))>
+ * esize=<bytes per streamed edge> gpu=<device name>". get: GXP_OK and *out
+ * when the file holds the key, GXP_E_INVAL when it does not (or the file is
+ * missing); put: adds or replaces the member (the file is rewritten through a
+ * temporary and renamed), GXP_E_INVAL if it cannot be written. Host-only:
+ * neither touches the GPU. */
+GXP_API gxp_status gxp_tune_cache_get(const char* path, const char* key, gxp_tune_record* out);
+GXP_API gxp_status gxp_tune_cache_put(const char* path, const char* key, const gxp_tune_record* rec);
 
 /* Multi-source Bellman-Ford (Section V-A runs several SSSP sources at once):
  * n_sources <= 64 sources advance together, every edge serving all of them.
@@ -457,7 +534,8 @@ GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double 
  *   d_src      uint32[n_edges] source ids (< n_vertices), dst-sorted
  *   d_w        uint32[n_edges] weights (SSSP only; NULL for CC)
  *   d_cur      uint32[n_vertices] current values (read only)
- *   d_next     uint32[n_vertices] next values (written)
+ *   d_next     uint32[n_vertices] next values (written); must not overlap
+ *              d_cur (GXP_E_INVAL)
  * d_col_ptr, d_src, d_w and d_cur must be 16-byte aligned and readable up to
  * round_up(n_vertices + 1, 4), round_up(n_edges, 4) and round_up(n_vertices, 4)
  * elements. n_changed
@@ -469,9 +547,17 @@ GXP_API gxp_status gxp_block_size_model(double k1, double k2, double k3, double 
  * device); make that first call before any stream capture. Every call clears
  * the parts of the scratch that must start at zero, but all calls share the
  * one array: calls that overlap on the GPU race and give wrong results.
- * Errors: GXP_E_INVAL (sizes, null or misaligned pointers, input beyond the
- * scratch limit), GXP_E_UNSUPPORTED (other algorithms), GXP_E_BOUNDS (a source
- * id out of range), GXP_E_TIMEOUT, GXP_E_CUDA. */
+ * Before any edge block is cut, a kernel checks the CSC on the device (the
+ * call waits for it): offsets that do not run from 0 to n_edges without
+ * decreasing return GXP_E_INVAL, a source id >= n_vertices GXP_E_BOUNDS, and
+ * nothing else runs. The kernel's bounded waits on its bulk copies return
+ * GXP_E_TIMEOUT when they run out (GXP_FAULT=timeout makes every wait give
+ * up at once, to test that path); a warp that gives up first waits for its
+ * own copies in flight.
+ * Errors: GXP_E_INVAL (sizes, null, misaligned or overlapping pointers,
+ * input beyond the scratch limit, CSC offsets out of order),
+ * GXP_E_UNSUPPORTED (other algorithms), GXP_E_BOUNDS (a source id out of
+ * range), GXP_E_TIMEOUT, GXP_E_CUDA. */
 GXP_API gxp_status gxp_superstep_min_noalloc(gxp_algo algo, uint32_t n_vertices, uint64_t n_edges,
                                              const uint32_t* d_col_ptr, const uint32_t* d_src,
                                              const uint32_t* d_w, const uint32_t* d_cur,

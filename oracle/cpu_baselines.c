@@ -208,3 +208,23 @@ void cb_union_find(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* 
     }
     for (uint64_t v = 0; v < n; ++v) label[v] = cb_find(label, (uint32_t)v);
 }
+
+/* Stable counting sort of m COO edges by destination (one core): col_ptr[n+1]
+ * (u64), csrc[m] and, when w != NULL, cw[m]. Returns 0, or -1 when scratch
+ * cannot be allocated. */
+int cb_csc_build(uint64_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, const uint32_t* w,
+                 uint64_t* col_ptr, uint32_t* csrc, uint32_t* cw) {
+    uint64_t* at = (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
+    if (!at) return -1;
+    memset(col_ptr, 0, sizeof(uint64_t) * (n + 1));
+    for (uint64_t i = 0; i < m; ++i) ++col_ptr[dst[i] + 1];
+    for (uint64_t v = 0; v < n; ++v) col_ptr[v + 1] += col_ptr[v];
+    memcpy(at, col_ptr, sizeof(uint64_t) * n);
+    for (uint64_t i = 0; i < m; ++i) {
+        const uint64_t k = at[dst[i]]++;
+        csrc[k] = src[i];
+        if (w) cw[k] = w[i];
+    }
+    free(at);
+    return 0;
+}

@@ -54,6 +54,8 @@ def _load():
         lib.cb_dijkstra.restype = C.c_int
         lib.cb_dijkstra.argtypes = [u64, p, p, p, u32, p]
         lib.cb_union_find.argtypes = [u64, u64, p, p, p]
+        lib.cb_csc_build.restype = C.c_int
+        lib.cb_csc_build.argtypes = [u64, u64, p, p, p, p, p, p]
         _lib = lib
     return _lib
 
@@ -77,13 +79,20 @@ def _p(a):
 
 
 def csc(n, src, dst, w=None):
-    """(col_ptr u64[n+1], sources, weights or None) grouped by destination."""
-    order = np.argsort(dst, kind="stable")
-    col_ptr = np.zeros(n + 1, np.uint64)
-    np.cumsum(np.bincount(dst, minlength=n), out=col_ptr[1:])
-    s = np.ascontiguousarray(src[order], dtype=np.uint32)
-    ws = None if w is None else np.ascontiguousarray(w[order], dtype=np.uint32)
-    return col_ptr, s, ws
+    """(col_ptr u64[n+1], sources, weights or None) grouped by destination
+    (a stable counting sort in C)."""
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    col_ptr = np.empty(n + 1, np.uint64)
+    s = np.empty(max(len(src), 1), np.uint32)
+    ws = None
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.uint32)
+        ws = np.empty(max(len(src), 1), np.uint32)
+    if _load().cb_csc_build(n, len(src), _p(src), _p(dst), None if w is None else _p(w), _p(col_ptr), _p(s),
+                            None if ws is None else _p(ws)):
+        raise MemoryError("cpu baseline allocation failed")
+    return col_ptr, s[:len(src)], None if ws is None else ws[:len(src)]
 
 
 def csr(n, src, dst, w):

@@ -12,8 +12,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "engine.hpp"
+#include "trace.hpp"
 
 namespace gxp {
 
@@ -74,9 +76,11 @@ void Engine::prepare_batch(bool streamed) {
         b.packed = packable(V, wmax);
         b.esize = b.packed ? 4u : 8u;
         b.d_units = (uint4*)dalloc(sizeof(uint4) * std::max<size_t>(b.units.size(), 1));
-        if (!b.units.empty())
+        if (!b.units.empty()) {
+            before_h2d("upload units");
             cuda_check(cudaMemcpy(b.d_units, b.units.data(), sizeof(uint4) * b.units.size(), cudaMemcpyHostToDevice),
                        "upload units");
+        }
         b.d_dist = (uint32_t*)dalloc(sizeof(uint32_t) * 64 * V);
         const size_t words = (V + 31) / 32 + 1;
         b.d_frontier[0] = (uint32_t*)dalloc(4 * words);
@@ -111,6 +115,7 @@ void Engine::prepare_batch(bool streamed) {
         b.d_edges = dalloc(std::max<size_t>(8 * E, 8));
         std::vector<uint2> tmp(E);
         fill(tmp.data(), false);
+        before_h2d("upload");
         cuda_check(cudaMemcpy(b.d_edges, tmp.data(), 8 * E, cudaMemcpyHostToDevice), "upload edges");
         b.resident = true;
     }
@@ -136,6 +141,7 @@ std::vector<uint64_t> Engine::block_cuts(uint64_t block_edges) const {
 // One superstep over all edge blocks (enqueued on stream_, the other two
 // streams forked from and joined back into it).
 void Engine::superstep_batch(const std::vector<uint64_t>& cuts, bool streamed, bool pipelined, bool dry, int parity) {
+    TraceRange trace_("gxp batched superstep (pipeline shuffle)");
     Batch& b = batch_;
     const size_t nb = cuts.size() - 1;
     const uint64_t words = (n_vertices_ + 31) / 32 + 1;
@@ -221,6 +227,7 @@ double Engine::time_pipeline(uint64_t block_edges, bool pipelined, bool dry, int
 
 void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_out, const gxp_batch_opts* opts_in,
                         gxp_batch_report* rep) {
+    TraceRange trace_("gxp batched SSSP");
     gxp_batch_opts opts{};
     if (opts_in) opts = *opts_in;
     if (n_src == 0 || n_src > 64) fail(GXP_E_INVAL, "n_sources must be in [1, 64]");
@@ -254,8 +261,30 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
                 b.max_blocks = blocks;
             }
         };
+        // the tune cache's key: the graph's shape, the streamed edge size and the GPU
+        std::string tune_key;
+        gxp_tune_record cached{};
+        bool from_cache = false;
+        if (!opts.block_edges && opts.tune_cache) {
+            cudaDeviceProp prop{};
+            cuda_check(cudaGetDeviceProperties(&prop, device_), "device properties");
+            const double deg = V ? (double)E / (double)V : 0.0;
+            tune_key = "sssp_batch V=" + std::to_string(V) + " E=" + std::to_string(E) +
+                       " deg=" + std::to_string(deg >= 1.0 ? (int)std::floor(std::log2(deg)) : 0) +
+                       " esize=" + std::to_string(b.esize) + " gpu=" + prop.name;
+            from_cache = tune_cache_get(opts.tune_cache, tune_key.c_str(), &cached) && cached.block_edges >= 1.0;
+        }
         if (opts.block_edges) {
             block_edges = opts.block_edges;
+        } else if (from_cache) {
+            r.k1 = cached.k1;
+            r.k2 = cached.k2;
+            r.k3 = cached.k3;
+            r.a = cached.a;
+            r.model_block_edges = cached.model_block_edges;
+            r.sweep_best_ms = cached.sweep_best_ms;
+            r.tune_from_cache = 1;
+            block_edges = (uint64_t)cached.block_edges;
         } else {
             ensure(sample + kUnitEdges, 64);
             // k1: download cost per edge (pinned H2D)
@@ -345,6 +374,11 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
                 }
             }
             r.sweep_best_ms = best_t;
+            if (opts.tune_cache) {
+                const gxp_tune_record rec{r.k1, r.k2, r.k3, r.a, r.model_block_edges, (double)block_edges, best_t};
+                if (!tune_cache_put(opts.tune_cache, tune_key.c_str(), rec))
+                    fail(GXP_E_INVAL, std::string("cannot write the tune cache ") + opts.tune_cache);
+            }
         }
     }
     const auto cuts = streamed ? block_cuts(block_edges) : std::vector<uint64_t>{0, b.units.size()};
@@ -367,6 +401,7 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
     r.blocks = (uint32_t)(cuts.size() - 1);
 
     // initial state: dist INF except each source's own slot, frontier = sources
+    before_h2d("upload");
     cuda_check(cudaMemcpyAsync(b.d_sources, src.data(), 4ull * n_src, cudaMemcpyHostToDevice, stream_), "sources");
     cuda_check(cudaMemsetAsync(b.d_frontier[0], 0, 4 * words, stream_), "memset");
     cuda_check(launch_msssp_init(b.d_dist, V, b.d_sources, n_src, b.d_frontier[0], stream_), "init");

@@ -20,7 +20,9 @@ namespace {
 
 thread_local std::string g_init_error;
 
-bool is_poisoning(gxp_status s) { return s == GXP_E_CUDA || s == GXP_E_TIMEOUT || s == GXP_E_BOUNDS; }
+bool is_poisoning(gxp_status s) {
+    return s == GXP_E_CUDA || s == GXP_E_TIMEOUT || s == GXP_E_BOUNDS || s == GXP_E_LOST;
+}
 
 template <class F>
 gxp_status guarded(gxp_ctx* ctx, F&& f) {
@@ -112,6 +114,7 @@ GXP_API const char* gxp_status_string(gxp_status s) {
         case GXP_E_STATE: return "GXP_E_STATE";
         case GXP_E_UNSUPPORTED: return "GXP_E_UNSUPPORTED";
         case GXP_E_BUSY: return "GXP_E_BUSY";
+        case GXP_E_LOST: return "GXP_E_LOST";
     }
     return "GXP_E_UNKNOWN";
 }
@@ -157,6 +160,28 @@ GXP_API gxp_status gxp_superstep(gxp_ctx* ctx, gxp_algo algo, gxp_msggen msggen,
 GXP_API gxp_status gxp_sync(gxp_ctx* ctx, uint32_t part, uint32_t* ids, void* vals, uint64_t cap,
                             uint64_t* n_out, int* skipped) {
     return guarded(ctx, [&](gxp::Engine& e) { e.sync_result(part, ids, vals, cap, n_out, skipped); });
+}
+
+GXP_API gxp_status gxp_tune_cache_get(const char* path, const char* key, gxp_tune_record* out) {
+    if (!path || !key || !out) return GXP_E_INVAL;
+    try {
+        return gxp::tune_cache_get(path, key, out) ? GXP_OK : GXP_E_INVAL;
+    } catch (...) {
+        return GXP_E_INVAL;
+    }
+}
+
+GXP_API gxp_status gxp_tune_cache_put(const char* path, const char* key, const gxp_tune_record* rec) {
+    if (!path || !key || !rec) return GXP_E_INVAL;
+    try {
+        return gxp::tune_cache_put(path, key, *rec) ? GXP_OK : GXP_E_INVAL;
+    } catch (...) {
+        return GXP_E_INVAL;
+    }
+}
+
+GXP_API gxp_status gxp_cache_get(gxp_ctx* ctx, uint32_t part, uint32_t* ids, uint64_t cap, uint64_t* n_out) {
+    return guarded(ctx, [&](gxp::Engine& e) { e.cache_contents(part, ids, cap, n_out); });
 }
 
 GXP_API gxp_status gxp_run(gxp_ctx* ctx, gxp_algo algo, uint32_t source, float damping, uint32_t max_steps,

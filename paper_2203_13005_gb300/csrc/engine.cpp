@@ -2,6 +2,7 @@
 // partition dst-sorted CSC with local source ids), device residency, the
 // superstep/sync/iteration control (Section II-C), and statistics.
 #include "engine.hpp"
+#include "trace.hpp"
 
 #include <algorithm>
 #include <cmath>
@@ -51,6 +52,7 @@ Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
     if (cfg_.max_slots == 0) cfg_.max_slots = 64;
     if (cfg_.pipeline_depth == 0) cfg_.pipeline_depth = 3;
     if (cfg_.push_div == 0) cfg_.push_div = 8;
+    faults_ = fault_plan(cfg_);
     if (cfg_.direction > GXP_DIR_PUSH) fail(GXP_E_INVAL, "direction must be GXP_DIR_AUTO, _PULL or _PUSH");
     if (cfg_.tile_items > (1u << 24) || cfg_.hub_items > (1u << 24))
         fail(GXP_E_INVAL, "tile_items and hub_items must not exceed 2^24");
@@ -62,6 +64,7 @@ Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
     stream_ = own_stream_;
     cuda_check(cudaEventCreate(&ev_a_), "cudaEventCreate");
     cuda_check(cudaEventCreate(&ev_b_), "cudaEventCreate");
+    cuda_check(cudaEventCreate(&ev_k_), "cudaEventCreate");
 }
 
 Engine::~Engine() {
@@ -71,9 +74,22 @@ Engine::~Engine() {
     for (auto& hp : parts_) release_part(hp);
     if (ev_a_) cudaEventDestroy(ev_a_);
     if (ev_b_) cudaEventDestroy(ev_b_);
+    if (ev_k_) cudaEventDestroy(ev_k_);
     if (h_ctl_) cudaFreeHost(h_ctl_);
     if (h_ring_) cudaFreeHost(h_ring_);
     if (own_stream_) cudaStreamDestroy(own_stream_);
+}
+
+cudaError_t Engine::device_malloc(void** p, size_t bytes) {
+    ++n_allocs_;
+    if (faults_.alloc_at == n_allocs_) return cudaErrorMemoryAllocation;   // injected fault
+    return cudaMalloc(p, bytes);
+}
+
+void Engine::before_h2d(const char* what) {
+    ++n_h2d_;
+    if (faults_.h2d_at == n_h2d_)
+        fail(GXP_E_CUDA, std::string(what) + ": host-to-device copy not enqueued (injected fault)");
 }
 
 void* Engine::dalloc(size_t bytes) {
@@ -81,7 +97,7 @@ void* Engine::dalloc(size_t bytes) {
     if (cfg_.mem_budget && graph_bytes_ + bytes > cfg_.mem_budget)
         fail(GXP_E_NOMEM, "allocation exceeds the context's mem_budget");
     void* p = nullptr;
-    cuda_check(cudaMalloc(&p, bytes), "cudaMalloc");
+    cuda_check(device_malloc(&p, bytes), "cudaMalloc");
     graph_allocs_.push_back(p);
     graph_bytes_ += bytes;
     return p;
@@ -96,8 +112,7 @@ void Engine::free_graph_device() {
     d_ctl_ = nullptr;
     h_old2new_.clear();
     lp_ = LpLists{};
-    d_pull_list_ = d_download_list_ = nullptr;
-    n_pull_ = n_download_ = 0;
+    lru_ = Lru{};
     for (void* p : graph_allocs_) cudaFree(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
@@ -125,6 +140,7 @@ void Engine::check_device_error() {
     if (d_err_) cuda_check(cudaMemcpy(&err, d_err_, 4, cudaMemcpyDeviceToHost), "read error word");
     if (err & kErrTimeout) fail(GXP_E_TIMEOUT, "a device-side wait exceeded timeout_ns");
     if (err & kErrBounds) fail(GXP_E_BOUNDS, "a device-side bounds check failed");
+    if (err & kErrInput) fail(GXP_E_BOUNDS, "a device-side check found CSC offsets out of order");
 }
 
 // ------------------------------------------------------------------ graph
@@ -198,6 +214,7 @@ static void build_local(HostPart& hp, uint64_t n_vertices, bool many_parts,
 
 void Engine::load_partition(uint32_t part, gxp_format fmt, uint64_t n_edges, const void* idx0,
                             const uint32_t* idx1, const uint32_t* weights) {
+    TraceRange trace_("gxp load partition");
     if (!have_graph_) fail(GXP_E_STATE, "gxp_create_graph must come first");
     if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
     if (n_edges > 0xFFFFFFFFull) fail(GXP_E_INVAL, "more than 2^32-1 edges in one partition");
@@ -279,7 +296,7 @@ void Engine::load_csc_device(HostPart& hp, uint64_t E, const void* cp_in, const 
         void* q = nullptr;
         if (cfg_.mem_budget && graph_bytes_ + bytes > cfg_.mem_budget)
             fail(GXP_E_NOMEM, "allocation exceeds the context's mem_budget");
-        cuda_check(cudaMalloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
+        cuda_check(device_malloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
         return q;
     };
     uint64_t* cp64 = nullptr;
@@ -294,11 +311,18 @@ void Engine::load_csc_device(HostPart& hp, uint64_t E, const void* cp_in, const 
         cuda_check(cudaMemsetAsync(flag, 0, 4, stream_), "memset");
         cuda_check(cudaMemsetAsync(hp.d_col_ptr, 0, 4 * pad4(n + 1), stream_), "memset");
         cuda_check(cudaMemsetAsync(hp.d_src + E, 0, 4 * (pad4(E) - E), stream_), "memset");
+        before_h2d("copy col_ptr");
         cuda_check(cudaMemcpyAsync(cp64, cp_in, 8 * ((size_t)n + 1), cudaMemcpyDefault, stream_), "copy col_ptr");
-        if (E) cuda_check(cudaMemcpyAsync(hp.d_src, src_in, 4 * E, cudaMemcpyDefault, stream_), "copy sources");
+        if (E) {
+            before_h2d("copy sources");
+            cuda_check(cudaMemcpyAsync(hp.d_src, src_in, 4 * E, cudaMemcpyDefault, stream_), "copy sources");
+        }
         if (w_in) {
             cuda_check(cudaMemsetAsync(hp.d_w + E, 0, 4 * (pad4(E) - E), stream_), "memset");
-            if (E) cuda_check(cudaMemcpyAsync(hp.d_w, w_in, 4 * E, cudaMemcpyDefault, stream_), "copy weights");
+            if (E) {
+                before_h2d("copy weights");
+                cuda_check(cudaMemcpyAsync(hp.d_w, w_in, 4 * E, cudaMemcpyDefault, stream_), "copy weights");
+            }
         }
         cuda_check(launch_csc_import(cp64, n, E, hp.d_col_ptr, hp.d_src, n, flag, stream_), "check CSC");
         uint32_t bad = 0;
@@ -351,7 +375,10 @@ void Engine::ensure_host(HostPart& hp) {
 uint32_t* Engine::upload_u32(const std::vector<uint32_t>& h, size_t n_pad) {
     uint32_t* d = (uint32_t*)dalloc(4 * std::max<size_t>(n_pad, 1));
     cuda_check(cudaMemsetAsync(d, 0, 4 * std::max<size_t>(n_pad, 1), stream_), "memset");
-    if (!h.empty()) cuda_check(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, stream_), "upload");
+    if (!h.empty()) {
+        before_h2d("upload");
+        cuda_check(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, stream_), "upload");
+    }
     cuda_check(cudaStreamSynchronize(stream_), "upload");   // the staging vector may die after this
     return d;
 }
@@ -366,6 +393,7 @@ uint32_t* Engine::upload_u32(const std::vector<uint32_t>& h, size_t n_pad) {
 // split into parts; then all slices ordered heavy-first. A few small counts
 // come back to the host to size the arrays.
 void Engine::build_sell() {
+    TraceRange trace_("gxp layout build");
     uint32_t T = cfg_.tile_items, H = cfg_.hub_items;
     if (auto_tiles_) {
         // by default the longest work item shrinks with the graph: a slice row
@@ -380,7 +408,7 @@ void Engine::build_sell() {
     std::vector<void*> tmp;   // freed when the build ends
     auto talloc = [&](size_t bytes) {
         void* q = nullptr;
-        cuda_check(cudaMalloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
+        cuda_check(device_malloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
         tmp.push_back(q);
         return q;
     };
@@ -433,9 +461,11 @@ void Engine::build_sell() {
         }
         if (ns * 32 > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many rows in one partition");
         uint32_t* d_bases = (uint32_t*)talloc(8 * (size_t)nw + 8);
-        if (nw)
+        if (nw) {
+            before_h2d("upload bases");
             cuda_check(cudaMemcpyAsync(d_bases, bases.data(), 8 * (size_t)nw, cudaMemcpyHostToDevice, stream_),
                        "upload bases");
+        }
         // 3. slices and their offsets
         uint32_t* perm = (uint32_t*)dalloc(4 * pad4(ns * 32));
         uint32_t* width = (uint32_t*)talloc(4 * ns + 4);
@@ -449,8 +479,8 @@ void Engine::build_sell() {
         uint32_t* sell_w = weighted ? (uint32_t*)dalloc(4 * pad4(sell_size)) : nullptr;
         part_desc[p] = (SellSlice*)talloc(sizeof(SellSlice) * (ns + 1));
         part_ns[p] = (uint32_t)ns;
-        cuda_check(launch_sell_fill(col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, sell_src, sell_w,
-                                    part_desc[p], stream_), "fill slices");
+        cuda_check(launch_sell_fill(col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, pd_[p].pad_id, sell_src,
+                                    sell_w, part_desc[p], stream_), "fill slices");
         // 5. hub rows -> parts of T edges
         uint32_t* hub_list = (uint32_t*)talloc(4 * nh_rows + 4);
         uint32_t* part_off = (uint32_t*)talloc(4 * nh_rows + 4);
@@ -474,9 +504,10 @@ void Engine::build_sell() {
     if (total_slices > 0xFFFFFFF0ull) fail(GXP_E_INVAL, "graph too large");
     n_slices_ = (uint32_t)total_slices;
     n_hubs_ = total_hubs;
+    before_h2d("upload");
     cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
                "upload parts");
-    // 6. all partitions' slices, heavy first; hub parts concatenated (t0 already global)
+    // 6. the partitions' slices, heavy first; hub parts concatenated (t0 already global)
     SellSlice* all = (SellSlice*)talloc(sizeof(SellSlice) * (total_slices + 1));
     uint64_t at = 0;
     for (uint32_t p = 0; p < n_parts_; ++p) {
@@ -485,9 +516,20 @@ void Engine::build_sell() {
                                        cudaMemcpyDeviceToDevice, stream_), "gather slices");
         at += part_ns[p];
     }
+    // Heavy first within each partition, partitions one after the other: the
+    // grid then works through one partition's rows at a time, so the values
+    // it gathers at any moment are that partition's own vertices and cached
+    // copies (tens of MB, L2-resident) rather than every partition's copies
+    // at once.
     d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(total_slices, 1));
     uint32_t* order_scratch = (uint32_t*)talloc(order_slices_scratch_bytes(n_slices_));
-    cuda_check(launch_order_slices(all, n_slices_, d_slices_, order_scratch, stream_), "order slices");
+    at = 0;
+    for (uint32_t p = 0; p < n_parts_; ++p) {
+        if (part_ns[p])
+            cuda_check(launch_order_slices(all + at, part_ns[p], d_slices_ + at, order_scratch, stream_),
+                       "order slices");
+        at += part_ns[p];
+    }
     const size_t nh1 = std::max<size_t>(total_hubs, 1);
     d_hubs_ = (HubPart*)dalloc(sizeof(HubPart) * nh1);
     at = 0;
@@ -507,6 +549,7 @@ void Engine::build_sell() {
 
 // Upload every partition, count out-degrees, build caches.
 void Engine::finalize() {
+    TraceRange trace_("gxp finalize");
     for (uint32_t p = 0; p < n_parts_; ++p)
         if (!parts_[p].loaded) fail(GXP_E_STATE, "partition " + std::to_string(p) + " not loaded");
     cuda_check(cudaStreamSynchronize(stream_), "sync");
@@ -534,7 +577,8 @@ void Engine::finalize() {
         }
         pd_[p] = PartDev{hp.d_col_ptr, hp.d_src, nullptr, hp.n_own, hp.v_begin,
                          (uint32_t)hp.ghost_gid.size(), hp.ghost_base, hp.n_edges(),
-                         nullptr, nullptr, nullptr, nullptr, nullptr};
+                         nullptr, nullptr, nullptr, nullptr, nullptr,
+                         hp.n_own + (n_ghost_total_ - hp.ghost_base), 0u};
     }
     // what the layout build reads: each partition's CSC as loaded (weights on
     // the device), and for a single partition (unless keep_ids) an order of
@@ -558,7 +602,7 @@ void Engine::finalize() {
         uint32_t* rcol = (uint32_t*)dalloc(4 * pad4(V + 1));
         cuda_check(cudaMemsetAsync(rcol, 0, 4 * pad4(V + 1), stream_), "memset");
         void* scratch = nullptr;
-        cudaError_t e = cudaMalloc(&scratch, relabel_scratch_bytes(V));
+        cudaError_t e = device_malloc(&scratch, relabel_scratch_bytes(V));
         if (e == cudaSuccess) e = launch_relabel(hp.d_col_ptr, V, d_new2old_, d_old2new_, rcol, (uint32_t*)scratch, stream_);
         cudaError_t e2 = cudaStreamSynchronize(stream_);
         if (scratch) cudaFree(scratch);
@@ -573,17 +617,20 @@ void Engine::finalize() {
         cuda_check(cudaMemcpy(h_old2new_.data(), d_old2new_, 4ull * V, cudaMemcpyDeviceToHost), "relabel map");
     }
     d_parts_ = (PartDev*)dalloc(sizeof(PartDev) * n_parts_);
+    before_h2d("upload");
     cuda_check(cudaMemcpyAsync(d_parts_, pd_.data(), sizeof(PartDev) * n_parts_, cudaMemcpyHostToDevice, stream_),
                "upload parts");
     sell_ready_ = false;
     const std::vector<PartDev>& pd = pd_;
 
     d_ghost_gid_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
-    d_ghost_ = (uint32_t*)dalloc(4 * (size_t)std::max<uint32_t>(n_ghost_total_, 1));
+    d_ghost_ = (uint32_t*)dalloc(4 * pad4((size_t)n_ghost_total_ + 1));   // + the identity slot
     for (auto& hp : parts_)
-        if (!hp.ghost_gid.empty())
+        if (!hp.ghost_gid.empty()) {
+            before_h2d("upload ghost ids");
             cuda_check(cudaMemcpyAsync(d_ghost_gid_ + hp.ghost_base, hp.ghost_gid.data(), 4 * hp.ghost_gid.size(),
                                        cudaMemcpyHostToDevice, stream_), "upload ghost ids");
+        }
     cuda_check(cudaStreamSynchronize(stream_), "upload");
 
     // out-degrees over all partitions' edges
@@ -656,39 +703,40 @@ void Engine::build_caches() {
     d_block_offsets_ = (uint32_t*)dalloc(4 * (size_t)n_parts_ * sync_blocks_x_);
     d_part_counts_ = (uint32_t*)dalloc(4 * n_parts_);
     d_done_ctr_ = (uint32_t*)dalloc(4);
+    before_h2d("upload");
     cuda_check(cudaMemcpyAsync(d_boundary_, bbits.data(), 4 * words, cudaMemcpyHostToDevice, stream_), "upload");
+    before_h2d("upload");
     cuda_check(cudaMemcpyAsync(d_gdq_base_, gb.data(), 8 * n_parts_, cudaMemcpyHostToDevice, stream_), "upload");
     cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * words, stream_), "memset");
     cuda_check(cudaMemsetAsync(d_part_counts_, 0, 4 * n_parts_, stream_), "memset");
     cuda_check(cudaMemsetAsync(d_done_ctr_, 0, 4, stream_), "memset");
-    // caching under a budget: each partition keeps the cache_slots copies
-    // read by the most in-edges (ties: lower id); the rest are downloaded
-    // again after every superstep
-    d_pull_list_ = d_download_list_ = nullptr;
-    n_pull_ = n_download_ = 0;
-    if (cfg_.cache_slots != 0) {
-        std::vector<uint32_t> pull, download;
-        for (auto& hp : parts_) {
-            const uint32_t G = (uint32_t)hp.ghost_gid.size();
-            const uint32_t keep = cfg_.cache_slots == GXP_CACHE_NONE ? 0u : std::min(G, cfg_.cache_slots);
-            std::vector<uint32_t> reads(G, 0), order(G);
+    // caching under a budget: the LRU state of every copy (lru.cu); the
+    // cache starts empty at every gxp_begin
+    lru_ = Lru{};
+    if (cfg_.cache_slots != 0 && n_ghost_total_ > 0) {
+        lru_.on = true;
+        lru_.capacity = cfg_.cache_slots == GXP_CACHE_NONE ? 0u : cfg_.cache_slots;
+        std::vector<uint32_t> reads(n_ghost_total_, 0), base(n_parts_ + 1, 0);
+        for (uint32_t p = 0; p < n_parts_; ++p) {
+            const HostPart& hp = parts_[p];
+            base[p] = hp.ghost_base;
+            base[p + 1] = hp.ghost_base + (uint32_t)hp.ghost_gid.size();
+            lru_.max_per_part = std::max<uint32_t>(lru_.max_per_part, (uint32_t)hp.ghost_gid.size());
             for (uint32_t u : hp.src)
-                if (u >= hp.n_own) ++reads[u - hp.n_own];
-            for (uint32_t i = 0; i < G; ++i) order[i] = i;
-            std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return reads[x] > reads[y]; });
-            std::vector<uint8_t> kept(G, 0);
-            for (uint32_t i = 0; i < keep; ++i) kept[order[i]] = 1;
-            for (uint32_t i = 0; i < G; ++i) (kept[i] ? pull : download).push_back(hp.ghost_base + i);
+                if (u >= hp.n_own) ++reads[hp.ghost_base + (u - hp.n_own)];
         }
-        n_pull_ = (uint32_t)pull.size();
-        n_download_ = (uint32_t)download.size();
-        d_pull_list_ = (uint32_t*)dalloc(4 * std::max<size_t>(pull.size(), 1));
-        d_download_list_ = (uint32_t*)dalloc(4 * std::max<size_t>(download.size(), 1));
-        if (!pull.empty())
-            cuda_check(cudaMemcpy(d_pull_list_, pull.data(), 4 * pull.size(), cudaMemcpyHostToDevice), "upload");
-        if (!download.empty())
-            cuda_check(cudaMemcpy(d_download_list_, download.data(), 4 * download.size(), cudaMemcpyHostToDevice),
-                       "upload");
+        const size_t G = n_ghost_total_;
+        lru_.d_base = upload_u32(base, base.size());
+        lru_.d_reads = upload_u32(reads, G);
+        lru_.d_weight = (uint32_t*)dalloc(4 * G);
+        lru_.d_flags = (uint8_t*)dalloc(G);
+        lru_.d_hist = (uint32_t*)dalloc(4ull * kLruBins * n_parts_);
+        lru_.d_part = (LruPart*)dalloc(sizeof(LruPart) * n_parts_);
+        lru_.d_tie = (uint32_t*)dalloc(4 * G);
+        lru_.d_tie_scan = (uint32_t*)dalloc(4 * (G + 1));
+        lru_.d_scratch = (uint32_t*)dalloc(4 * ((G + 2047) / 2048 + 1));
+        cuda_check(cudaMemsetAsync(lru_.d_hist, 0, 4ull * kLruBins * n_parts_, stream_), "memset");
+        cuda_check(cudaMemsetAsync(lru_.d_part, 0, sizeof(LruPart) * n_parts_, stream_), "memset");
     }
     // the host copies must outlive the async uploads
     cuda_check(cudaStreamSynchronize(stream_), "upload caches");
@@ -708,13 +756,12 @@ static Algo to_algo(gxp_algo a) {
 }
 
 void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
+    TraceRange trace_("gxp begin");
     if (!have_graph_) fail(GXP_E_STATE, "no graph");
     const Algo a = to_algo(algo);
     const bool personalized = algo == GXP_ALGO_PPR;
     if ((a == Algo::SSSP || personalized) && source >= n_vertices_) fail(GXP_E_INVAL, "source out of range");
     if (a == Algo::PR && !(damping >= 0.0f && damping < 1.0f)) fail(GXP_E_INVAL, "damping must be in [0, 1)");
-    if ((a == Algo::SSSP || a == Algo::CC) && n_parts_ > 1 && cfg_.direction == GXP_DIR_PUSH)
-        fail(GXP_E_UNSUPPORTED, "push direction is implemented for single-partition graphs");
     if (!finalized_) finalize();
     if (a == Algo::SSSP && !weighted_) fail(GXP_E_INVAL, "SSSP needs edge weights on every partition");
     if (!sell_ready_) build_sell();
@@ -728,15 +775,22 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
                                   relabeled_ ? d_new2old_ : nullptr, stream_),
                "init values");
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
+    {   // the identity slots empty SELL slots read: 0 (sums) or INF (minima)
+        const uint32_t id = (a == Algo::PR) ? 0u : kInf;
+        for (int b = 0; b < 2; ++b) cuda_check(launch_fill_u32(d_own_[b] + V, 1, id, stream_), "identity slot");
+        cuda_check(launch_fill_u32(d_ghost_ + n_ghost_total_, 1, id, stream_), "identity slot");
+    }
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
+    cur_ = 0;
+    lru_reset(a == Algo::SSSP || personalized ? src_int : kInf);
     // (the packed frontier counter needs lists of fewer than 2^32 items)
     if (a == Algo::LP) {
         build_lp();
         // rows without in-edges are never written: both buffers hold their labels
         cuda_check(cudaMemcpyAsync(d_own_[1], d_own_[0], 4ull * V, cudaMemcpyDeviceToDevice, stream_), "copy values");
     }
-    frontier_ = (a == Algo::SSSP || a == Algo::CC) && n_parts_ == 1 && cfg_.direction != GXP_DIR_PULL &&
-                (uint64_t)V + (total_edges_ + kItemEdges - 1) / kItemEdges < (1ull << 32);
+    frontier_ = (a == Algo::SSSP || a == Algo::CC) && cfg_.direction != GXP_DIR_PULL &&
+                (uint64_t)V + n_ghost_total_ + (total_edges_ + kItemEdges - 1) / kItemEdges < (1ull << 32);
     if (frontier_) {
         build_out_edges();
         // both value buffers start equal: the push superstep lowers the next
@@ -765,6 +819,8 @@ SellArgs Engine::sell_args() const {
     a.hubs = d_hubs_;
     a.n_hubs = n_hubs_;
     a.parts = d_parts_;
+    a.n_parts = n_parts_;
+    a.n_vertices = (uint32_t)n_vertices_;
     a.own[0] = d_own_[0];
     a.own[1] = d_own_[1];
     a.rank[0] = d_rank_[0];
@@ -798,7 +854,70 @@ SellArgs Engine::sell_args() const {
     return a;
 }
 
+LruArgs Engine::lru_args(StepStats* out, const StepStats* quiet) const {
+    LruArgs a{};
+    a.n_parts = n_parts_;
+    a.n_ghost = n_ghost_total_;
+    a.ghost_base = lru_.d_base;
+    a.ghost_gid = d_ghost_gid_;
+    a.reads = lru_.d_reads;
+    a.weight = lru_.d_weight;
+    a.flags = lru_.d_flags;
+    a.ghost = d_ghost_;
+    a.capacity = lru_.capacity;
+    a.hist = lru_.d_hist;
+    a.part_state = lru_.d_part;
+    a.tie = lru_.d_tie;
+    a.tie_scan = lru_.d_tie_scan;
+    a.scan_scratch = lru_.d_scratch;
+    a.stats_out = out;
+    a.quiet_check = quiet;
+    return a;
+}
+
+// A new run starts with empty caches; the boundary before its first
+// superstep admits the copies that superstep uses (every vertex, or the
+// source of SSSP / personalized PageRank) into the stats of superstep 0.
+void Engine::lru_reset(uint32_t source_int) {
+    if (!lru_.on) return;
+    cuda_check(cudaMemsetAsync(lru_.d_flags, 0, n_ghost_total_, stream_), "memset");
+    cuda_check(cudaMemsetAsync(lru_.d_weight, 0, 4ull * n_ghost_total_, stream_), "memset");
+    LruArgs la = lru_args(d_stats_ + 1, nullptr);
+    la.own_val = d_own_[cur_];
+    la.frontier_all = source_int == kInf ? 1u : 0u;
+    la.frontier_one = source_int;
+    cuda_check(launch_lru_boundary(la, lru_.max_per_part, stream_), "cache start");
+}
+
+// The vertex ids of the copies partition `part` holds in its cache now
+// (ascending).
+void Engine::cache_contents(uint32_t part, uint32_t* ids, uint64_t cap, uint64_t* n_out) {
+    if (!finalized_) fail(GXP_E_STATE, "no graph is loaded");
+    if (part >= n_parts_) fail(GXP_E_INVAL, "partition index out of range");
+    if (!n_out) fail(GXP_E_INVAL, "n_out is required");
+    const HostPart& hp = parts_[part];
+    std::vector<uint32_t> kept;
+    if (!lru_.on) {
+        kept = hp.ghost_gid;   // no budget: every copy is cached
+    } else {
+        std::vector<uint8_t> f(hp.ghost_gid.size());
+        cuda_check(cudaStreamSynchronize(stream_), "sync");
+        if (!f.empty())
+            cuda_check(cudaMemcpy(f.data(), lru_.d_flags + hp.ghost_base, f.size(), cudaMemcpyDeviceToHost),
+                       "read cache flags");
+        for (size_t i = 0; i < f.size(); ++i)
+            if (f[i] & 1u) kept.push_back(hp.ghost_gid[i]);
+    }
+    *n_out = kept.size();
+    if (cap < kept.size()) fail(GXP_E_INVAL, "cap smaller than the number of cached copies");
+    if (!kept.empty()) {
+        if (!ids) fail(GXP_E_INVAL, "null output array");
+        cuda_check(cudaMemcpy(ids, kept.data(), 4 * kept.size(), cudaMemcpyDefault), "copy cached ids");
+    }
+}
+
 uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply ap, bool want) {
+    TraceRange trace_("gxp superstep");
     if (!begun_) fail(GXP_E_STATE, "gxp_begin must come first");
     if (to_algo(algo) != algo_ || (algo == GXP_ALGO_PPR) != (ppr_source_ != kInf))
         fail(GXP_E_INVAL, "algorithm differs from the one begun");
@@ -842,6 +961,7 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         const SellArgs a = sell_args();
         cuda_check(launch_superstep_sell(algo_, a, stream_), "superstep kernel");
     }
+    cuda_check(cudaEventRecord(ev_k_, stream_), "event");
     if (n_parts_ > 1) {
         SyncArgs s{};
         s.parts = d_parts_;
@@ -852,8 +972,8 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         s.ghost_gid = d_ghost_gid_;
         s.n_ghost = n_ghost_total_;
         s.ghost = d_ghost_;
-        s.pull_list = d_pull_list_;
-        s.n_pull = d_pull_list_ ? n_pull_ : n_ghost_total_;
+        s.cached = lru_.on ? lru_.d_flags : nullptr;
+        s.n_pull = n_ghost_total_;
         s.gdq_ids = d_gdq_ids_;
         s.gdq_vals = d_gdq_vals_;
         s.gdq_base = d_gdq_base_;
@@ -863,10 +983,31 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
         s.done_ctr = d_done_ctr_;
         s.blocks_x = sync_blocks_x_;
         s.stats_out = d_stats_ + (step_ + 1) % kStatRing;
-        cuda_check(launch_sync(s, max_words_, stream_), "sync kernels");
-        if (n_download_)
-            cuda_check(launch_download(d_download_list_, n_download_, d_ghost_gid_, d_own_[nx], d_ghost_, stream_),
-                       "download uncached copies");
+        if (frontier_) {   // delivered copies join the next superstep's frontier
+            s.fc.list_out = d_list_[(step_ + 1) & 1];
+            s.fc.list_cap = list_cap_;
+            s.fc.err = d_err_;
+            s.out_ptr = d_out_ptr_;
+            s.n_vertices = (uint32_t)n_vertices_;
+        }
+        // an injected fault drops the whole exchange, as a lost message would;
+        // the superstep's delivery mark then stays unset (see account())
+        if (faults_.sync_at != ++n_exchanges_) {
+            TraceRange trace_sync("gxp exchange (lazy upload, skip, cache)");
+            cuda_check(launch_sync(s, max_words_, stream_), "sync kernels");
+            // the cache before the next superstep: its frontier is this
+            // superstep's changed vertices; what it uses and does not hold
+            // is downloaded (counted in the next superstep's stats)
+            if (lru_.on) {
+                // a superstep after a quiet one (inside gxp_run) did nothing: neither does its boundary
+                const bool maybe_quiet = early_exit_ && algo_ != Algo::PR && step_ > 0;
+                LruArgs la = lru_args(d_stats_ + (step_ + 2) % kStatRing,
+                                      maybe_quiet ? d_stats_ + step_ % kStatRing : nullptr);
+                la.own_val = d_own_[nx];
+                la.frontier_bits = d_changed_;
+                cuda_check(launch_lru_boundary(la, lru_.max_per_part, stream_), "cache update");
+            }
+        }
         cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)n_vertices_ + 31) / 32 + 2), stream_), "memset");
     }
     cuda_check(cudaEventRecord(ev_b_, stream_), "event");
@@ -909,7 +1050,12 @@ uint64_t Engine::account(bool stop_at_quiet, bool ring_copied) {
             st_.last_l1_delta = fx_to_double(l1);
         }
         if (n_parts_ > 1) {
-            st_.cache_downloads += n_download_;
+            // every exchange marks its superstep's slot; a missing mark means
+            // the caches and upload lists of that superstep were never delivered
+            if (!s.exchanged)
+                fail(GXP_E_LOST, "the exchange between partitions of superstep " + std::to_string(t) +
+                                     " did not arrive");
+            st_.cache_downloads += s.downloads;
             st_.last_boundary_changed = s.boundary_changed;
             st_.sync_pairs += s.boundary_changed;
             if (s.skipped) st_.syncs_skipped++;
@@ -922,6 +1068,8 @@ uint64_t Engine::account(bool stop_at_quiet, bool ring_copied) {
     }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) st_.last_superstep_ms = ms;
+    else cudaGetLastError();
+    if (cudaEventElapsedTime(&ms, ev_a_, ev_k_) == cudaSuccess) st_.last_kernel_ms = ms;
     else cudaGetLastError();
     if (quiet && quiet < step_) {
         // the next two supersteps accumulate into these slots: clear the overshoot's values
@@ -936,36 +1084,79 @@ uint64_t Engine::account(bool stop_at_quiet, bool ring_copied) {
 
 // Out-edge copy for the push direction: offsets from the out-degrees and the
 // edges of the layout's CSC (renumbered like the layout), grouped by source.
+// Several partitions: the edges' sources are slots, the V vertices (their
+// out-edges into their own partition) then every partition's cached copies
+// (that partition's in-edges from the copied vertex), built from a CSC over
+// global rows with slot sources (temporary).
 void Engine::build_out_edges() {
+    TraceRange trace_("gxp out-edge build");
     if (out_ready_) return;
     const uint32_t V = (uint32_t)n_vertices_;
     const uint64_t E = total_edges_;
-    d_out_ptr_ = (uint32_t*)dalloc(4 * pad4((size_t)V + 1));
+    const uint32_t S = V + n_ghost_total_;   // slots
+    if ((uint64_t)V + n_ghost_total_ >= 0xFFFFFFF0ull) fail(GXP_E_INVAL, "too many vertices and cached copies");
+    n_slots_ = S;
+    d_out_ptr_ = (uint32_t*)dalloc(4 * pad4((size_t)S + 1));
     d_out_dst_ = (uint32_t*)dalloc(4 * std::max<uint64_t>(E, 1));
     d_out_w_ = weighted_ ? (uint32_t*)dalloc(4 * std::max<uint64_t>(E, 1)) : nullptr;
-    list_cap_ = (uint64_t)V + (E + kItemEdges - 1) / kItemEdges;
+    list_cap_ = (uint64_t)S + (E + kItemEdges - 1) / kItemEdges;
     for (auto& l : d_list_) l = (uint2*)dalloc(sizeof(uint2) * std::max<uint64_t>(list_cap_, 1));
-    void* scratch = nullptr;
-    cudaError_t e = cudaMalloc(&scratch, 4 * out_edges_scratch_words(V, E));
-    if (e == cudaSuccess) {
-        e = launch_out_edges(work_[0].in, V, E, d_outdeg_, d_out_ptr_, (uint32_t*)scratch, d_out_dst_,
-                             weighted_ ? d_out_w_ : nullptr, stream_);
+    std::vector<void*> tmp;
+    auto talloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        cuda_check(device_malloc(&q, std::max<size_t>(bytes, 16)), "cudaMalloc");
+        tmp.push_back(q);
+        return q;
+    };
+    struct FreeTmp {
+        std::vector<void*>& v;
+        cudaStream_t s;
+        ~FreeTmp() {
+            cudaStreamSynchronize(s);
+            for (void* q : v) cudaFree(q);
+        }
+    } free_tmp{tmp, stream_};
+    RowSource in = work_[0].in;
+    const uint32_t* deg = d_outdeg_;
+    if (n_parts_ > 1) {
+        uint32_t* ucol = (uint32_t*)talloc(4 * ((size_t)V + 1));
+        uint32_t* usrc = (uint32_t*)talloc(4 * std::max<uint64_t>(E, 1));
+        uint32_t* uw = weighted_ ? (uint32_t*)talloc(4 * std::max<uint64_t>(E, 1)) : nullptr;
+        uint64_t at = 0;
+        for (uint32_t p = 0; p < n_parts_; ++p) {
+            cuda_check(launch_unify_csc(pd_[p], V, at, ucol, usrc, p + 1 == n_parts_, stream_), "slot CSC");
+            if (uw && pd_[p].n_edges)
+                cuda_check(cudaMemcpyAsync(uw + at, work_[p].in.w, 4 * pd_[p].n_edges, cudaMemcpyDeviceToDevice,
+                                           stream_), "slot CSC weights");
+            at += pd_[p].n_edges;
+        }
+        uint32_t* sdeg = (uint32_t*)talloc(4 * ((size_t)S + 1));
+        cuda_check(launch_slot_degrees(usrc, E, S, sdeg, stream_), "slot degrees");
+        in = RowSource{ucol, usrc, uw, nullptr, nullptr};
+        deg = sdeg;
     }
-    cudaError_t e2 = cudaStreamSynchronize(stream_);
-    if (scratch) cudaFree(scratch);
-    cuda_check(e, "out-edges");
-    cuda_check(e2, "out-edges");
+    uint32_t* scratch = (uint32_t*)talloc(4 * out_edges_scratch_words(S, E));
+    cuda_check(launch_out_edges(in, V, S, E, deg, d_out_ptr_, scratch, d_out_dst_, weighted_ ? d_out_w_ : nullptr,
+                                stream_), "out-edges");
+    cuda_check(cudaStreamSynchronize(stream_), "out-edges");
     out_ready_ = true;
 }
 
-// The frontier the next superstep reads: one vertex, or all (kInf).
+// The frontier the next superstep reads: one vertex, or all (kInf) slots.
+// Several partitions start from the slots whose value is finite (every slot
+// for CC; SSSP: the source and its cached copies).
 void Engine::seed_frontier(uint32_t source_int) {
     FrontierCfg f{};
     f.list_out = d_list_[step_ & 1];
     f.list_cap = list_cap_;
     f.err = d_err_;
-    cuda_check(launch_seed_frontier((uint32_t)n_vertices_, source_int, d_out_ptr_, f, d_stats_ + (step_ % kStatRing),
-                                    stream_), "seed frontier");
+    if (n_parts_ > 1 && source_int != kInf) {
+        cuda_check(launch_seed_finite((uint32_t)n_vertices_, n_ghost_total_, d_own_[cur_], d_ghost_, d_out_ptr_, f,
+                                      d_stats_ + (step_ % kStatRing), stream_), "seed frontier");
+        return;
+    }
+    cuda_check(launch_seed_frontier(n_slots_, source_int, d_out_ptr_, f, d_stats_ + (step_ % kStatRing), stream_),
+               "seed frontier");
 }
 
 // Row lists of label propagation, by in-degree class (host-built once per
@@ -973,6 +1164,7 @@ void Engine::seed_frontier(uint32_t source_int) {
 // warp windows of adjacent edges, in CSC order), up to kLpChunk, and hub rows
 // cut into chunks of kLpChunk with a hash table each, cut into segments.
 void Engine::build_lp() {
+    TraceRange trace_("gxp label-propagation lists");
     if (lp_.ready) return;
     std::vector<LpPart> parts(n_parts_);
     std::vector<LpRow> chunks, warp_rows;
@@ -1031,7 +1223,10 @@ void Engine::build_lp() {
     }
     auto upload = [&](const void* h, size_t bytes) {
         void* d = dalloc(std::max<size_t>(bytes, 16));
-        if (bytes) cuda_check(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice), "upload label propagation lists");
+        if (bytes) {
+            before_h2d("upload label propagation lists");
+            cuda_check(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice), "upload label propagation lists");
+        }
         return d;
     };
     lp_.d_parts = (LpPart*)upload(parts.data(), sizeof(LpPart) * parts.size());
@@ -1132,6 +1327,7 @@ bool Engine::run_graph_ready() {
 }
 
 uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max_steps) {
+    TraceRange trace_("gxp run");
     begin(algo, source, damping);
     const gxp_msggen g = algo_ == Algo::SSSP ? GXP_GEN_RELAX : algo_ == Algo::PR ? GXP_GEN_CONTRIB : GXP_GEN_LABEL;
     const gxp_merge m = algo_ == Algo::PR ? GXP_MERGE_SUM : algo_ == Algo::LP ? GXP_MERGE_MODE : GXP_MERGE_MIN;
@@ -1150,6 +1346,7 @@ uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max
         while (steps < max_steps) {
             const uint32_t k = std::min<uint32_t>(kRunChunk, max_steps - steps);
             h_ctl_[0] = RunCtl{step_, step_ + k, 1u, 0u};
+            before_h2d("run control");
             cuda_check(cudaMemcpyAsync(d_ctl_, h_ctl_, sizeof(RunCtl), cudaMemcpyHostToDevice, stream_), "run control");
             cuda_check(cudaEventRecord(ev_a_, stream_), "event");
             cuda_check(cudaGraphLaunch(ge, stream_), "run graph");
@@ -1168,7 +1365,8 @@ uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max
             const uint64_t n_run = done - accounted_;
             const uint64_t quiet = account(true, true);
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess) st_.last_superstep_ms = ms / (double)n_run;
+            if (cudaEventElapsedTime(&ms, ev_a_, ev_b_) == cudaSuccess)
+                st_.last_superstep_ms = st_.last_kernel_ms = ms / (double)n_run;
             if (quiet) return (uint32_t)quiet;
         }
         return steps;
@@ -1228,10 +1426,12 @@ void Engine::set_values(uint32_t part, const void* in, uint64_t n) {
     if (n != cnt) fail(GXP_E_INVAL, "n must equal the number of vertices given");
     account(false);
     if (relabeled_) {   // input ids -> internal order
+        before_h2d("copy values");
         cuda_check(cudaMemcpyAsync(d_perm_tmp_, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
         cuda_check(launch_permute_u32(d_perm_tmp_, d_old2new_, (uint32_t)cnt, d_own_[cur_], true, stream_),
                    "map values");
     } else {
+        before_h2d("copy values");
         cuda_check(cudaMemcpyAsync(d_own_[cur_] + off, in, 4 * cnt, cudaMemcpyDefault, stream_), "copy values");
     }
     cuda_check(launch_init_ghosts(algo_, n_ghost_total_, d_ghost_gid_, d_own_[cur_], d_ghost_, stream_), "refresh caches");

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "fault.hpp"
 #include "gxp_internal.hpp"
 
 namespace gxp {
@@ -58,6 +59,7 @@ public:
     void begin(gxp_algo algo, uint32_t source, float damping);
     uint64_t superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a, bool want_changed);
     void sync_result(uint32_t part, uint32_t* ids, void* vals, uint64_t cap, uint64_t* n_out, int* skipped);
+    void cache_contents(uint32_t part, uint32_t* ids, uint64_t cap, uint64_t* n_out);
     uint32_t run(gxp_algo algo, uint32_t source, float damping, uint32_t max_steps);
     void get_values(uint32_t part, void* out, uint64_t n);
     void set_values(uint32_t part, const void* in, uint64_t n);
@@ -72,6 +74,12 @@ public:
 
 private:
     void* dalloc(size_t bytes);
+    // every device allocation and host-to-device copy of the context goes
+    // through these, so that an injected fault can fail the n-th one
+    cudaError_t device_malloc(void** p, size_t bytes);
+    void before_h2d(const char* what);
+    FaultPlan faults_;
+    uint64_t n_allocs_ = 0, n_h2d_ = 0, n_exchanges_ = 0;
     void free_graph_device();
     void finalize();
     void build_sell();
@@ -95,7 +103,7 @@ private:
     int device_;
     gxp_config cfg_;
     cudaStream_t own_stream_ = nullptr, stream_ = nullptr;
-    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr;
+    cudaEvent_t ev_a_ = nullptr, ev_b_ = nullptr, ev_k_ = nullptr;   // superstep start, end, kernel end
 
     // graph
     uint64_t n_vertices_ = 0;
@@ -132,9 +140,17 @@ private:
     uint64_t* d_gdq_base_ = nullptr;
     uint32_t *d_block_counts_ = nullptr, *d_block_offsets_ = nullptr, *d_part_counts_ = nullptr;
     uint32_t* d_done_ctr_ = nullptr;
-    uint32_t* d_pull_list_ = nullptr;       // cache budget: the kept copies, or nullptr = all
-    uint32_t* d_download_list_ = nullptr;   // and the ones downloaded every superstep
-    uint32_t n_pull_ = 0, n_download_ = 0;
+    // LRU-based caching under a budget (cache_slots): per-copy state, see lru.cu
+    struct Lru {
+        bool on = false;
+        uint32_t capacity = 0, max_per_part = 0;
+        uint32_t *d_base = nullptr, *d_reads = nullptr, *d_weight = nullptr, *d_hist = nullptr;
+        uint32_t *d_tie = nullptr, *d_tie_scan = nullptr, *d_scratch = nullptr;
+        uint8_t* d_flags = nullptr;
+        LruPart* d_part = nullptr;
+    } lru_;
+    LruArgs lru_args(StepStats* out, const StepStats* quiet) const;
+    void lru_reset(uint32_t source_int);
     uint32_t sync_blocks_x_ = 0, max_words_ = 0;
     StepStats* d_stats_ = nullptr;
     uint32_t* d_err_ = nullptr;
@@ -178,6 +194,7 @@ private:
     uint32_t* d_out_w_ = nullptr;
     uint2* d_list_[2] = {nullptr, nullptr};
     uint64_t list_cap_ = 0;
+    uint32_t n_slots_ = 0;         // push sources: the vertices, then (several partitions) the cached copies
     void build_out_edges();
     void seed_frontier(uint32_t source_int);
     // label propagation: rows by in-degree class, hub hash tables
@@ -216,6 +233,10 @@ private:
     gxp_stats st_{};
     uint64_t total_edges_ = 0;
 };
+
+// The autotuner's JSON cache (tune_cache.cpp).
+bool tune_cache_get(const char* path, const char* key, gxp_tune_record* out);
+bool tune_cache_put(const char* path, const char* key, const gxp_tune_record& rec);
 
 // Lemma 1 block-size model (host arithmetic).
 void block_size_model(double k1, double k2, double k3, double a, uint64_t d, uint64_t* b,

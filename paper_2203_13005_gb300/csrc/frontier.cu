@@ -215,7 +215,83 @@ __global__ void __launch_bounds__(256) k_seed_frontier(uint32_t n, uint32_t sour
     }
 }
 
+// one partition's rows and edges into the CSC over global rows with slot sources
+__global__ void __launch_bounds__(256) k_unify_csc(const PartDev p, uint32_t V, uint64_t edge_base, uint32_t* ucol,
+                                                   uint32_t* usrc, bool last) {
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = t0; r < p.n_own + (last ? 1u : 0u); r += nt)
+        ucol[p.v_begin + r] = (uint32_t)(edge_base + p.col_ptr[r]);
+    const uint32_t copy0 = V + p.ghost_base;
+    for (uint64_t e = t0; e < p.n_edges; e += nt) {
+        const uint32_t u = p.src[e];
+        usrc[edge_base + e] = u < p.n_own ? p.v_begin + u : copy0 + (u - p.n_own);
+    }
+}
+
+// out-degree of every slot; lanes with equal slots add once
+__global__ void __launch_bounds__(256) k_slot_degrees(const uint32_t* usrc, uint64_t n_edges, uint32_t* outdeg) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n_edges; b += nt) {
+        const uint64_t e = b + (uint64_t)lane;
+        const bool has = e < n_edges;
+        const uint32_t u = has ? usrc[e] : 0u;
+        const unsigned act = __ballot_sync(0xFFFFFFFFu, has);
+        if (has) {
+            const unsigned grp = __match_any_sync(act, u);
+            if (lane == __ffs(grp) - 1) atomicAdd(outdeg + u, (uint32_t)__popc(grp));
+        }
+    }
+}
+
+// every slot (vertices, then cached copies) whose value is below INF
+__global__ void __launch_bounds__(256) k_seed_finite(uint32_t V, uint32_t n_ghost, const uint32_t* own,
+                                                     const uint32_t* ghost, const uint32_t* out_ptr,
+                                                     const FrontierCfg f, StepStats* st) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t n = (uint64_t)V + n_ghost;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
+        const uint64_t u = b + (uint64_t)lane;
+        bool has = false;
+        uint32_t deg = 0;
+        if (u < n) {
+            const uint32_t x = u < V ? own[u] : ghost[u - V];
+            has = x != kInf;
+            deg = has ? out_ptr[u + 1] - out_ptr[u] : 0u;
+        }
+        frontier_append(has, (uint32_t)u, deg, f, st, lane);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_unify_csc(const PartDev& p, uint32_t n_vertices, uint64_t edge_base, uint32_t* ucol,
+                             uint32_t* usrc, bool last, cudaStream_t s) {
+    const uint64_t work = std::max<uint64_t>((uint64_t)p.n_own + 1, p.n_edges);
+    const uint32_t g = (uint32_t)std::min<uint64_t>((work + 255) / 256, 152ull * 16);
+    k_unify_csc<<<g, 256, 0, s>>>(p, n_vertices, edge_base, ucol, usrc, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_degrees(const uint32_t* usrc, uint64_t n_edges, uint32_t n_slots, uint32_t* outdeg,
+                                cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(outdeg, 0, 4ull * n_slots, s);
+    if (e != cudaSuccess || n_edges == 0) return e;
+    const uint32_t g = (uint32_t)std::min<uint64_t>((n_edges + 255) / 256, 152ull * 16);
+    k_slot_degrees<<<g, 256, 0, s>>>(usrc, n_edges, outdeg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_finite(uint32_t n_vertices, uint32_t n_ghost, const uint32_t* own, const uint32_t* ghost,
+                               const uint32_t* out_ptr, const FrontierCfg& f, StepStats* stats, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&stats->list_ne, 0, sizeof(unsigned long long), s);
+    const uint64_t n = (uint64_t)n_vertices + n_ghost;
+    if (e != cudaSuccess || n == 0) return e;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, 152ull * 16);
+    k_seed_finite<<<grid, 256, 0, s>>>(n_vertices, n_ghost, own, ghost, out_ptr, f, stats);
+    return cudaGetLastError();
+}
 
 // scratch words: cursors, scan sums, heavy chunk count, then the heavy
 // chunks (uint2, from a 16-byte aligned word)
@@ -224,31 +300,32 @@ static size_t heavy_offset_words(uint32_t n) {
     return (w + 3) & ~(size_t)3;
 }
 
-size_t out_edges_scratch_words(uint32_t n, uint64_t n_edges) {
+size_t out_edges_scratch_words(uint32_t n_src, uint64_t n_edges) {
     const size_t heavy = 2 * (n_edges / kHeavyEdges + 1);   // chunk entries: at most 2 E / kHeavyEdges
-    return heavy_offset_words(n) + 2 * heavy;
+    return heavy_offset_words(n_src) + 2 * heavy;
 }
 
-cudaError_t launch_out_edges(const RowSource& in, uint32_t n, uint64_t n_edges, const uint32_t* outdeg,
-                             uint32_t* out_ptr, uint32_t* scratch, uint32_t* out_dst, uint32_t* out_w,
-                             cudaStream_t s) {
+cudaError_t launch_out_edges(const RowSource& in, uint32_t n, uint32_t n_src, uint64_t n_edges,
+                             const uint32_t* outdeg, uint32_t* out_ptr, uint32_t* scratch, uint32_t* out_dst,
+                             uint32_t* out_w, cudaStream_t s) {
     Cursors cur;
     cur.hot = scratch;
     cur.warm = cur.hot + (size_t)kHot * kSub * kLine;
     cur.cold = cur.warm + (size_t)(kWarm - kHot) * kLine;
-    uint32_t* scan = scratch + cursor_words(n);                  // scan scratch
-    uint32_t* n_heavy = scan + ((size_t)n + 2047) / 2048 + 1;    // heavy chunk count
-    uint2* heavy = reinterpret_cast<uint2*>(scratch + heavy_offset_words(n));   // heavy chunks
-    cudaError_t e = launch_exclusive_scan_u32(outdeg, n, out_ptr, scan, s);
+    uint32_t* scan = scratch + cursor_words(n_src);                  // scan scratch
+    uint32_t* n_heavy = scan + ((size_t)n_src + 2047) / 2048 + 1;    // heavy chunk count
+    uint2* heavy = reinterpret_cast<uint2*>(scratch + heavy_offset_words(n_src));   // heavy chunks
+    cudaError_t e = launch_exclusive_scan_u32(outdeg, n_src, out_ptr, scan, s);
     if (e != cudaSuccess || n == 0) return e;
     if ((e = cudaMemsetAsync(cur.hot, 0, 4ull * kHot * kSub * kLine, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(n_heavy, 0, 4, s)) != cudaSuccess) return e;
     const uint32_t gl = (uint32_t)std::min<uint64_t>(((uint64_t)n + 255) / 256, 152ull * 16);
+    const uint32_t gs = (uint32_t)std::min<uint64_t>(((uint64_t)n_src + 255) / 256, 152ull * 16);
     const uint32_t gh = (uint32_t)std::min<uint64_t>((n_edges / kHeavyEdges + 8) / 8 + 1, 152ull * 16);
     const EdgeOp<false> count{in, cur, nullptr, nullptr};
     k_edges_light<false><<<gl, 256, 0, s>>>(count, n, heavy, n_heavy);
     k_edges_heavy<false><<<gh, 256, 0, s>>>(count, heavy, n_heavy);
-    k_cursor_init<<<gl, 256, 0, s>>>(out_ptr, n, cur);
+    k_cursor_init<<<gs, 256, 0, s>>>(out_ptr, n_src, cur);
     const EdgeOp<true> fill{in, cur, out_dst, out_w};
     k_edges_light<true><<<gl, 256, 0, s>>>(fill, n, heavy, n_heavy);
     k_edges_heavy<true><<<gh, 256, 0, s>>>(fill, heavy, n_heavy);

@@ -95,10 +95,20 @@ __device__ __forceinline__ uint32_t push_message(uint32_t du, uint32_t w) {
     }
 }
 
-// Push superstep of the min-label algorithms on one partition (called by
-// every warp of the superstep grid when push_chosen): MSGGen over the
-// out-edges of the frontier only (the vertices the previous superstep
-// changed); MSGMerge + MSGApply become an atomic min into the next values.
+// Push superstep of the min-label algorithms (called by every warp of the
+// superstep grid when push_chosen): MSGGen over the out-edges of the
+// frontier only (the vertices the previous superstep changed); MSGMerge +
+// MSGApply become an atomic min into the next values.
+// Sources are *slots*: [0, n_own_total) are the vertices themselves (their
+// out-edges into their own partition), [n_own_total, ...) the partitions'
+// cached copies of remote vertices (slot n_own_total + g for copy g, with
+// that partition's in-edges from the vertex as out-edges). One partition has
+// vertex slots only. Every edge belongs to exactly one slot, and every
+// destination is a vertex of the partition holding the edge, so each
+// partition's push writes only its own values. A destination that joins the
+// next frontier also gets its changed bit (changed_bits, several partitions),
+// from which the exchange uploads it; its cached copies join the next
+// frontier when the exchange delivers them (k_sync_pull).
 // Values stay double-buffered, so this is the same Jacobi superstep as the
 // pull direction (same values, same changed set):
 //  * sources' values come from the previous superstep's buffer, which
@@ -119,6 +129,8 @@ template <bool kW>
 __device__ __forceinline__ uint32_t push_superstep(const FrontierCfg& f, const uint32_t* out_ptr,
                                                    const uint32_t* out_dst, const uint32_t* out_w,
                                                    const uint32_t* own_cur, uint32_t* own_nxt,
+                                                   const uint32_t* ghost, uint32_t n_own_total,
+                                                   uint32_t* changed_bits,
                                                    const StepStats* stats_in, StepStats* stats_out,
                                                    uint64_t warp0, uint64_t n_warps, int lane) {
     const unsigned long long ne = stats_in->list_ne;
@@ -135,14 +147,15 @@ __device__ __forceinline__ uint32_t push_superstep(const FrontierCfg& f, const u
         uint32_t e_lo = 0, n = 0, du = kInf;
         if ((uint32_t)lane < c && i < n_items) {
             const uint2 it = f.list_in[i];
-            const uint32_t u = it.x;
-            du = own_cur[u];
+            const uint32_t u = it.x;   // a slot
+            const bool vertex = u < n_own_total;
+            du = vertex ? own_cur[u] : ghost[u - n_own_total];
             const uint32_t r1 = out_ptr[u + 1];
             e_lo = out_ptr[u] + it.y * kItemEdges;
             n = min(r1 - e_lo, kItemEdges);
-            // bring the next buffer up to date at u (values only decrease, so
-            // an entry already at or below du needs nothing)
-            if (it.y == 0u && __ldcg(own_nxt + u) > du) atomicMin(own_nxt + u, du);
+            // bring the next buffer up to date at vertex u (values only
+            // decrease, so an entry already at or below du needs nothing)
+            if (vertex && it.y == 0u && __ldcg(own_nxt + u) > du) atomicMin(own_nxt + u, du);
             if (kW && du == kInf) n = 0;   // unreachable: sends nothing
         }
         const uint32_t incl = warp_inclusive_scan(n, lane);
@@ -160,7 +173,10 @@ __device__ __forceinline__ uint32_t push_superstep(const FrontierCfg& f, const u
                 const uint32_t m = push_message<kW>(dj, kW ? out_w[e] : 0u);
                 const uint32_t nv = __ldcg(own_nxt + v), cv = __ldg(own_cur + v);   // both in flight
                 if (m < nv && m < cv) app = atomicMin(own_nxt + v, m) >= cv;
-                if (app) deg = __ldg(out_ptr + v + 1) - __ldg(out_ptr + v);
+                if (app) {
+                    deg = __ldg(out_ptr + v + 1) - __ldg(out_ptr + v);
+                    if (changed_bits) atomicOr(changed_bits + (v >> 5), 1u << (v & 31u));
+                }
             }
             n_changed += (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, app));
             frontier_append(app, v, deg, f, stats_out, lane);

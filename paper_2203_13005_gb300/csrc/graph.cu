@@ -7,7 +7,7 @@
 //    III-B, Algorithm 3): changed ∩ boundary -> global data queue (sorted by
 //    id) -> the caches of the partitions that read those vertices; the
 //    exchange is skipped on the device when the queue is empty everywhere.
-#include "gxp_internal.hpp"
+#include "frontier.cuh"
 
 #include <algorithm>
 
@@ -130,7 +130,9 @@ __global__ void k_validate(const uint32_t* __restrict__ col_ptr, uint32_t n_own,
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_edges; e += stride)
         if (src[e] >= n_local) atomicOr(err, kErrBounds);
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n_own; v += stride)
-        if (col_ptr[v] > col_ptr[v + 1]) atomicOr(err, kErrBounds);
+        if (col_ptr[v] > col_ptr[v + 1]) atomicOr(err, kErrInput);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (col_ptr[0] != 0u || (uint64_t)col_ptr[n_own] != n_edges))
+        atomicOr(err, kErrInput);
 }
 
 // CSC imported as given: col_ptr (u64) -> u32 with its checks (bit 0 of
@@ -177,6 +179,11 @@ __global__ void k_init_values(int algo, uint32_t ppr_source, uint32_t n, uint32_
         if ((threadIdx.x & 31) == 0 && dang)
             atomicAdd(&st->dangling_fx[(blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) % kStatLanes], dang);
     }
+}
+
+__global__ void k_fill_u32(uint32_t* p, uint64_t n, uint32_t v) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 __global__ void k_init_ghosts(uint32_t n_ghost, const uint32_t* __restrict__ gid,
@@ -264,6 +271,7 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_count(const SyncArgs a) {
     if (threadIdx.x == 0) {
         a.stats_out->boundary_changed = grand;
         a.stats_out->skipped = grand == 0 ? 1ull : 0ull;
+        a.stats_out->exchanged = 1ull;
         *a.done_ctr = 0u;
     }
 }
@@ -300,22 +308,27 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
 // per cached copy reads the changed bits and the owners' values in
 // ascending order and writes the cache sequentially.
 // With a cache budget only the kept copies (pull_list) are refreshed here.
+// With frontier lists on, every copy whose vertex changed (cached or not)
+// also joins the next frontier as slot n_vertices + g: the partition that
+// holds it relaxes its in-edges from that vertex if the next superstep pushes.
 __global__ void k_sync_pull(const SyncArgs a) {
     if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_pull; i += gridDim.x * blockDim.x) {
-        const uint32_t g = a.pull_list ? a.pull_list[i] : i;
-        const uint32_t gid = a.ghost_gid[g];
-        if ((a.changed_bits[gid >> 5] >> (gid & 31u)) & 1u) a.ghost[g] = a.own_val[gid];
-    }
-}
-
-// Copies a partition does not keep cached: downloaded again from their
-// owners after every superstep, exchange skipped or not.
-__global__ void k_download(const uint32_t* __restrict__ list, uint32_t n, const uint32_t* __restrict__ gid,
-                           const uint32_t* __restrict__ own, uint32_t* __restrict__ ghost) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t g = list[i];
-        ghost[g] = own[gid[g]];
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < a.n_pull; b += stride) {
+        const uint32_t g = b + (uint32_t)lane;
+        bool ch = false;
+        if (g < a.n_pull) {
+            const uint32_t gid = a.ghost_gid[g];
+            ch = ((a.changed_bits[gid >> 5] >> (gid & 31u)) & 1u) != 0u;
+            // not cached: downloaded when used (lru.cu)
+            if (ch && (!a.cached || (a.cached[g] & 1u))) a.ghost[g] = a.own_val[gid];
+        }
+        if (a.fc.list_out) {
+            const uint32_t slot = a.n_vertices + g;
+            const uint32_t deg = ch ? __ldg(a.out_ptr + slot + 1) - __ldg(a.out_ptr + slot) : 0u;
+            frontier_append(ch, slot, deg, a.fc, a.stats_out, lane);
+        }
     }
 }
 
@@ -347,8 +360,7 @@ cudaError_t launch_outdeg(const PartDev& p, const uint32_t* src, const uint32_t*
 
 cudaError_t launch_validate_csc(const uint32_t* col_ptr, uint32_t n_own, const uint32_t* src,
                                 uint64_t n_edges, uint32_t n_local, uint32_t* err, cudaStream_t s) {
-    const uint64_t work = std::max<uint64_t>(n_edges, n_own);
-    if (work == 0) return cudaSuccess;
+    const uint64_t work = std::max<uint64_t>(std::max<uint64_t>(n_edges, n_own), 1);
     const uint64_t blocks = std::min<uint64_t>((work + 255) / 256, 152ull * 16);
     k_validate<<<(unsigned)blocks, 256, 0, s>>>(col_ptr, n_own, src, n_edges, n_local, err);
     return cudaGetLastError();
@@ -370,6 +382,12 @@ cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n, uint32_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_fill_u32<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 8), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_ghosts(Algo, uint32_t n_ghost, const uint32_t* gid, const uint32_t* own,
                                uint32_t* ghost, cudaStream_t s) {
     if (n_ghost == 0) return cudaSuccess;
@@ -388,11 +406,5 @@ cudaError_t launch_sync(const SyncArgs& a, uint32_t, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_download(const uint32_t* list, uint32_t n, const uint32_t* ghost_gid, const uint32_t* own_val,
-                            uint32_t* ghost, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    k_download<<<std::min<uint32_t>((n + 255) / 256, 152u * 16), 256, 0, s>>>(list, n, ghost_gid, own_val, ghost);
-    return cudaGetLastError();
-}
 
 }  // namespace gxp

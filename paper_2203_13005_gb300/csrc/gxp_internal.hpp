@@ -24,6 +24,8 @@ constexpr int kStatRing = 64;        // superstep stat slots kept on the device
 // Device error word bits (ORed by kernels, read by the host at sync points).
 constexpr uint32_t kErrBounds = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrDrain = 4u;     // a give-up drain ran out before its copies landed
+constexpr uint32_t kErrInput = 8u;     // CSC offsets not running from 0 to n_edges, non-decreasing
 
 // Fixed-point scale of the exact global sums (dangling mass, L1 delta):
 // an fp32 value x in [0, 2] is held as round(x * 2^60) in a uint64.
@@ -60,7 +62,7 @@ struct SellSlice {
     uint32_t pad0;
     uint64_t off;      // first element of the slice in the partition's sell arrays
 };
-constexpr uint32_t kSellPad = 0xFFFFFFFFu;   // empty edge slot / empty row slot
+constexpr uint32_t kSellPad = 0xFFFFFFFFu;   // empty row slot of a slice (perm)
 constexpr uint32_t kSellWindow = 65536;      // rows sorted by degree within windows of this size
 
 // A slice of the in-edges of one hub row (in-degree above the SELL limit),
@@ -86,11 +88,18 @@ struct PartDev {
     uint32_t ghost_base;       // offset of this partition's ghosts in the ghost array
     uint64_t n_edges;
     // sliced-ELL layout (engine path)
-    const uint32_t* sell_src;  // column-major slices, kSellPad in empty slots
+    const uint32_t* sell_src;  // column-major slices, pad_id in empty slots
     const uint32_t* sell_w;    // weights in the same layout, or nullptr
     const uint32_t* perm;      // slice row slot -> local vertex (kSellPad = empty)
     const uint32_t* hsrc;      // hub rows' in-edges, row after row
     const uint32_t* hw;        // and weights, or nullptr
+    // local id of the identity slot that empty SELL slots name: one partition,
+    // n_own (own[V], past the last vertex); several, the slot past every
+    // partition's cached copies (ghost[n_ghost_total]). The slot holds the
+    // merge's identity (0 for sums, INF for minima) and is never written by
+    // a superstep, so padding needs no test in the kernel.
+    uint32_t pad_id;
+    uint32_t pad1;
 };
 
 // Accumulators of one superstep (one ring slot).
@@ -106,7 +115,10 @@ struct StepStats {
     unsigned long long list_ne;
     unsigned long long pushed;                    // 1: the superstep ran in push direction,
     unsigned long long push_edges;                //    relaxing this many out-edges
-    unsigned long long pad[3];
+    unsigned long long exchanged;                 // 1 once the superstep's exchange between
+                                                  // partitions ran (skipped or not)
+    unsigned long long downloads;                 // copies the superstep used that were not cached
+    unsigned long long pad[1];
 };
 __host__ __device__ constexpr unsigned long long list_pack(uint32_t items, uint32_t edges) {
     return ((unsigned long long)items << 32) | edges;
@@ -152,6 +164,7 @@ struct SuperstepArgs {
     StepStats* stats_clear;      // slot zeroed for the superstep after next
     uint32_t* err;               // device error word
     uint64_t timeout_ns;         // limit of any device-side wait
+    uint32_t force_timeout;      // injected fault: every wait gives up at once (then drains)
     uint32_t check_bounds;
     float damping;
     double inv_n;                // 1 / N
@@ -165,6 +178,8 @@ struct SellArgs {
     const HubPart* hubs;
     uint32_t n_hubs;
     const PartDev* parts;
+    uint32_t n_parts;            // 1: the single-partition kernel (no cached copies, no bitmap)
+    uint32_t n_vertices;         // V: the first cached-copy slot of the push direction
     // superstep t reads value buffer t & 1, stat slot t % kStatRing and
     // frontier list t & 1; it writes buffer / list (t + 1) & 1 and slot t + 1,
     // and clears slot t + 2
@@ -185,12 +200,13 @@ struct SellArgs {
     double inv_n;
     uint32_t ppr_source;         // PageRank: kInf; personalized PageRank: the source vertex
     uint32_t early_exit;         // 1: a superstep (t > 0) after a quiet one returns at once
-    // SSSP / CC on one partition: fc.list_out != nullptr turns the frontier
-    // lists on (the kernel points list_in / list_out at lists[]); the
-    // out-edge copy is what the push direction reads
+    // SSSP / CC: fc.list_out != nullptr turns the frontier lists on (the
+    // kernel points list_in / list_out at lists[]); the out-edge copy is
+    // what the push direction reads. Its sources are slots: the V vertices,
+    // then (several partitions) the cached copies, slot V + g for copy g.
     FrontierCfg fc;
-    const uint32_t* out_ptr;     // [V + 1] out-edge offsets, internal ids
-    const uint32_t* out_dst;     // [E] destinations, grouped by source
+    const uint32_t* out_ptr;     // [slots + 1] out-edge offsets, internal ids
+    const uint32_t* out_dst;     // [E] destinations (vertices), grouped by source slot
     const uint32_t* out_w;       // [E] weights, or nullptr (CC)
 };
 
@@ -328,7 +344,7 @@ struct SyncArgs {
     const uint32_t* ghost_gid;        // [n_ghost] global id of each cached copy (sorted per partition)
     uint32_t n_ghost;                 // cached copies over all partitions
     uint32_t* ghost;                  // [n_ghost] caches to update
-    const uint32_t* pull_list;        // the cached copies (ghost indices, ascending), or nullptr = all
+    const uint8_t* cached;            // [n_ghost] LRU flags (bit 0: cached), or nullptr = all cached
     uint32_t n_pull;
     uint32_t* gdq_ids;                // [sum of boundary counts]
     uint32_t* gdq_vals;
@@ -339,6 +355,11 @@ struct SyncArgs {
     uint32_t* done_ctr;               // arrival counter of the count kernel
     uint32_t blocks_x;
     StepStats* stats_out;
+    // frontier lists on (push direction possible): every cached copy whose
+    // vertex changed joins the next frontier as slot n_vertices + g
+    FrontierCfg fc;                   // fc.list_out = the next superstep's list, or nullptr
+    const uint32_t* out_ptr;          // slot out-edge offsets
+    uint32_t n_vertices;
 };
 
 // ------------------------------------------------------------ launchers
@@ -352,12 +373,15 @@ cudaError_t launch_outdeg(const PartDev& p, const uint32_t* d_src, const uint32_
                           uint32_t* d_outdeg, cudaStream_t s);
 cudaError_t launch_csc_import(const uint64_t* cp64, uint32_t n, uint64_t n_edges, uint32_t* cp32,
                               const uint32_t* src, uint32_t n_local, uint32_t* err, cudaStream_t s);
+// sources >= n_local set kErrBounds; offsets that do not run from 0 to n_edges
+// without decreasing set kErrInput
 cudaError_t launch_validate_csc(const uint32_t* d_col_ptr, uint32_t n_own, const uint32_t* d_src,
                                 uint64_t n_edges, uint32_t n_local, uint32_t* d_err, cudaStream_t s);
 
 cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n_vertices, uint32_t source,
                                uint32_t* own_cur, float* rank_cur, const uint32_t* outdeg,
                                StepStats* stats0, const uint32_t* label_of, cudaStream_t s);
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, cudaStream_t s);   // p[0 .. n) = v
 cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* ghost_gid_all,
                                const uint32_t* own_cur, uint32_t* ghost, cudaStream_t s);
 
@@ -376,20 +400,61 @@ cudaError_t launch_run_control(RunCtl* ctl, const StepStats* ring, cudaGraphCond
 size_t superstep_smem_bytes(Algo a, uint32_t max_items);
 
 cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);
-// copies not kept in a partition's cache: ghost[i] = own_val[ghost_gid[i]]
-// for every ghost index i of list[0 .. n)
-cudaError_t launch_download(const uint32_t* list, uint32_t n, const uint32_t* ghost_gid, const uint32_t* own_val,
-                            uint32_t* ghost, cudaStream_t s);
+
+// LRU-based caching under a budget (lru.cu): the superstep-boundary update of
+// every partition's cached copies. Weights saturate at kLruWMax.
+constexpr uint32_t kLruWMax = 65535;
+constexpr uint32_t kLruBins = kLruWMax + 1;
+struct LruPart {
+    uint32_t cand;      // candidates (cached or used) at this boundary
+    uint32_t w_star;    // the lowest weight kept
+    uint32_t ties;      // candidates of weight w_star kept (lowest ids first); kInf = all candidates
+    uint32_t pad;
+};
+struct LruArgs {
+    uint32_t n_parts, n_ghost;
+    const uint32_t* ghost_base;       // [n_parts + 1] first copy of each partition
+    const uint32_t* ghost_gid;        // [n_ghost] vertex of each copy (ascending per partition)
+    const uint32_t* reads;            // [n_ghost] the partition's in-edges from that vertex
+    uint32_t* weight;                 // [n_ghost]
+    uint8_t* flags;                   // [n_ghost] bit 0 cached, bit 1 candidate (transient)
+    uint32_t* ghost;                  // [n_ghost] copy values (downloads write here)
+    const uint32_t* own_val;          // owners' current values
+    // the frontier of the coming superstep: every vertex, a bitmap, or one vertex
+    uint32_t frontier_all;
+    const uint32_t* frontier_bits;
+    uint32_t frontier_one;
+    uint32_t capacity;                // copies kept per partition
+    uint32_t* hist;                   // [n_parts][kLruBins], zero between boundaries
+    LruPart* part_state;              // [n_parts], cand zero between boundaries
+    uint32_t* tie;                    // [n_ghost]
+    uint32_t* tie_scan;               // [n_ghost + 1]
+    uint32_t* scan_scratch;           // (n_ghost + 2047) / 2048 + 1 words
+    StepStats* stats_out;             // `downloads` of the coming superstep
+    const StepStats* quiet_check;     // non-null: no-op when that superstep changed nothing
+};
+cudaError_t launch_lru_boundary(const LruArgs& a, uint32_t max_ghosts_per_part, cudaStream_t s);
 
 // push direction (frontier.cu)
 struct RowSource;
 // out-edge copy of the CSC `in` (rows renumbered as the layout build does):
 // out_ptr = exclusive scan of outdeg (internal ids); scratch holds
 // out_edges_scratch_words(n, n_edges) words
-cudaError_t launch_out_edges(const RowSource& in, uint32_t n, uint64_t n_edges, const uint32_t* outdeg,
-                             uint32_t* out_ptr, uint32_t* scratch, uint32_t* out_dst, uint32_t* out_w,
-                             cudaStream_t s);
-size_t out_edges_scratch_words(uint32_t n, uint64_t n_edges);
+// (rows: n, sources: n_src >= n; out_ptr[n_src + 1])
+cudaError_t launch_out_edges(const RowSource& in, uint32_t n, uint32_t n_src, uint64_t n_edges,
+                             const uint32_t* outdeg, uint32_t* out_ptr, uint32_t* scratch, uint32_t* out_dst,
+                             uint32_t* out_w, cudaStream_t s);
+size_t out_edges_scratch_words(uint32_t n_src, uint64_t n_edges);
+// several partitions: the CSC over global rows whose sources are slots
+// (own vertex u -> v_begin + u, cached copy u -> V + ghost_base + u - n_own)
+// and the out-degree of every slot (counted into outdeg, zeroed first)
+cudaError_t launch_unify_csc(const PartDev& p, uint32_t n_vertices, uint64_t edge_base, uint32_t* ucol,
+                             uint32_t* usrc, bool last, cudaStream_t s);
+cudaError_t launch_slot_degrees(const uint32_t* usrc, uint64_t n_edges, uint32_t n_slots, uint32_t* outdeg,
+                                cudaStream_t s);
+// every slot whose value is below INF joins the list (partitioned starts)
+cudaError_t launch_seed_finite(uint32_t n_vertices, uint32_t n_ghost, const uint32_t* own, const uint32_t* ghost,
+                               const uint32_t* out_ptr, const FrontierCfg& f, StepStats* stats, cudaStream_t s);
 // f.list_out <- items of vertex `source` (all vertices when source == kInf);
 // the counts go to stats->list_ne (zeroed here first)
 cudaError_t launch_seed_frontier(uint32_t n, uint32_t source, const uint32_t* out_ptr, const FrontierCfg& f,
@@ -426,7 +491,7 @@ cudaError_t launch_sell_slices(const uint32_t* col_ptr, uint32_t n, const uint32
                                uint32_t* width, uint64_t* off, uint32_t n_slices, cudaStream_t s);
 cudaError_t launch_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
                              const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
-                             uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s);
+                             uint32_t pad_id, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s);
 cudaError_t launch_hub_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t* hub_out, const uint32_t* hub_cnt,
                             const uint32_t* hub_base, uint32_t* hub_list, uint32_t n_hub_rows, uint32_t T,
                             uint32_t* part_off, cudaStream_t s);

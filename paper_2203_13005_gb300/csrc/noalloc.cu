@@ -19,6 +19,7 @@
 // on the array and must not be made.
 #include <mutex>
 
+#include "fault.hpp"
 #include "gxp_internal.hpp"
 
 namespace gxp {
@@ -90,6 +91,20 @@ gxp_status scratch_for_current_device(unsigned char** out) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+bool overlap(const void* a, const void* b, size_t bytes) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+// Read the scratch's error word (enqueued after the kernels that set it) and
+// wait for the stream.
+gxp_status read_error(const Layout& L, cudaStream_t s, uint32_t* err) {
+    if (cudaMemcpyAsync(err, L.err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GXP_E_CUDA;
+    return GXP_OK;
+}
+
 }  // namespace
 }  // namespace gxp
 
@@ -104,6 +119,7 @@ extern "C" GXP_API gxp_status gxp_superstep_min_noalloc(gxp_algo algo, uint32_t 
         return GXP_E_INVAL;
     if (!aligned16(d_col_ptr) || !aligned16(d_cur) || (d_src && !aligned16(d_src)) || (d_w && !aligned16(d_w)))
         return GXP_E_INVAL;
+    if (overlap(d_cur, d_next, 4ull * n_vertices)) return GXP_E_INVAL;   // Jacobi: two distinct buffers
     const uint32_t n_tiles = tile_count(n_vertices, n_edges, kNoAllocTileItems);
     if ((uint64_t)n_tiles > kNoAllocMaxTiles) return GXP_E_INVAL;   // beyond the scratch's fixed size
     unsigned char* base = nullptr;
@@ -118,6 +134,14 @@ extern "C" GXP_API gxp_status gxp_superstep_min_noalloc(gxp_algo algo, uint32_t 
     if (n_tiles && cudaMemsetAsync(L.hub_cnt, 0, 4ull * n_tiles, s) != cudaSuccess) return GXP_E_CUDA;
     const PartDev pd{d_col_ptr, d_src, algo == GXP_ALGO_SSSP ? d_w : nullptr, n_vertices, 0u, 0u, 0u, n_edges};
     if (cudaMemcpyAsync(L.part, &pd, sizeof(pd), cudaMemcpyHostToDevice, s) != cudaSuccess) return GXP_E_CUDA;
+    // The tiles are cut from the offsets and the kernel stages them with bulk
+    // copies sized from those cuts: check the CSC before either runs.
+    uint32_t err = 0;
+    if (launch_validate_csc(d_col_ptr, n_vertices, d_src, n_edges, n_vertices, L.err, s) != cudaSuccess)
+        return GXP_E_CUDA;
+    if ((st = read_error(L, s, &err)) != GXP_OK) return st;
+    if (err & kErrInput) return GXP_E_INVAL;
+    if (err & kErrBounds) return GXP_E_BOUNDS;
     if (launch_build_tiles(d_col_ptr, n_vertices, (uint32_t)n_edges, kNoAllocTileItems, kNoAllocHubItems, 0u, 0u,
                            n_tiles, L.tiles, L.cuts, s) != cudaSuccess)
         return GXP_E_CUDA;
@@ -137,17 +161,16 @@ extern "C" GXP_API gxp_status gxp_superstep_min_noalloc(gxp_algo algo, uint32_t 
     args.stats_clear = nullptr;
     args.err = L.err;
     args.timeout_ns = 2000000000ull;
+    args.force_timeout = fault_plan_from_env().timeout ? 1u : 0u;
     args.check_bounds = 1;
     args.max_items = kNoAllocTileItems + kNoAllocHubItems;
     if (launch_superstep(a, args, superstep_smem_bytes(a, args.max_items), s) != cudaSuccess) return GXP_E_CUDA;
 
     StepStats host_stats;
-    uint32_t err = 0;
-    if (cudaMemcpyAsync(&host_stats, L.stats, sizeof(host_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&err, L.err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (cudaMemcpyAsync(&host_stats, L.stats, sizeof(host_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return GXP_E_CUDA;
-    if (err & kErrTimeout) return GXP_E_TIMEOUT;
+    if ((st = read_error(L, s, &err)) != GXP_OK) return st;
+    if (err & (kErrTimeout | kErrDrain)) return GXP_E_TIMEOUT;
     if (err & kErrBounds) return GXP_E_BOUNDS;
     if (n_changed) {
         unsigned long long c = 0;

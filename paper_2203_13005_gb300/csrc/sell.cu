@@ -23,6 +23,10 @@
 
 #include <algorithm>
 
+#ifndef PR_ITEMS
+#define PR_ITEMS 1
+#endif
+
 namespace gxp {
 namespace {
 
@@ -32,10 +36,13 @@ constexpr int kSellWarps = kSellBlock / 32;
 
 template <Algo A> struct Ops;
 
+// kMinBlocks: CTAs per SM the register budget is fitted to
 template <> struct Ops<Algo::SSSP> {
     using T = uint32_t;
     static constexpr bool kWeighted = true;
     static constexpr int kUnroll = 8;
+    static constexpr int kMinBlocks = 6;
+    static constexpr int kItems = 1;
     __device__ static T ident() { return kInf; }
     __device__ static T combine(T a, T b) { return min(a, b); }
     __device__ static T from_bits(uint32_t x) { return x; }
@@ -53,6 +60,8 @@ template <> struct Ops<Algo::CC> {
     using T = uint32_t;
     static constexpr bool kWeighted = false;
     static constexpr int kUnroll = 8;
+    static constexpr int kMinBlocks = 6;
+    static constexpr int kItems = 1;
     __device__ static T ident() { return kInf; }
     __device__ static T combine(T a, T b) { return min(a, b); }
     __device__ static T from_bits(uint32_t x) { return x; }
@@ -60,10 +69,15 @@ template <> struct Ops<Algo::CC> {
     __device__ static T gen(uint32_t lu, uint32_t) { return lu; }
 };
 
+#ifndef PR_UNROLL
+#define PR_UNROLL 8
+#endif
 template <> struct Ops<Algo::PR> {
     using T = float;
     static constexpr bool kWeighted = false;
-    static constexpr int kUnroll = 8;
+    static constexpr int kUnroll = PR_UNROLL;
+    static constexpr int kMinBlocks = 6;
+    static constexpr int kItems = PR_ITEMS;   // work items per warp
     __device__ static T ident() { return 0.0f; }
     __device__ static T combine(T a, T b) { return a + b; }
     __device__ static T from_bits(uint32_t x) { return __uint_as_float(x); }
@@ -71,6 +85,37 @@ template <> struct Ops<Algo::PR> {
     // The message array already holds r[u] / outdeg(u) (written by Apply).
     __device__ static T gen(uint32_t cu, uint32_t) { return __uint_as_float(cu); }
 };
+
+// Loads of the edge stream (source ids, weights: each read once per
+// superstep) and of the gathered values.
+#ifndef SELL_IDX_LOAD
+#define SELL_IDX_LOAD 0
+#endif
+#ifndef SELL_GATHER_LOAD
+#define SELL_GATHER_LOAD 0
+#endif
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
+#if SELL_IDX_LOAD == 1
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#elif SELL_IDX_LOAD == 2
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#else
+    return __ldcs(p);
+#endif
+}
+__device__ __forceinline__ uint32_t ld_value(const uint32_t* p) {
+#if SELL_GATHER_LOAD == 1
+    uint32_t v;
+    asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
 
 __device__ __forceinline__ uint32_t arrive_acq_rel(uint32_t* ctr) {
     uint32_t old;
@@ -85,8 +130,38 @@ __device__ __forceinline__ typename Op::T warp_all(typename Op::T v) {
     return v;
 }
 
-template <Algo A>
-__global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
+// Exact warp sum of 64-bit values below 2^62 (the fixed-point sums and
+// counts): three 27-bit limbs, each summed by one warp reduction.
+__device__ __forceinline__ unsigned long long warp_sum_u62(unsigned long long x) {
+    const uint32_t a0 = (uint32_t)(x & 0x7FFFFFFull), a1 = (uint32_t)((x >> 27) & 0x7FFFFFFull),
+                   a2 = (uint32_t)(x >> 54);
+    return (unsigned long long)__reduce_add_sync(kFull, a0) +
+           ((unsigned long long)__reduce_add_sync(kFull, a1) << 27) +
+           ((unsigned long long)__reduce_add_sync(kFull, a2) << 54);
+}
+
+// The value of local source u of partition P: an owned vertex, a cached
+// copy, or (the padding id of empty slots) the identity slot. kOne: one
+// partition, whose local ids are global ids and whose padding id is V.
+template <bool kOne>
+struct Source {
+    const uint32_t* own;    // own_cur + v_begin
+    const uint32_t* copy;   // ghost + ghost_base - n_own: copy(u) for u >= n_own
+    uint32_t n_own;
+    __device__ __forceinline__ Source(const uint32_t* own_cur, const uint32_t* ghost, const PartDev& P)
+        : own(own_cur + P.v_begin), copy(ghost + P.ghost_base - (ptrdiff_t)P.n_own), n_own(P.n_own) {}
+    __device__ __forceinline__ const uint32_t* at(uint32_t u) const {
+        if constexpr (kOne) return own + u;
+        else return u < n_own ? own + u : copy + u;
+    }
+};
+
+// Superstep over the sliced-ELL layout (see the top of the file). kOne: a
+// single partition (no cached copies); kCheck: range-check every source id
+// (gxp_config.check_bounds), setting kErrBounds instead of loading.
+template <Algo A, bool kOne, bool kCheck>
+__global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : Ops<A>::kMinBlocks)
+    k_sell(const SellArgs a) {
     using Op = Ops<A>;
     using T = typename Op::T;
     constexpr int kU = Op::kUnroll;
@@ -112,33 +187,40 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats + (t + 2) % kStatRing);
         for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
     }
-    if (a.early_exit && t > 0) {
-        // min-label algorithms at a fixed point: nothing can change any more
-        unsigned long long c = stats_in->changed[lane] + stats_in->changed[lane + 32];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-        if (c == 0ull) return;   // same for every thread of the grid
-    }
+    __shared__ float s_base[2];
+    __shared__ bool s_quiet;
     if (tid == 0) {
         s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
         s_done = 0u;
+        s_quiet = false;
     }
-    float base = 0.0f, base_src = 0.0f;
+    if (a.early_exit && t > 0 && warp == 0) {
+        // min-label algorithms at a fixed point: nothing can change any more
+        const unsigned long long c = warp_sum_u62(stats_in->changed[lane] + stats_in->changed[lane + 32]);
+        if (lane == 0 && c == 0ull) s_quiet = true;
+    }
     if constexpr (A == Algo::PR) {
-        // from the exact dangling-mass sum D of the current ranks: PageRank
-        // spreads (1-d) + d*D evenly, (1-d)/N + d*D/N to every vertex;
-        // personalized PageRank returns all of it to the source vertex
-        unsigned long long sd = stats_in->dangling_fx[lane] + stats_in->dangling_fx[lane + 32];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(kFull, sd, o);
-        const double d = (double)a.damping;
-        if (a.ppr_source == kInf) {
-            base = base_src = (float)((1.0 - d) * a.inv_n + d * fx_to_double(sd) * a.inv_n);
-        } else {
-            base_src = (float)((1.0 - d) + d * fx_to_double(sd));
+        // warp 0, for the CTA: from the exact dangling-mass sum D of the
+        // current ranks, PageRank spreads (1-d) + d*D evenly, (1-d)/N + d*D/N
+        // to every vertex; personalized PageRank returns all of it to the
+        // source vertex
+        if (warp == 0) {
+            const unsigned long long sd =
+                warp_sum_u62(stats_in->dangling_fx[lane] + stats_in->dangling_fx[lane + 32]);
+            const double d = (double)a.damping;
+            if (lane == 0) {
+                if (a.ppr_source == kInf) {
+                    s_base[0] = s_base[1] = (float)((1.0 - d) * a.inv_n + d * fx_to_double(sd) * a.inv_n);
+                } else {
+                    s_base[0] = 0.0f;
+                    s_base[1] = (float)((1.0 - d) + d * fx_to_double(sd));
+                }
+            }
         }
     }
     __syncthreads();
+    if (s_quiet) return;   // same for every thread of the grid
+    const float base = s_base[0], base_src = s_base[1];
     const float damping = a.damping;
 
     uint32_t n_changed = 0;
@@ -159,7 +241,8 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
             l1 += fn > fo ? fn - fo : fo - fn;
             if (od == 0u) dang += fn;
             // message changes are tracked only when a bitmap is wanted (partitions)
-            return a.changed_bits != nullptr && cb != own_cur[gid];
+            if constexpr (kOne) return false;
+            else return a.changed_bits != nullptr && cb != own_cur[gid];
         } else {
             const uint32_t old = own_cur[gid];
             const uint32_t nw = min(old, (uint32_t)m);
@@ -167,57 +250,65 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
             return nw != old;
         }
     };
-    // gather the value of local source u of partition P
-    auto gather = [&](const PartDev& P, uint32_t u, bool& ok) -> uint32_t {
-        ok = true;
-        if (a.check_bounds && u >= P.n_own + P.n_ghost) {
-            atomicOr(a.err, kErrBounds);
-            ok = false;
-            return 0u;
+    // kCheck: a source id outside the partition's ids (and not its padding id)
+    // is reported and replaced by the padding id
+    auto checked = [&](const PartDev& P, uint32_t u) -> uint32_t {
+        if constexpr (kCheck) {
+            if (u >= P.n_own + P.n_ghost && u != P.pad_id) {
+                atomicOr(a.err, kErrBounds);
+                return P.pad_id;
+            }
         }
-        return __ldg(u < P.n_own ? own_cur + P.v_begin + u : a.ghost + P.ghost_base + (u - P.n_own));
+        return u;
     };
 
-    const uint32_t gw = blockIdx.x * kSellWarps + (uint32_t)warp;
+    // a CTA takes kSellWarps * kItems consecutive work items, warp w the items
+    // w, w + kSellWarps, ...: the heavy-first order still spreads over the warps
+    constexpr int kItems = Op::kItems;
+    const uint32_t gw0 = blockIdx.x * (kSellWarps * kItems) + (uint32_t)warp;
+    const uint32_t gw = gw0;
     bool f_has = false;   // pull direction with frontier lists: this lane's changed vertex
     uint32_t f_v = 0;
     bool pushed = false;
     if constexpr (A != Algo::PR) {
         if (push_chosen(fc, stats_in)) {   // same choice in every thread of the grid
             const uint32_t c = push_superstep<Op::kWeighted>(fc, a.out_ptr, a.out_dst, a.out_w, own_cur,
-                                                             own_nxt, stats_in, stats_out, gw,
-                                                             (uint64_t)gridDim.x * kSellWarps, lane);
+                                                             own_nxt, a.ghost, a.n_vertices,
+                                                             kOne ? nullptr : a.changed_bits, stats_in, stats_out,
+                                                             gw, (uint64_t)gridDim.x * kSellWarps, lane);
             if (lane == 0) n_changed += c;
             pushed = true;
         }
     }
+#pragma unroll 1
+    for (int it = 0; it < kItems; ++it) {
+    const uint32_t gw = gw0 + (uint32_t)it * kSellWarps;
     if (pushed) {
         // the frontier's out-edges were relaxed above
     } else if (gw < a.n_hubs) {
         // ============================================================ hub part
         const HubPart hp = a.hubs[gw];
-        const PartDev P = a.parts[hp.part];
+        const PartDev P = a.parts[kOne ? 0 : hp.part];
+        const Source<kOne> S(own_cur, a.ghost, P);
         const uint32_t* src = P.hsrc + hp.e0;
         const uint32_t* wts = P.hw + hp.e0;
         T acc = Op::ident();
         for (uint32_t jb = 0; jb < hp.ne; jb += 32u * kU) {
             uint32_t u[kU], x[kU], wv[kU];
-            bool ok[kU];
 #pragma unroll
             for (int q = 0; q < kU; ++q) {
                 const uint32_t j = jb + (uint32_t)q * 32u + (uint32_t)lane;
-                u[q] = kSellPad;
-                wv[q] = 0u;
-                if (j < hp.ne) {
-                    u[q] = __ldcs(src + j);
-                    if (Op::kWeighted) wv[q] = __ldcs(wts + j);
-                }
+                const bool in = j < hp.ne;
+                u[q] = in ? ld_stream(src + j) : 0u;
+                wv[q] = (Op::kWeighted && in) ? ld_stream(wts + j) : 0u;
             }
 #pragma unroll
-            for (int q = 0; q < kU; ++q) x[q] = u[q] != kSellPad ? gather(P, u[q], ok[q]) : (ok[q] = false, 0u);
+            for (int q = 0; q < kU; ++q)
+                x[q] = jb + (uint32_t)q * 32u + (uint32_t)lane < hp.ne ? ld_value(S.at(checked(P, u[q])))
+                                                                        : Op::to_bits(Op::ident());
 #pragma unroll
             for (int q = 0; q < kU; ++q)
-                if (ok[q]) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+                if (jb + (uint32_t)q * 32u + (uint32_t)lane < hp.ne) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
         }
         T total = warp_all<Op>(acc);
         bool do_apply = hp.nparts == 1u;
@@ -241,7 +332,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
         const bool ch = do_apply && lane == 0 && apply(P, hp.v, total);
         if (ch) {
             ++n_changed;
-            if (a.changed_bits) {
+            if (!kOne && a.changed_bits) {
                 const uint32_t g = P.v_begin + hp.v;
                 atomicOr(&a.changed_bits[g >> 5], 1u << (g & 31u));
             }
@@ -255,28 +346,40 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
     } else if (gw - a.n_hubs < a.n_slices) {
         // =============================================================== slice
         const SellSlice sl = a.slices[gw - a.n_hubs];
-        const PartDev P = a.parts[sl.part];
+        const PartDev P = a.parts[kOne ? 0 : sl.part];
+        const Source<kOne> S(own_cur, a.ghost, P);
         const uint32_t row = P.perm[sl.row0 + lane];
         const uint32_t* col = P.sell_src + sl.off + lane;
         const uint32_t* wcol = P.sell_w + sl.off + lane;
         T acc = Op::ident();
-        for (uint32_t kb = 0; kb < sl.width; kb += kU) {
+        uint32_t kb = 0;
+        // whole batches of kU columns: no tests, kU gathers in flight per lane
+        for (; kb + kU <= sl.width; kb += kU) {
             uint32_t u[kU], x[kU], wv[kU];
-            bool ok[kU];
 #pragma unroll
             for (int q = 0; q < kU; ++q) {
-                u[q] = kSellPad;
-                wv[q] = 0u;
-                if (kb + q < sl.width) {
-                    u[q] = __ldcs(col + 32u * (kb + q));
-                    if (Op::kWeighted) wv[q] = __ldcs(wcol + 32u * (kb + q));
-                }
+                u[q] = ld_stream(col + 32u * (kb + q));
+                wv[q] = Op::kWeighted ? ld_stream(wcol + 32u * (kb + q)) : 0u;
             }
 #pragma unroll
-            for (int q = 0; q < kU; ++q) x[q] = u[q] != kSellPad ? gather(P, u[q], ok[q]) : (ok[q] = false, 0u);
+            for (int q = 0; q < kU; ++q) x[q] = ld_value(S.at(checked(P, u[q])));
+#pragma unroll
+            for (int q = 0; q < kU; ++q) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+        }
+        if (kb < sl.width) {   // the last, partial batch: loads past the width are predicated off
+            uint32_t u[kU], x[kU], wv[kU];
+#pragma unroll
+            for (int q = 0; q < kU; ++q) {
+                const bool in = kb + q < sl.width;
+                u[q] = in ? ld_stream(col + 32u * (kb + q)) : 0u;
+                wv[q] = (Op::kWeighted && in) ? ld_stream(wcol + 32u * (kb + q)) : 0u;
+            }
 #pragma unroll
             for (int q = 0; q < kU; ++q)
-                if (ok[q]) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+                x[q] = kb + q < sl.width ? ld_value(S.at(checked(P, u[q]))) : Op::to_bits(Op::ident());
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+                if (kb + q < sl.width) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
         }
         const bool ch = row != kSellPad && apply(P, row, acc);
         const unsigned chm = __ballot_sync(kFull, ch);
@@ -287,7 +390,7 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
                 f_v = P.v_begin + row;
             }
         }
-        if (ch && a.changed_bits) {
+        if (!kOne && ch && a.changed_bits) {
             // one atomic per bitmap word touched by this warp
             const uint32_t g = P.v_begin + row;
             const unsigned grp = __match_any_sync(chm, g >> 5);
@@ -295,17 +398,17 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
             if ((uint32_t)lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(&a.changed_bits[g >> 5], bits);
         }
     }
+    }   // work items
 
     if constexpr (A != Algo::PR) {
         if (fc.list_out && !pushed) {   // uniform over the grid
             // the changed vertices join the next frontier: one atomic per CTA
-            // reserves the CTA's items, each warp writes its own
-            const uint32_t deg = f_has ? __ldg(a.outdeg + f_v) : 0u;
+            // reserves the CTA's items, each warp writes its own; a vertex's
+            // items cover the out-edges of its slot
+            const uint32_t deg = f_has ? __ldg(a.out_ptr + f_v + 1) - __ldg(a.out_ptr + f_v) : 0u;
             const uint32_t nit = f_has ? frontier_items(deg) : 0u;
             const uint32_t incl = warp_inclusive_scan(nit, lane);
-            uint32_t edges = deg;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) edges += __shfl_xor_sync(kFull, edges, o);
+            const uint32_t edges = __reduce_add_sync(kFull, deg);
             if (lane == 31) {
                 s_ftot[warp] = incl;
                 s_fedges[warp] = edges;
@@ -327,14 +430,10 @@ __global__ void __launch_bounds__(kSellBlock) k_sell(const SellArgs a) {
     }
 
     // warp totals -> CTA totals in shared memory; the last warp flushes them
-    unsigned long long c64 = n_changed;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c64 += __shfl_xor_sync(kFull, c64, o);
-        if constexpr (A == Algo::PR) {
-            l1 += __shfl_xor_sync(kFull, l1, o);
-            dang += __shfl_xor_sync(kFull, dang, o);
-        }
+    const unsigned long long c64 = __reduce_add_sync(kFull, n_changed);
+    if constexpr (A == Algo::PR) {
+        l1 = warp_sum_u62(l1);
+        dang = warp_sum_u62(dang);
     }
     if (lane == 0) {
         if (c64) atomicAdd(&s_acc[0], c64);
@@ -384,15 +483,29 @@ cudaError_t launch_run_control(RunCtl* ctl, const StepStats* ring, cudaGraphCond
     return cudaGetLastError();
 }
 
+template <Algo A>
+static void launch_sell(const SellArgs& args, bool one, uint32_t grid, cudaStream_t s) {
+    if (one) {
+        if (args.check_bounds) k_sell<A, true, true><<<grid, kSellBlock, 0, s>>>(args);
+        else k_sell<A, true, false><<<grid, kSellBlock, 0, s>>>(args);
+    } else {
+        if (args.check_bounds) k_sell<A, false, true><<<grid, kSellBlock, 0, s>>>(args);
+        else k_sell<A, false, false><<<grid, kSellBlock, 0, s>>>(args);
+    }
+}
+
 cudaError_t launch_superstep_sell(Algo alg, const SellArgs& args, cudaStream_t s) {
     const uint64_t work = (uint64_t)args.n_hubs + args.n_slices;
     // an empty layout still runs one block: it clears the stat slot two
     // supersteps ahead (and the step may live in device memory)
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, (work + kSellWarps - 1) / kSellWarps);
+    const uint64_t per_cta = (uint64_t)kSellWarps * (alg == Algo::PR ? Ops<Algo::PR>::kItems : 1);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, (work + per_cta - 1) / per_cta);
+    const bool one = args.n_parts == 1;
     switch (alg) {
-        case Algo::SSSP: k_sell<Algo::SSSP><<<grid, kSellBlock, 0, s>>>(args); break;
-        case Algo::CC: k_sell<Algo::CC><<<grid, kSellBlock, 0, s>>>(args); break;
-        case Algo::PR: k_sell<Algo::PR><<<grid, kSellBlock, 0, s>>>(args); break;
+        case Algo::SSSP: launch_sell<Algo::SSSP>(args, one, grid, s); break;
+        case Algo::CC: launch_sell<Algo::CC>(args, one, grid, s); break;
+        case Algo::PR: launch_sell<Algo::PR>(args, one, grid, s); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

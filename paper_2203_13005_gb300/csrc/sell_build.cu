@@ -13,7 +13,9 @@
 //     share power-of-two bins), and the list of hub rows (more than H in-edges).
 //  3. k_sell_slices: slices of 32 consecutive sorted rows, their widths and
 //     row slots; k_scan_widths: element offsets of the slices.
-//  4. k_sell_fill: the column-major slice arrays (one warp per slice).
+//  4. k_sell_fill: the column-major slice arrays (one warp per slice); the
+//     empty slots of rows shorter than their slice hold the partition's
+//     padding id, whose value slot always holds the merge's identity.
 //  5. k_hub_rows / k_scan_parts / k_hub_parts: hub rows in id order, split
 //     into parts of T edges.
 //  6. k_order_count / k_order_offsets / k_order_scatter: all partitions'
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(1024) k_scan_widths(const uint32_t* width, uin
 // one warp per slice: column-major fill of sources (and weights), descriptors
 __global__ void k_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
                             const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
-                            uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc) {
+                            uint32_t pad_id, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -368,7 +370,7 @@ __global__ void k_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const
         const uint32_t d = r != kSellPad ? col_ptr[r + 1] - b : 0u;
         for (uint32_t k = 0; k < wd; ++k) {
             const bool has = k < d;
-            sell_src[o + 32ull * k + lane] = has ? ssrc[b + k] : kSellPad;
+            sell_src[o + 32ull * k + lane] = has ? ssrc[b + k] : pad_id;
             if (sell_w) sell_w[o + 32ull * k + lane] = has ? sw[b + k] : 0u;
         }
         if (lane == 0) desc[s] = SellSlice{part, (uint32_t)(s * 32), wd, 0u, o};
@@ -637,10 +639,10 @@ cudaError_t launch_sell_slices(const uint32_t* col_ptr, uint32_t n, const uint32
 
 cudaError_t launch_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
                              const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
-                             uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s) {
+                             uint32_t pad_id, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s) {
     if (n_slices == 0) return cudaSuccess;
     k_sell_fill<<<grid_warps(n_slices, 256), 256, 0, s>>>(col_ptr, ssrc, sw, perm, width, off, n_slices, part,
-                                                          sell_src, sell_w, desc);
+                                                          pad_id, sell_src, sell_w, desc);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // with their admission / superstep / retirement loop, and the thread-safe
 // query calls.
 #include "server.hpp"
+#include "trace.hpp"
 
 #include <omp.h>
 
@@ -406,6 +407,7 @@ void Server::lane_loop(Lane& L) {
 // One superstep of a lane: initialise admitted slots, advance every busy
 // slot, retire finished ones. Only this lane's thread touches its slots.
 void Server::lane_step(Lane& L, ServedGraph& G, uint64_t admit) {
+    TraceRange trace_("gxp serving lane superstep");
     const bool sssp = L.kind == GXP_QUERY_SSSP;
     const cudaStream_t st = L.stream;
     if (admit) {

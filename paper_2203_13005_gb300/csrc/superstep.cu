@@ -33,6 +33,7 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarps = kBlock / 32;
 constexpr int kStages = 2;
+constexpr uint64_t kDrainNs = 4000000000ull;   // smallest limit of the give-up drain (4 s)
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -78,8 +79,11 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait for phase `parity` of `bar`, giving up after timeout_ns (and after a
-// fixed iteration cap as a backstop). Returns false on give-up.
-__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+// fixed iteration cap as a backstop). Returns false on give-up. With
+// `give_up` set (the injected timeout fault) it gives up at once, whether or
+// not the phase has completed.
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t timeout_ns, bool give_up = false) {
+    if (give_up) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < (1u << 26); ++it) {
@@ -305,12 +309,21 @@ __global__ void __launch_bounds__(kBlock) k_superstep(const SuperstepArgs args) 
     uint32_t i = 0;
     for (uint32_t tix = t_begin; tix < t_end; ++tix, ++i) {
         const int s = (int)(i % kStages);
-        const bool ok = mbar_wait_bounded(&s_bar[warp][s], (i / kStages) & 1u, args.timeout_ns);
+        const bool ok = mbar_wait_bounded(&s_bar[warp][s], (i / kStages) & 1u, args.timeout_ns,
+                                          args.force_timeout != 0u);
         if (__any_sync(kFull, !ok)) {
             if (lane == 0) atomicOr(args.err, kErrTimeout);
-            // let this warp's copies in flight land before leaving
-            for (uint32_t k = 1; k < (uint32_t)kStages && tix + k < t_end; ++k)
-                mbar_wait_bounded(&s_bar[warp][(i + k) % kStages], ((i + k) / kStages) & 1u, args.timeout_ns);
+            // Before leaving, every copy this warp has issued must land in its
+            // shared memory: those of this tile's stage and of the stages
+            // after it (tiles tix .. tix + kStages - 1). The drain has its own
+            // limit, at least kDrainNs, independent of timeout_ns; a drain
+            // that also runs out is recorded as kErrDrain.
+            const uint64_t drain_ns = args.timeout_ns > kDrainNs ? args.timeout_ns : kDrainNs;
+            for (uint32_t k = 0; k < (uint32_t)kStages && tix + k < t_end; ++k) {
+                const bool landed =
+                    mbar_wait_bounded(&s_bar[warp][(i + k) % kStages], ((i + k) / kStages) & 1u, drain_ns);
+                if (!__all_sync(kFull, landed) && lane == 0) atomicOr(args.err, kErrDrain);
+            }
             break;
         }
         const Tile tile = s_tile[warp][s];
@@ -534,28 +547,20 @@ size_t superstep_smem_bytes(Algo a, uint32_t max_items) {
 
 template <Algo A>
 static cudaError_t launch_persistent(const SuperstepArgs& args, cudaStream_t s) {
-    static int n_sm = 0;
-    static int cached_blocks[3] = {0, 0, 0};
-    static size_t cached_smem[3] = {0, 0, 0};
     const uint32_t nw = warps_per_cta(A, args.max_items);
     if (nw == 0) return cudaErrorInvalidValue;   // a single warp's stages exceed shared memory
     const size_t smem = superstep_smem_bytes(A, args.max_items);
     cudaError_t e = cudaFuncSetAttribute(k_superstep<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const int ai = (int)A;
-    if (cached_smem[ai] != smem || cached_blocks[ai] == 0) {
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_superstep<A>, (int)(32 * nw), smem);
-        if (e != cudaSuccess) return e;
-        cached_blocks[ai] = b > 0 ? b : 1;
-        cached_smem[ai] = smem;
-    }
-    const uint64_t blocks_max = (uint64_t)n_sm * cached_blocks[ai];
+    // SM count and occupancy of the current device, queried per launch (host
+    // threads may drive different GPUs; the queries cost microseconds)
+    int dev = 0, n_sm = 0, blocks = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_superstep<A>, (int)(32 * nw), smem)) !=
+        cudaSuccess)
+        return e;
+    const uint64_t blocks_max = (uint64_t)n_sm * (uint64_t)(blocks > 0 ? blocks : 1);
     const uint64_t blocks_needed = ((uint64_t)args.n_tiles + nw - 1) / nw;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(blocks_max, blocks_needed));
     k_superstep<A><<<grid, 32 * nw, smem, s>>>(args);

@@ -19,7 +19,9 @@ from . import build as _build
 
 # status codes
 GXP_OK, GXP_E_INVAL, GXP_E_NOMEM, GXP_E_CUDA, GXP_E_TIMEOUT = 0, 1, 2, 3, 4
-GXP_E_BOUNDS, GXP_E_STATE, GXP_E_UNSUPPORTED, GXP_E_BUSY = 5, 6, 7, 8
+GXP_E_BOUNDS, GXP_E_STATE, GXP_E_UNSUPPORTED, GXP_E_BUSY, GXP_E_LOST = 5, 6, 7, 8, 9
+# host-side fault injection (gxp_config.fault)
+GXP_FAULT_NONE, GXP_FAULT_ALLOC, GXP_FAULT_H2D, GXP_FAULT_SYNC_DROP, GXP_FAULT_TIMEOUT = 0, 1, 2, 3, 4
 # algorithms and template operators
 GXP_ALGO_SSSP, GXP_ALGO_CC, GXP_ALGO_PAGERANK, GXP_ALGO_PPR, GXP_ALGO_LP = 0, 1, 2, 3, 4
 GXP_GEN_RELAX, GXP_GEN_LABEL, GXP_GEN_CONTRIB = 0, 1, 2
@@ -47,7 +49,8 @@ class gxp_config(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("tile_items", C.c_uint32), ("hub_items", C.c_uint32),
                 ("timeout_ns", C.c_uint64), ("check_bounds", C.c_uint32), ("max_slots", C.c_uint32),
                 ("pipeline_depth", C.c_uint32), ("keep_ids", C.c_uint32), ("direction", C.c_uint32),
-                ("push_div", C.c_uint32), ("cache_slots", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("push_div", C.c_uint32), ("cache_slots", C.c_uint32), ("fault", C.c_uint32),
+                ("fault_at", C.c_uint32), ("reserved", C.c_uint32 * 1)]
 
 
 class gxp_stats(C.Structure):
@@ -56,7 +59,7 @@ class gxp_stats(C.Structure):
                 ("syncs_skipped", C.c_uint64), ("sync_pairs", C.c_uint64), ("last_l1_delta", C.c_double),
                 ("last_dangling", C.c_double), ("last_superstep_ms", C.c_double),
                 ("device_bytes", C.c_uint64), ("push_supersteps", C.c_uint64), ("cache_downloads", C.c_uint64),
-                ("reserved", C.c_uint64 * 4)]
+                ("last_kernel_ms", C.c_double), ("reserved", C.c_uint64 * 3)]
 
 
 # (name, restype, argtypes) of every exported symbol
@@ -76,6 +79,9 @@ SIGNATURES = [
     ("gxp_superstep", _I, [_P, _I, _I, _I, _I, _P]),
     ("gxp_sync", _I, [_P, _U32, _P, _P, _U64, _P, _P]),
     ("gxp_run", _I, [_P, _I, _U32, _F, _U32, _P]),
+    ("gxp_cache_get", _I, [_P, _U32, _P, _U64, _P]),
+    ("gxp_tune_cache_get", _I, [C.c_char_p, C.c_char_p, _P]),
+    ("gxp_tune_cache_put", _I, [C.c_char_p, C.c_char_p, _P]),
     ("gxp_stats_get", _I, [_P, _P]),
     ("gxp_block_size_model", _I, [_D, _D, _D, _D, _U64, _P, _P, _P]),
     ("gxp_superstep_min_noalloc", _I, [_I, _U32, _U64, _P, _P, _P, _P, _P, _P, _P]),
@@ -154,7 +160,8 @@ def block_size_model(k1: float, k2: float, k3: float, a: float, d: int):
 
 class gxp_batch_opts(C.Structure):
     _fields_ = [("streamed", C.c_uint32), ("pipelined", C.c_uint32), ("block_edges", C.c_uint64),
-                ("use_graph", C.c_uint32), ("max_steps", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+                ("use_graph", C.c_uint32), ("max_steps", C.c_uint32), ("tune_cache", C.c_char_p),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class gxp_batch_report(C.Structure):
@@ -162,7 +169,12 @@ class gxp_batch_report(C.Structure):
                 ("ms_total", C.c_double), ("k1", C.c_double), ("k2", C.c_double), ("k3", C.c_double),
                 ("a", C.c_double), ("model_block_edges", C.c_double), ("model_ms", C.c_double),
                 ("sweep_best_ms", C.c_double), ("edges_per_superstep", C.c_uint64),
-                ("reserved", C.c_uint64 * 6)]
+                ("tune_from_cache", C.c_uint64), ("reserved", C.c_uint64 * 5)]
+
+
+class gxp_tune_record(C.Structure):
+    _fields_ = [("k1", C.c_double), ("k2", C.c_double), ("k3", C.c_double), ("a", C.c_double),
+                ("model_block_edges", C.c_double), ("block_edges", C.c_double), ("sweep_best_ms", C.c_double)]
 
 
 class Context:
@@ -170,10 +182,12 @@ class Context:
 
     def __init__(self, device: int = 0, tile_items: int = 0, hub_items: int = 0,
                  check_bounds: bool = False, timeout_ns: int = 0, mem_budget: int = 0, keep_ids: bool = False,
-                 direction: int = GXP_DIR_AUTO, push_div: int = 0, cache_slots: int = 0):
+                 direction: int = GXP_DIR_AUTO, push_div: int = 0, cache_slots: int = 0,
+                 fault: int = GXP_FAULT_NONE, fault_at: int = 0):
         self.lib = load()
         cfg = gxp_config()
         self.lib.gxp_config_default(C.byref(cfg))
+        cfg.fault, cfg.fault_at = fault, fault_at
         cfg.tile_items, cfg.hub_items, cfg.keep_ids = tile_items, hub_items, int(keep_ids)
         cfg.direction, cfg.push_div, cfg.cache_slots = direction, push_div, cache_slots
         cfg.check_bounds, cfg.timeout_ns, cfg.mem_budget = int(check_bounds), timeout_ns, mem_budget
@@ -272,6 +286,16 @@ class Context:
         arr = np.ascontiguousarray(arr)
         self._ck(self.lib.gxp_set_values(self.h, part, _ptr(arr), len(arr)))
 
+    def cache(self, part: int) -> np.ndarray:
+        """Vertex ids of the copies partition `part` holds cached now (ascending)."""
+        n = C.c_uint64()
+        rc = self.lib.gxp_cache_get(self.h, part, None, 0, C.byref(n))
+        if rc not in (GXP_OK, GXP_E_INVAL) or (rc == GXP_E_INVAL and n.value == 0):
+            self._ck(rc)
+        out = np.empty(max(n.value, 1), dtype=np.uint32)
+        self._ck(self.lib.gxp_cache_get(self.h, part, _ptr(out), n.value, C.byref(n)))
+        return out[:n.value]
+
     def sync(self, part: int):
         """(ids, values, skipped) of partition `part`'s last upload (Algorithm 3)."""
         n, sk = C.c_uint64(), C.c_int()
@@ -286,7 +310,7 @@ class Context:
         return ids[:cnt], vals[:cnt], bool(sk.value)
 
     def sssp_batch(self, sources, out=None, streamed=False, pipelined=True, block_edges=0,
-                   use_graph=False, max_steps=0):
+                   use_graph=False, max_steps=0, tune_cache=None):
         """Multi-source SSSP: returns (dist uint32[V][n_sources] (or `out`), report dict)."""
         srcs = np.ascontiguousarray(sources, dtype=np.uint32)
         if out is None:
@@ -294,6 +318,7 @@ class Context:
         o = gxp_batch_opts()
         o.streamed, o.pipelined, o.block_edges = int(streamed), int(pipelined), block_edges
         o.use_graph, o.max_steps = int(use_graph), max_steps
+        o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
         r = gxp_batch_report()
         self._ck(self.lib.gxp_sssp_batch(self.h, _ptr(srcs), len(srcs), _ptr(out), C.byref(o), C.byref(r)))
         return out, {k: getattr(r, k) for k, _ in gxp_batch_report._fields_ if k != "reserved"}

@@ -106,14 +106,23 @@ def test_batch_errors(g12):
 
 
 @pytest.mark.slow
-def test_batch_rmat24_streamed_two_sources_vs_oracle():
+def test_batch_rmat24_streamed_vs_oracle_and_single_source_runs():
+    """The full batched workload (R-MAT 24, 64 sources, edges streamed through
+    the pipeline shuffle): 4 sources against the oracle, and all 64 columns
+    against single-source runs of the superstep engine on the same GPU."""
     wl = synth.MSSSP_RMAT24
     src, dst, w = wl.edges()
     n = wl.n_vertices
     sources = synth.sources_with_out_edges(n, src, 64, wl.seed)
     with _ctx(n, src, dst, w) as c:
         dist, rep = c.sssp_batch(sources, streamed=True, use_graph=True)
-    _check(n, src, dst, w, sources[:2], dist)
+    _check(n, src, dst, w, sources[:4], dist)
+    with gxp.Context(0) as c:
+        c.create_graph(n, 1)
+        c.load_coo(src, dst, w)
+        for j, s in enumerate(sources):
+            c.run(gxp.GXP_ALGO_SSSP, source=int(s))
+            assert np.array_equal(c.values(), dist[:, j]), j
 
 
 def test_batch_wide_weights_unpacked_edges():
@@ -129,3 +138,21 @@ def test_batch_wide_weights_unpacked_edges():
         dist_s, _ = c.sssp_batch(sources, streamed=True, block_edges=5000)
     assert np.array_equal(dist, dist_s)
     _check(n, src, dst, w, sources, dist)
+
+
+def test_batch_tune_cache_skips_the_measurements(tmp_path, g12):
+    """With a tune cache, the first autotuned run measures and stores its
+    coefficients and block size; the next run on the same shape and GPU reads
+    them (tune_from_cache) and gives the same distances."""
+    n, src, dst, w, sources = g12
+    path = str(tmp_path / "tune.json")
+    with _ctx(n, src, dst, w) as c:
+        d1, r1 = c.sssp_batch(sources, streamed=True, tune_cache=path)
+        d2, r2 = c.sssp_batch(sources, streamed=True, tune_cache=path)
+    assert r1["tune_from_cache"] == 0 and r2["tune_from_cache"] == 1
+    assert r2["block_edges"] == r1["block_edges"] and r2["k2"] == r1["k2"] and r2["a"] == r1["a"]
+    assert np.array_equal(d1, d2)
+    _check(n, src, dst, w, sources[:3], d2)
+    import json
+    data = json.load(open(path))
+    assert len(data) == 1 and next(iter(data)).startswith(f"sssp_batch V={n} ")

@@ -1,12 +1,15 @@
 """Push-direction and direction-switching supersteps of SSSP and CC against
 the oracle: the same values and the same changed counts after every
-superstep (Jacobi order), whichever direction each superstep takes; frontier
-work items cut at 32 out-edges; values set between supersteps; partitioned
-graphs staying on the pull path."""
+superstep (Jacobi order), whichever direction each superstep takes, on one
+partition and on several (where a push relaxes each partition's in-edges
+from its own changed vertices and from its cached copies of changed remote
+vertices, and the exchange's upload lists stay the oracle's); frontier work
+items cut at 32 out-edges; values set between supersteps."""
 import numpy as np
 import pytest
 
 import oracle
+from oracle import sync as osync
 from paper_2203_13005_gb300 import gxp, synth
 
 pytestmark = pytest.mark.gpu
@@ -20,12 +23,12 @@ def _rmat(scale, ef=16, seed=0x51, w_hi=100):
     return 1 << scale, src, dst, w
 
 
-@pytest.mark.parametrize("keep_ids", [False, True])
+@pytest.mark.parametrize("parts,keep_ids", [(1, False), (1, True), (2, False), (8, False)])
 @pytest.mark.parametrize("direction", ["pull", "push", "auto"])
-def test_sssp_every_superstep_matches_oracle(direction, keep_ids):
+def test_sssp_every_superstep_matches_oracle(direction, parts, keep_ids):
     n, src, dst, w = _rmat(12)
     with gxp.Context(0, direction=DIRS[direction], keep_ids=keep_ids) as c:
-        c.create_graph(n, 1)
+        c.create_graph(n, parts)
         c.load_coo(src, dst, w)
         c.begin(gxp.GXP_ALGO_SSSP, 0)
         d = np.full(n, gxp.INF, np.uint32)
@@ -74,15 +77,18 @@ def test_sssp_run_matches_oracle(direction, push_div):
         assert np.array_equal(c.values(), d2)
 
 
+@pytest.mark.parametrize("parts", [1, 2, 8])
 @pytest.mark.parametrize("direction", ["pull", "push", "auto"])
-def test_cc_every_superstep_matches_oracle(direction):
+def test_cc_every_superstep_matches_oracle(direction, parts):
     rng = np.random.default_rng(9)
     n = 3000
     a = rng.integers(0, n, 2500, dtype=np.uint32)
     b = rng.integers(0, n, 2500, dtype=np.uint32)
     src, dst = np.concatenate([a, b]), np.concatenate([b, a])
+    bounds = [n * p // parts for p in range(parts + 1)]
+    _, _, trace = osync.min_label_sync_trace(n, src, dst, bounds, "cc")
     with gxp.Context(0, direction=DIRS[direction]) as c:
-        c.create_graph(n, 1)
+        c.create_graph(n, parts)
         c.load_coo(src, dst)
         c.begin(gxp.GXP_ALGO_CC)
         lab = np.arange(n, dtype=np.uint32)
@@ -93,9 +99,17 @@ def test_cc_every_superstep_matches_oracle(direction):
             steps += 1
             assert ch == ch_ref, f"superstep {steps}"
             assert np.array_equal(c.values(), l_ref), f"superstep {steps}"
+            if parts > 1:   # the exchange uploads the oracle's pairs whichever direction ran
+                uploads, skipped = trace[steps - 1]
+                for p in range(parts):
+                    ids, vals, sk = c.sync(p)
+                    assert sk == skipped and np.array_equal(ids, uploads[p][0]), (steps, p)
+                    assert np.array_equal(vals, uploads[p][1]), (steps, p)
             lab = l_ref
             if ch_ref == 0:
                 break
+        if direction == "push":
+            assert c.stats()["push_supersteps"] == steps
         labels, steps_ref, _ = oracle.cc(n, src, dst)
         assert steps == steps_ref
         assert c.run(gxp.GXP_ALGO_CC) == steps_ref
@@ -132,11 +146,12 @@ def test_item_boundaries(direction):
         assert c.run(gxp.GXP_ALGO_SSSP, 0) == steps_ref
 
 
+@pytest.mark.parametrize("parts", [1, 3])
 @pytest.mark.parametrize("direction", ["pull", "push", "auto"])
-def test_values_set_between_supersteps(direction):
+def test_values_set_between_supersteps(direction, parts):
     n, src, dst, w = _rmat(11, seed=0x77)
     with gxp.Context(0, direction=DIRS[direction]) as c:
-        c.create_graph(n, 1)
+        c.create_graph(n, parts)
         c.load_coo(src, dst, w)
         c.begin(gxp.GXP_ALGO_SSSP, 5)
         c.superstep()
@@ -172,22 +187,29 @@ def test_degenerate_graphs_push():
             assert np.array_equal(c.values(), np.arange(n, dtype=np.uint32))
 
 
-def test_partitioned_graphs_pull():
+@pytest.mark.parametrize("cache_slots", [0, 16, gxp.GXP_CACHE_NONE])
+@pytest.mark.parametrize("direction", ["push", "auto"])
+def test_partitioned_runs_and_caches(direction, cache_slots):
+    """Whole runs over 4 partitions from two sources, with the LRU cache on or
+    off; PageRank and label propagation on the same context pull as before."""
     n, src, dst, w = _rmat(10, seed=0x33)
     d_ref, steps_ref, _ = oracle.sssp(n, src, dst, w, 0)
-    with gxp.Context(0, direction=gxp.GXP_DIR_PUSH) as c:
-        c.create_graph(n, 2)
-        c.load_coo(src, dst, w)
-        with pytest.raises(gxp.GxpError) as ei:
-            c.run(gxp.GXP_ALGO_SSSP, 0)
-        assert ei.value.code == gxp.GXP_E_UNSUPPORTED
-        c.run(gxp.GXP_ALGO_PAGERANK, max_steps=2)     # other algorithms are unaffected
-    with gxp.Context(0) as c:
-        c.create_graph(n, 2)
+    s2 = int(np.flatnonzero(np.bincount(src, minlength=n))[11])
+    d2, st2, _ = oracle.sssp(n, src, dst, w, s2)
+    with gxp.Context(0, direction=DIRS[direction], cache_slots=cache_slots) as c:
+        c.create_graph(n, 4)
         c.load_coo(src, dst, w)
         assert c.run(gxp.GXP_ALGO_SSSP, 0) == steps_ref
         assert np.array_equal(c.values(), d_ref)
-        assert c.stats()["push_supersteps"] == 0
+        if direction == "push":
+            assert c.stats()["push_supersteps"] == steps_ref
+        else:
+            assert c.stats()["push_supersteps"] > 0
+        assert c.run(gxp.GXP_ALGO_SSSP, s2) == st2
+        assert np.array_equal(c.values(), d2)
+        c.run(gxp.GXP_ALGO_PAGERANK, max_steps=2)     # other algorithms are unaffected
+        r_ref, _, _ = oracle.pagerank(n, src, dst, 0.85, 2)
+        assert np.max(np.abs(c.values() - r_ref) / r_ref) <= 1e-4
 
 
 def test_invalid_direction():

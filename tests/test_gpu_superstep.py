@@ -281,7 +281,8 @@ def test_pagerank_rmat22_full_and_deterministic():
         r2 = c.values()
     _pr_check(r1, r_ref)
     assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))
-    assert abs(float(r1.astype(np.float64).sum()) - 1.0) < 1e-4
+    # the mass stays 1 to within fp32 rounding of the ranks (the global sums are exact)
+    assert abs(float(r1.astype(np.float64).sum()) - 1.0) <= 1e-6
     assert st["last_dangling"] == pytest.approx(
         float(r_ref[np.bincount(src, minlength=n) == 0].sum()), rel=1e-5)
 
