@@ -43,7 +43,13 @@ KERNEL_SRC = os.path.join(REPO, "paper_2203_13005_gb300", "csrc", "sell.cu")
 def algorithmic_bytes(n_vertices: int, n_edges: int) -> int:
     """Bytes one PageRank superstep must move at minimum: per edge the source
     index (4) and the gathered contribution (4); per vertex col_ptr (4),
-    out-degree (4), old rank (4), new rank (4), new contribution (4)."""
+    out-degree (4), new rank (4), new contribution (4): 604.0 MB at R-MAT 22."""
+    return 8 * n_edges + 16 * n_vertices
+
+
+def algorithmic_bytes_with_old_rank(n_vertices: int, n_edges: int) -> int:
+    """The same plus the old rank (4 B per vertex), which the kernel also reads
+    to form the exact sum of |r_new - r_old| (the convergence sum)."""
     return 8 * n_edges + 20 * n_vertices
 
 
@@ -427,7 +433,7 @@ def run_cc(args):
     skipping: per-superstep GTEPS, exchange statistics, roofline of the kernel."""
     import torch
     from paper_2203_13005_gb300 import gxp
-    wl = synth.CC_ER24_P8
+    wl = synth.CC_ER24_P8 if args.cc_scale == 24 else synth.CC_ER24_P8.scaled(args.cc_scale)
     src, dst, _ = wl.edges()
     n, m = wl.n_vertices, wl.n_edges
     cpu, uf = ({}, None) if args.no_cpu_baseline else cpu_cc_baselines(wl, src, dst, n, m)
@@ -757,6 +763,17 @@ def run_serve(args):
 
     main = replay(rate, dur)
     second = replay(args.serve_rate2, dur) if args.serve_rate2 > 0 else None
+    # lower offered rates, shorter windows: the highest rate whose p99 stays under 1 s
+    sweep = []
+    for r in [float(x) for x in args.serve_sweep.split(",") if x.strip()]:
+        res = replay(r, args.serve_sweep_seconds)
+        sweep.append({"offered_qps": r, "achieved_qps": res["achieved_qps"], "completed": res["completed"],
+                      "p50_ms": res["latency"]["p50_ms"], "p99_ms": res["latency"]["p99_ms"],
+                      "backlog_at_end": res["backlog_at_end"]})
+    tried = sweep + [{"offered_qps": rate, **main["latency"]}]
+    if second is not None:
+        tried.append({"offered_qps": args.serve_rate2, **second["latency"]})
+    held = [x["offered_qps"] for x in tried if x.get("p99_ms") is not None and x["p99_ms"] < 1000.0]
 
     # closed loop on the first K queries: one at a time vs all queued at once
     K = min(N, args.serve_closed)
@@ -800,6 +817,8 @@ def run_serve(args):
         "submitted": main["submitted"], "completed": main["completed"], "backlog_at_end": main["backlog_at_end"],
         "lane_supersteps": main["lane_supersteps"],
         "at_lower_rate": second,
+        "rate_sweep": sweep,
+        "highest_rate_with_p99_under_1s": max(held) if held else None,
         "closed_loop": {"queries": int(K), "one_at_a_time_qps": K / single_s, "batched_qps": K / batched_s,
                         "speedup": single_s / batched_s},
         "server_device_bytes": rep["device_bytes"], "graph_load_s": load_s,
@@ -827,6 +846,7 @@ def main():
                     help="extra workloads print their own line; the default is the headline")
     ap.add_argument("--cache-slots", type=int, default=0,
                     help="cc_er24_8parts: cached remote vertices per partition (0 = all, 4294967295 = none)")
+    ap.add_argument("--cc-scale", type=int, default=24, help="cc_er24_8parts: log2 vertices (smaller for profiling)")
     ap.add_argument("--lp-parts", type=int, default=8, help="lp_er24_8parts: partitions (1 = one, renumbered)")
     ap.add_argument("--lp-scale", type=int, default=24, help="lp_er24_8parts: log2 vertices (smaller for profiling)")
     ap.add_argument("--lp-graph", default="er", choices=["er", "rmat"],
@@ -840,6 +860,9 @@ def main():
     ap.add_argument("--serve-closed", type=int, default=1000, help="serve: queries of the closed-loop comparison")
     ap.add_argument("--serve-scales", default="18,20,22,24", help="serve: R-MAT scales of the served graphs")
     ap.add_argument("--serve-priorities", action="store_true", help="serve: smaller graphs' lanes first")
+    ap.add_argument("--serve-sweep", default="", help="serve: further offered rates (comma-separated), "
+                    "each replayed for --serve-sweep-seconds")
+    ap.add_argument("--serve-sweep-seconds", type=float, default=8.0)
     ap.add_argument("--serve-rate2", type=float, default=800.0,
                     help="serve: a second open-loop run at this rate (0: none)")
     args = ap.parse_args()
@@ -962,6 +985,7 @@ def main():
     if rank == 0:
         peaks = measured_peaks()
         bytes_launch = algorithmic_bytes(n, m)
+        bytes_launch_old_rank = algorithmic_bytes_with_old_rank(n, m)
         avg_kernel_s = statistics.mean(kernel_ms) * 1e-3
         achieved = bytes_launch / avg_kernel_s / 1e9
         traffic = profiled_traffic()
@@ -975,11 +999,13 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_launch,
+                         "frac_with_old_rank_read": bytes_launch_old_rank / avg_kernel_s / 1e9 / peaks["hbm_gbs"],
                          "kernel": "k_sell<PR>", "avg_launch_us": avg_kernel_s * 1e6},
             "e2e": {"value": ITERS * m / e2e_s / 1e9, "unit": "GTEPS",
                     "h2d_bytes_per_step": 8 * (n + 1) + 4 * m, "d2h_bytes_per_step": 4 * n,
                     "ms_per_step": e2e_s * 1e3},
-            "gpu_launches": args.steps * (ITERS + 1),
+            # per step: initial values, the identity slots, 20 supersteps
+            "gpu_launches": args.steps * (ITERS + 2),
             "clocks": clk.summary(),
         }
         if base is not None:

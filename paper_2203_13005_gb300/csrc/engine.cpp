@@ -471,7 +471,7 @@ void Engine::build_sell() {
         uint32_t* width = (uint32_t*)talloc(4 * ns + 4);
         uint64_t* off = (uint64_t*)talloc(8 * ns + 8);
         cuda_check(launch_sell_slices(col_ptr, n, rows_out, counts, d_bases, perm, width, off, (uint32_t)ns,
-                                      stream_), "slices");
+                                      n_parts_ == 1, stream_), "slices");
         uint64_t sell_size = 0;
         d2h(&sell_size, off + ns, 8);
         // 4. fill
@@ -479,8 +479,8 @@ void Engine::build_sell() {
         uint32_t* sell_w = weighted ? (uint32_t*)dalloc(4 * pad4(sell_size)) : nullptr;
         part_desc[p] = (SellSlice*)talloc(sizeof(SellSlice) * (ns + 1));
         part_ns[p] = (uint32_t)ns;
-        cuda_check(launch_sell_fill(col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, pd_[p].pad_id, sell_src,
-                                    sell_w, part_desc[p], stream_), "fill slices");
+        cuda_check(launch_sell_fill(col_ptr, ssrc, sw, perm, width, off, (uint32_t)ns, p, pd_[p].pad_id,
+                                    n_parts_ == 1, sell_src, sell_w, part_desc[p], stream_), "fill slices");
         // 5. hub rows -> parts of T edges
         uint32_t* hub_list = (uint32_t*)talloc(4 * nh_rows + 4);
         uint32_t* part_off = (uint32_t*)talloc(4 * nh_rows + 4);
@@ -524,10 +524,17 @@ void Engine::build_sell() {
     d_slices_ = (SellSlice*)dalloc(sizeof(SellSlice) * std::max<size_t>(total_slices, 1));
     uint32_t* order_scratch = (uint32_t*)talloc(order_slices_scratch_bytes(n_slices_));
     at = 0;
+    n_zero_slices_ = 0;
     for (uint32_t p = 0; p < n_parts_; ++p) {
         if (part_ns[p])
             cuda_check(launch_order_slices(all + at, part_ns[p], d_slices_ + at, order_scratch, stream_),
                        "order slices");
+        if (n_parts_ == 1 && part_ns[p]) {
+            // width 0 sorts last: the order's first offset of that bin counts the other slices
+            uint32_t nonzero = 0;
+            d2h(&nonzero, order_scratch, 4);
+            if (nonzero <= part_ns[p]) n_zero_slices_ = part_ns[p] - nonzero;
+        }
         at += part_ns[p];
     }
     const size_t nh1 = std::max<size_t>(total_hubs, 1);
@@ -775,11 +782,10 @@ void Engine::begin(gxp_algo algo, uint32_t source, float damping) {
                                   relabeled_ ? d_new2old_ : nullptr, stream_),
                "init values");
     cuda_check(launch_init_ghosts(a, n_ghost_total_, d_ghost_gid_, d_own_[0], d_ghost_, stream_), "init caches");
-    {   // the identity slots empty SELL slots read: 0 (sums) or INF (minima)
-        const uint32_t id = (a == Algo::PR) ? 0u : kInf;
-        for (int b = 0; b < 2; ++b) cuda_check(launch_fill_u32(d_own_[b] + V, 1, id, stream_), "identity slot");
-        cuda_check(launch_fill_u32(d_ghost_ + n_ghost_total_, 1, id, stream_), "identity slot");
-    }
+    // the identity slots empty SELL slots read: 0 (sums) or INF (minima)
+    cuda_check(launch_identity_slots(d_own_[0] + V, d_own_[1] + V, d_ghost_ + n_ghost_total_,
+                                     a == Algo::PR ? 0u : kInf, stream_),
+               "identity slots");
     if (d_changed_) cuda_check(cudaMemsetAsync(d_changed_, 0, 4 * (((size_t)V + 31) / 32 + 2), stream_), "memset");
     cur_ = 0;
     lru_reset(a == Algo::SSSP || personalized ? src_int : kInf);
@@ -837,9 +843,10 @@ SellArgs Engine::sell_args() const {
     a.err = d_err_;
     a.check_bounds = cfg_.check_bounds;
     a.damping = damping_;
-    a.inv_n = 1.0 / (double)n_vertices_;
+    a.inv_n = (float)(1.0 / (double)n_vertices_);
     a.ppr_source = ppr_source_;
     a.early_exit = (early_exit_ && algo_ != Algo::PR) ? 1u : 0u;
+    a.n_zero = (algo_ == Algo::PR && n_parts_ == 1) ? n_zero_slices_ : 0u;
     if (frontier_) {   // the kernel picks the direction on the device from the frontier's size
         a.fc.list_out = d_list_[1];   // non-null: lists on
         a.fc.direction = cfg_.direction;
@@ -987,6 +994,9 @@ uint64_t Engine::superstep(gxp_algo algo, gxp_msggen g, gxp_merge m, gxp_apply a
             s.fc.list_out = d_list_[(step_ + 1) & 1];
             s.fc.list_cap = list_cap_;
             s.fc.err = d_err_;
+            s.fc.direction = cfg_.direction;
+            s.fc.push_div = cfg_.push_div;
+            s.fc.total_edges = total_edges_;
             s.out_ptr = d_out_ptr_;
             s.n_vertices = (uint32_t)n_vertices_;
         }

@@ -128,6 +128,7 @@ private:
     SellSlice* d_slices_ = nullptr;
     HubPart* d_hubs_ = nullptr;
     uint32_t n_slices_ = 0, n_hubs_ = 0;
+    uint32_t n_zero_slices_ = 0;   // one partition: trailing slices of rows without in-edges
     uint32_t *d_hub_val_ = nullptr, *d_hub_arrive_ = nullptr;
     uint32_t* d_outdeg_ = nullptr;
     uint32_t* d_own_[2] = {nullptr, nullptr};

@@ -181,9 +181,10 @@ __global__ void k_init_values(int algo, uint32_t ppr_source, uint32_t n, uint32_
     }
 }
 
-__global__ void k_fill_u32(uint32_t* p, uint64_t n, uint32_t v) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        p[i] = v;
+__global__ void k_identity_slots(uint32_t* a, uint32_t* b, uint32_t* c, uint32_t v) {
+    *a = v;
+    *b = v;
+    *c = v;
 }
 
 __global__ void k_init_ghosts(uint32_t n_ghost, const uint32_t* __restrict__ gid,
@@ -313,6 +314,13 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
 // holds it relaxes its in-edges from that vertex if the next superstep pushes.
 __global__ void k_sync_pull(const SyncArgs a) {
     if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
+    // the next superstep pulls anyway when its frontier's own vertices alone
+    // are too much work to push: then its cached copies are not listed
+    bool list = a.fc.list_out != nullptr;
+    if (list && a.fc.direction == GXP_DIR_AUTO) {
+        const unsigned long long ne = a.stats_out->list_ne;
+        list = ((ne >> 32) + (ne & 0xFFFFFFFFull)) * (unsigned long long)a.fc.push_div <= a.fc.total_edges;
+    }
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < a.n_pull; b += stride) {
@@ -324,7 +332,7 @@ __global__ void k_sync_pull(const SyncArgs a) {
             // not cached: downloaded when used (lru.cu)
             if (ch && (!a.cached || (a.cached[g] & 1u))) a.ghost[g] = a.own_val[gid];
         }
-        if (a.fc.list_out) {
+        if (list) {
             const uint32_t slot = a.n_vertices + g;
             const uint32_t deg = ch ? __ldg(a.out_ptr + slot + 1) - __ldg(a.out_ptr + slot) : 0u;
             frontier_append(ch, slot, deg, a.fc, a.stats_out, lane);
@@ -382,9 +390,8 @@ cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    k_fill_u32<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 152ull * 8), 256, 0, s>>>(p, n, v);
+cudaError_t launch_identity_slots(uint32_t* a, uint32_t* b, uint32_t* c, uint32_t v, cudaStream_t s) {
+    k_identity_slots<<<1, 1, 0, s>>>(a, b, c, v);
     return cudaGetLastError();
 }
 

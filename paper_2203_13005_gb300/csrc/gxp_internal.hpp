@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -53,8 +54,9 @@ constexpr uint32_t kTailOpen = 2u;
 
 // Sliced-ELL layout of the non-hub rows (SELL-32-sigma): rows are sorted by
 // in-degree inside windows of kSellWindow rows and grouped into slices of 32;
-// a slice stores its rows' in-edges column-major (edge k of all 32 rows, then
-// edge k+1, ...), padded to the slice's largest degree with kSellPad.
+// a slice stores its rows' in-edges column-major, for a single partition in
+// groups of 4 columns (edges 4g..4g+3 of row slot l at off + 128 g + 4 l, see
+// sell_idx), padded with the partition's padding id.
 struct SellSlice {
     uint32_t part;     // partition index
     uint32_t row0;     // first entry of the slice in the partition's perm array
@@ -63,7 +65,17 @@ struct SellSlice {
     uint64_t off;      // first element of the slice in the partition's sell arrays
 };
 constexpr uint32_t kSellPad = 0xFFFFFFFFu;   // empty row slot of a slice (perm)
+// Element of column k, row slot l in a slice's storage. A single partition
+// stores its columns in groups of 4 (g4: a lane reads 4 of its row's sources
+// with one 128-bit load); several partitions column by column (measured
+// faster on their uniform graphs, whose widths the rounding would pad more).
+__host__ __device__ constexpr uint64_t sell_idx(uint32_t k, uint32_t l, bool g4) {
+    return g4 ? 128ull * (k >> 2) + 4ull * l + (k & 3u) : 32ull * k + l;
+}
+// columns a slice stores: its width, rounded up to a whole group with g4
+__host__ __device__ constexpr uint32_t sell_cols(uint32_t width, bool g4) { return g4 ? (width + 3u) & ~3u : width; }
 constexpr uint32_t kSellWindow = 65536;      // rows sorted by degree within windows of this size
+constexpr uint32_t kZeroGroup = 4;           // slices of rows without in-edges per warp (PageRank)
 
 // A slice of the in-edges of one hub row (in-degree above the SELL limit),
 // reduced by one warp; the last part of a row to arrive combines all parts.
@@ -197,9 +209,12 @@ struct SellArgs {
     uint32_t* err;
     uint32_t check_bounds;
     float damping;
-    double inv_n;
+    float inv_n;                 // 1 / N
     uint32_t ppr_source;         // PageRank: kInf; personalized PageRank: the source vertex
     uint32_t early_exit;         // 1: a superstep (t > 0) after a quiet one returns at once
+    // PageRank on one partition: the last n_zero slices (heavy-first order)
+    // hold rows without in-edges; a warp applies kZeroGroup of them at once
+    uint32_t n_zero;
     // SSSP / CC: fc.list_out != nullptr turns the frontier lists on (the
     // kernel points list_in / list_out at lists[]); the out-edge copy is
     // what the push direction reads. Its sources are slots: the V vertices,
@@ -381,7 +396,7 @@ cudaError_t launch_validate_csc(const uint32_t* d_col_ptr, uint32_t n_own, const
 cudaError_t launch_init_values(Algo a, uint32_t ppr_source, uint32_t n_vertices, uint32_t source,
                                uint32_t* own_cur, float* rank_cur, const uint32_t* outdeg,
                                StepStats* stats0, const uint32_t* label_of, cudaStream_t s);
-cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t v, cudaStream_t s);   // p[0 .. n) = v
+cudaError_t launch_identity_slots(uint32_t* a, uint32_t* b, uint32_t* c, uint32_t v, cudaStream_t s);   // *a = *b = *c = v
 cudaError_t launch_init_ghosts(Algo a, uint32_t n_ghost_total, const uint32_t* ghost_gid_all,
                                const uint32_t* own_cur, uint32_t* ghost, cudaStream_t s);
 
@@ -488,16 +503,19 @@ cudaError_t launch_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H,
                                 uint32_t* hub_out, uint32_t* nonhub_cnt, uint32_t* hub_cnt, cudaStream_t s);
 cudaError_t launch_sell_slices(const uint32_t* col_ptr, uint32_t n, const uint32_t* rows_out,
                                const uint32_t* nonhub_cnt, const uint32_t* slice_base, uint32_t* perm,
-                               uint32_t* width, uint64_t* off, uint32_t n_slices, cudaStream_t s);
+                               uint32_t* width, uint64_t* off, uint32_t n_slices, bool g4, cudaStream_t s);
 cudaError_t launch_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
                              const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
-                             uint32_t pad_id, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s);
+                             uint32_t pad_id, bool g4, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc,
+                             cudaStream_t s);
 cudaError_t launch_hub_rows(const uint32_t* col_ptr, uint32_t n, const uint32_t* hub_out, const uint32_t* hub_cnt,
                             const uint32_t* hub_base, uint32_t* hub_list, uint32_t n_hub_rows, uint32_t T,
                             uint32_t* part_off, cudaStream_t s);
 cudaError_t launch_hub_parts(const uint32_t* col_ptr, const uint32_t* hub_list, const uint32_t* part_off,
                              uint32_t n_hub_rows, uint32_t T, uint32_t part, uint32_t part_base, HubPart* hubs,
                              cudaStream_t s);
+// slices by decreasing width (stable); afterwards scratch[0] holds the number
+// of slices wider than 0 (the first offset of the last bin, width 0)
 cudaError_t launch_order_slices(const SellSlice* in, uint32_t n, SellSlice* out, uint32_t* scratch, cudaStream_t s);
 size_t order_slices_scratch_bytes(uint32_t n);
 
@@ -526,6 +544,30 @@ cudaError_t launch_gather_columns(const uint32_t* mat, uint64_t n_vertices, cons
 // Fixed point -> double (exact for sums below 2^53 units, else rounded once).
 __host__ __device__ inline double fx_to_double(unsigned long long v) {
     return (double)v * (1.0 / (double)(1ULL << kFxShift));
+}
+
+// Fixed point (2^-60) -> fp32, from its two 32-bit halves (no FP64).
+__host__ __device__ inline float fx_to_float(unsigned long long v) {
+    const float hi = (float)(uint32_t)(v >> 32), lo = (float)(uint32_t)v;
+    return fmaf(hi, 0x1p-28f, lo * 0x1p-60f);
+}
+
+// The base terms of a PageRank superstep from the exact dangling mass D of
+// its input ranks (fixed point), for damping d and 1 / N: PageRank spreads
+// (1-d) + d*D evenly, (1-d)/N + d*D/N to every vertex; personalized PageRank
+// returns all of it to the source vertex (base_pr = 0 elsewhere).
+// In fp32 only (the FP64 pipe of this GPU is narrow and every warp of the
+// superstep forms these terms).
+__host__ __device__ inline void pagerank_base(unsigned long long dangling_fx, float d, float inv_n, bool personalized,
+                                              float* base_pr, float* base_src) {
+    const float mass = fx_to_float(dangling_fx);   // D
+    const float spread = fmaf(d, mass, 1.0f - d);
+    if (!personalized) {
+        *base_pr = *base_src = spread * inv_n;
+    } else {
+        *base_pr = 0.0f;
+        *base_src = spread;
+    }
 }
 
 #ifdef __CUDACC__

@@ -87,35 +87,10 @@ template <> struct Ops<Algo::PR> {
 };
 
 // Loads of the edge stream (source ids, weights: each read once per
-// superstep) and of the gathered values.
-#ifndef SELL_IDX_LOAD
-#define SELL_IDX_LOAD 0
-#endif
-#ifndef SELL_GATHER_LOAD
-#define SELL_GATHER_LOAD 0
-#endif
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
-#if SELL_IDX_LOAD == 1
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-#elif SELL_IDX_LOAD == 2
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-#else
-    return __ldcs(p);
-#endif
-}
-__device__ __forceinline__ uint32_t ld_value(const uint32_t* p) {
-#if SELL_GATHER_LOAD == 1
-    uint32_t v;
-    asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-#else
-    return __ldg(p);
-#endif
-}
+// superstep, evict-first) and of the gathered values (read-only path).
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ uint4 ld_stream4(const uint4* p) { return __ldcs(p); }
+__device__ __forceinline__ uint32_t ld_value(const uint32_t* p) { return __ldg(p); }
 
 __device__ __forceinline__ uint32_t arrive_acq_rel(uint32_t* ctr) {
     uint32_t old;
@@ -187,7 +162,6 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
         unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats + (t + 2) % kStatRing);
         for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
     }
-    __shared__ float s_base[2];
     __shared__ bool s_quiet;
     if (tid == 0) {
         s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
@@ -199,28 +173,15 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
         const unsigned long long c = warp_sum_u62(stats_in->changed[lane] + stats_in->changed[lane + 32]);
         if (lane == 0 && c == 0ull) s_quiet = true;
     }
+    // PageRank base terms, from the exact dangling mass of the current ranks
+    // (every warp forms them itself: no wait on another warp's loads)
+    float base = 0.0f, base_src = 0.0f;
     if constexpr (A == Algo::PR) {
-        // warp 0, for the CTA: from the exact dangling-mass sum D of the
-        // current ranks, PageRank spreads (1-d) + d*D evenly, (1-d)/N + d*D/N
-        // to every vertex; personalized PageRank returns all of it to the
-        // source vertex
-        if (warp == 0) {
-            const unsigned long long sd =
-                warp_sum_u62(stats_in->dangling_fx[lane] + stats_in->dangling_fx[lane + 32]);
-            const double d = (double)a.damping;
-            if (lane == 0) {
-                if (a.ppr_source == kInf) {
-                    s_base[0] = s_base[1] = (float)((1.0 - d) * a.inv_n + d * fx_to_double(sd) * a.inv_n);
-                } else {
-                    s_base[0] = 0.0f;
-                    s_base[1] = (float)((1.0 - d) + d * fx_to_double(sd));
-                }
-            }
-        }
+        const unsigned long long sd = warp_sum_u62(stats_in->dangling_fx[lane] + stats_in->dangling_fx[lane + 32]);
+        pagerank_base(sd, a.damping, a.inv_n, a.ppr_source != kInf, &base, &base_src);
     }
     __syncthreads();
     if (s_quiet) return;   // same for every thread of the grid
-    const float base = s_base[0], base_src = s_base[1];
     const float damping = a.damping;
 
     uint32_t n_changed = 0;
@@ -293,23 +254,24 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
         const uint32_t* src = P.hsrc + hp.e0;
         const uint32_t* wts = P.hw + hp.e0;
         T acc = Op::ident();
-        for (uint32_t jb = 0; jb < hp.ne; jb += 32u * kU) {
+        auto hbatch = [&](uint32_t j0, auto load) {   // in-edges [j0, j0 + 32 kU) of the part, lane-strided
             uint32_t u[kU], x[kU], wv[kU];
 #pragma unroll
             for (int q = 0; q < kU; ++q) {
-                const uint32_t j = jb + (uint32_t)q * 32u + (uint32_t)lane;
+                const uint32_t j = j0 + (uint32_t)q * 32u + (uint32_t)lane;
                 const bool in = j < hp.ne;
                 u[q] = in ? ld_stream(src + j) : 0u;
                 wv[q] = (Op::kWeighted && in) ? ld_stream(wts + j) : 0u;
             }
 #pragma unroll
             for (int q = 0; q < kU; ++q)
-                x[q] = jb + (uint32_t)q * 32u + (uint32_t)lane < hp.ne ? ld_value(S.at(checked(P, u[q])))
+                x[q] = j0 + (uint32_t)q * 32u + (uint32_t)lane < hp.ne ? load(S.at(checked(P, u[q])))
                                                                         : Op::to_bits(Op::ident());
 #pragma unroll
             for (int q = 0; q < kU; ++q)
-                if (jb + (uint32_t)q * 32u + (uint32_t)lane < hp.ne) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
-        }
+                if (j0 + (uint32_t)q * 32u + (uint32_t)lane < hp.ne) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+        };
+        for (uint32_t jb = 0; jb < hp.ne; jb += 32u * kU) hbatch(jb, [](const uint32_t* p) { return ld_value(p); });
         T total = warp_all<Op>(acc);
         bool do_apply = hp.nparts == 1u;
         if (!do_apply) {
@@ -343,44 +305,61 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
                 f_v = P.v_begin + hp.v;
             }
         }
-    } else if (gw - a.n_hubs < a.n_slices) {
+    } else if (gw - a.n_hubs < a.n_slices - a.n_zero) {
         // =============================================================== slice
         const SellSlice sl = a.slices[gw - a.n_hubs];
         const PartDev P = a.parts[kOne ? 0 : sl.part];
         const Source<kOne> S(own_cur, a.ghost, P);
         const uint32_t row = P.perm[sl.row0 + lane];
-        const uint32_t* col = P.sell_src + sl.off + lane;
-        const uint32_t* wcol = P.sell_w + sl.off + lane;
+        // groups of 4 columns: lane l's 4 sources of group g are one 128-bit
+        // load at group g's 512 bytes (the warp's load is contiguous)
+        const uint4* col4 = reinterpret_cast<const uint4*>(P.sell_src + sl.off) + lane;
+        const uint4* wcol4 = reinterpret_cast<const uint4*>(P.sell_w + sl.off) + lane;
         T acc = Op::ident();
+        static_assert(kU % 4 == 0, "a batch is whole groups of 4 columns");
+        auto batch = [&](uint32_t k0, uint32_t ncols) {   // columns [k0, k0 + ncols), k0 % kU == 0
+            uint32_t u[kU], x[kU], wv[kU];
+            if constexpr (!kOne) {   // several partitions: column by column, 128-byte warp loads
+                const uint32_t* col = P.sell_src + sl.off + lane;
+                const uint32_t* wcol = P.sell_w + sl.off + lane;
+#pragma unroll
+                for (int q = 0; q < kU; ++q) {
+                    const bool in = (uint32_t)q < ncols;
+                    u[q] = in ? ld_stream(col + 32u * (k0 + q)) : 0u;
+                    wv[q] = (Op::kWeighted && in) ? ld_stream(wcol + 32u * (k0 + q)) : 0u;
+                }
+            } else {   // one partition: groups of 4 columns, a 128-bit load per lane and group
+#pragma unroll
+                for (int h = 0; h < kU / 4; ++h) {
+                    const bool in = 4u * h < ncols;   // a group holding at least one column
+                    const uint4 s4 = in ? ld_stream4(col4 + 32u * (k0 / 4u + h)) : make_uint4(0u, 0u, 0u, 0u);
+                    u[4 * h] = s4.x;
+                    u[4 * h + 1] = s4.y;
+                    u[4 * h + 2] = s4.z;
+                    u[4 * h + 3] = s4.w;
+                    if constexpr (Op::kWeighted) {
+                        const uint4 w4 = in ? ld_stream4(wcol4 + 32u * (k0 / 4u + h)) : make_uint4(0u, 0u, 0u, 0u);
+                        wv[4 * h] = w4.x;
+                        wv[4 * h + 1] = w4.y;
+                        wv[4 * h + 2] = w4.z;
+                        wv[4 * h + 3] = w4.w;
+                    } else {
+                        wv[4 * h] = wv[4 * h + 1] = wv[4 * h + 2] = wv[4 * h + 3] = 0u;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+                x[q] = (uint32_t)q < ncols ? ld_value(S.at(checked(P, u[q]))) : Op::to_bits(Op::ident());
+#pragma unroll
+            for (int q = 0; q < kU; ++q)
+                if ((uint32_t)q < ncols) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
+        };
+        // whole batches of kU columns (kU gathers in flight per lane), then the rest
+        const uint32_t full = sl.width - sl.width % kU;
         uint32_t kb = 0;
-        // whole batches of kU columns: no tests, kU gathers in flight per lane
-        for (; kb + kU <= sl.width; kb += kU) {
-            uint32_t u[kU], x[kU], wv[kU];
-#pragma unroll
-            for (int q = 0; q < kU; ++q) {
-                u[q] = ld_stream(col + 32u * (kb + q));
-                wv[q] = Op::kWeighted ? ld_stream(wcol + 32u * (kb + q)) : 0u;
-            }
-#pragma unroll
-            for (int q = 0; q < kU; ++q) x[q] = ld_value(S.at(checked(P, u[q])));
-#pragma unroll
-            for (int q = 0; q < kU; ++q) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
-        }
-        if (kb < sl.width) {   // the last, partial batch: loads past the width are predicated off
-            uint32_t u[kU], x[kU], wv[kU];
-#pragma unroll
-            for (int q = 0; q < kU; ++q) {
-                const bool in = kb + q < sl.width;
-                u[q] = in ? ld_stream(col + 32u * (kb + q)) : 0u;
-                wv[q] = (Op::kWeighted && in) ? ld_stream(wcol + 32u * (kb + q)) : 0u;
-            }
-#pragma unroll
-            for (int q = 0; q < kU; ++q)
-                x[q] = kb + q < sl.width ? ld_value(S.at(checked(P, u[q]))) : Op::to_bits(Op::ident());
-#pragma unroll
-            for (int q = 0; q < kU; ++q)
-                if (kb + q < sl.width) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
-        }
+        for (; kb < full; kb += kU) batch(kb, kU);
+        if (kb < sl.width) batch(kb, sl.width - kb);
         const bool ch = row != kSellPad && apply(P, row, acc);
         const unsigned chm = __ballot_sync(kFull, ch);
         if (lane == 0) n_changed += __popc(chm);
@@ -396,6 +375,40 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
             const unsigned grp = __match_any_sync(chm, g >> 5);
             const unsigned bits = __reduce_or_sync(grp, 1u << (g & 31u));
             if ((uint32_t)lane == (uint32_t)(__ffs(grp) - 1)) atomicOr(&a.changed_bits[g >> 5], bits);
+        }
+    } else {
+        if constexpr (A == Algo::PR && kOne) {
+            // ============================================ rows without in-edges
+            // kZeroGroup slices of rows whose merged message is the identity:
+            // the new rank is the base term (as MSGApply gives for m = 0). All
+            // of the group's loads are issued before any store, so their
+            // latencies overlap instead of forming one chain per slice.
+            const uint32_t zg = gw - a.n_hubs - (a.n_slices - a.n_zero);
+            if (zg < (a.n_zero + kZeroGroup - 1) / kZeroGroup) {
+                const uint32_t* perm = a.parts[0].perm;
+                const uint32_t s0 = a.n_slices - a.n_zero + zg * kZeroGroup;
+                uint32_t v[kZeroGroup], od[kZeroGroup];
+                float ro[kZeroGroup];
+#pragma unroll
+                for (int j = 0; j < (int)kZeroGroup; ++j)
+                    v[j] = s0 + j < a.n_slices ? __ldg(perm + __ldg(&a.slices[s0 + j].row0) + lane) : kSellPad;
+#pragma unroll
+                for (int j = 0; j < (int)kZeroGroup; ++j) {
+                    const bool has = v[j] != kSellPad;
+                    ro[j] = has ? __ldg(rank_cur + v[j]) : 0.0f;
+                    od[j] = has ? __ldg(a.outdeg + v[j]) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < (int)kZeroGroup; ++j) {
+                    if (v[j] == kSellPad) continue;
+                    const float rn = v[j] == a.ppr_source ? base_src : base;
+                    rank_nxt[v[j]] = rn;
+                    own_nxt[v[j]] = __float_as_uint(od[j] ? __fdiv_rn(rn, (float)od[j]) : 0.0f);
+                    const unsigned long long fn = fx_of(rn), fo = fx_of(ro[j]);
+                    l1 += fn > fo ? fn - fo : fo - fn;
+                    if (od[j] == 0u) dang += fn;
+                }
+            }
         }
     }
     }   // work items
@@ -495,7 +508,10 @@ static void launch_sell(const SellArgs& args, bool one, uint32_t grid, cudaStrea
 }
 
 cudaError_t launch_superstep_sell(Algo alg, const SellArgs& args, cudaStream_t s) {
-    const uint64_t work = (uint64_t)args.n_hubs + args.n_slices;
+    if (args.n_zero > args.n_slices || (args.n_zero && (alg != Algo::PR || args.n_parts != 1)))
+        return cudaErrorInvalidValue;
+    const uint64_t work = (uint64_t)args.n_hubs + (args.n_slices - args.n_zero) +
+                          (args.n_zero + kZeroGroup - 1) / kZeroGroup;
     // an empty layout still runs one block: it clears the stat slot two
     // supersteps ahead (and the step may live in device memory)
     const uint64_t per_cta = (uint64_t)kSellWarps * (alg == Algo::PR ? Ops<Algo::PR>::kItems : 1);

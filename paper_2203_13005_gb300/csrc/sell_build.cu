@@ -13,9 +13,11 @@
 //     share power-of-two bins), and the list of hub rows (more than H in-edges).
 //  3. k_sell_slices: slices of 32 consecutive sorted rows, their widths and
 //     row slots; k_scan_widths: element offsets of the slices.
-//  4. k_sell_fill: the column-major slice arrays (one warp per slice); the
-//     empty slots of rows shorter than their slice hold the partition's
-//     padding id, whose value slot always holds the merge's identity.
+//  4. k_sell_fill: the slice arrays (one warp per slice), columns in groups
+//     of 4 so that a lane reads 4 of its row's sources with one 128-bit load;
+//     the empty slots of rows shorter than their slice (and of the columns
+//     rounding the width up to 4) hold the partition's padding id, whose
+//     value slot always holds the merge's identity.
 //  5. k_hub_rows / k_scan_parts / k_hub_parts: hub rows in id order, split
 //     into parts of T edges.
 //  6. k_order_count / k_order_offsets / k_order_scatter: all partitions'
@@ -331,14 +333,16 @@ __global__ void k_sell_slices(const uint32_t* col_ptr, const uint32_t* rows_out,
     }
 }
 
-// single CTA: exclusive prefix of 32 * width (u64) over n slices; out[n] = total
-__global__ void __launch_bounds__(1024) k_scan_widths(const uint32_t* width, uint32_t n, uint64_t* out) {
+// single CTA: exclusive prefix of a slice's storage, 32 * round_up(width, 4)
+// words (u64), over n slices; out[n] = total
+__global__ void __launch_bounds__(1024) k_scan_widths(const uint32_t* width, uint32_t n, bool g4, uint64_t* out) {
+    auto slice_words = [g4](uint32_t w) { return 32ull * sell_cols(w, g4); };
     __shared__ unsigned long long part[1024];
     const uint32_t t = threadIdx.x;
     const uint32_t per = (n + 1023) / 1024;
     const uint32_t a = min(n, t * per), b = min(n, a + per);
     unsigned long long s = 0;
-    for (uint32_t i = a; i < b; ++i) s += 32ull * width[i];
+    for (uint32_t i = a; i < b; ++i) s += slice_words(width[i]);
     part[t] = s;
     __syncthreads();
     for (uint32_t o = 1; o < 1024; o <<= 1) {
@@ -350,28 +354,30 @@ __global__ void __launch_bounds__(1024) k_scan_widths(const uint32_t* width, uin
     unsigned long long run = part[t] - s;
     for (uint32_t i = a; i < b; ++i) {
         out[i] = run;
-        run += 32ull * width[i];
+        run += slice_words(width[i]);
     }
     if (t == 1023) out[n] = part[1023];
 }
 
-// one warp per slice: column-major fill of sources (and weights), descriptors
+// one warp per slice: the sources (and weights) in groups of 4 columns, lane
+// l's 4 entries of group g at off + 128 g + 4 l (sell_idx), descriptors
 __global__ void k_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
                             const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
-                            uint32_t pad_id, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc) {
+                            uint32_t pad_id, bool g4, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t s = warp0; s < n_slices; s += n_warps) {
         const uint32_t r = perm[s * 32 + lane];
-        const uint32_t wd = width[s];
+        const uint32_t wd = width[s], w4 = sell_cols(wd, g4);
         const uint64_t o = off[s];
         const uint32_t b = r != kSellPad ? col_ptr[r] : 0u;
         const uint32_t d = r != kSellPad ? col_ptr[r + 1] - b : 0u;
-        for (uint32_t k = 0; k < wd; ++k) {
+        for (uint32_t k = 0; k < w4; ++k) {
             const bool has = k < d;
-            sell_src[o + 32ull * k + lane] = has ? ssrc[b + k] : pad_id;
-            if (sell_w) sell_w[o + 32ull * k + lane] = has ? sw[b + k] : 0u;
+            const uint64_t at = o + sell_idx(k, (uint32_t)lane, g4);
+            sell_src[at] = has ? ssrc[b + k] : pad_id;
+            if (sell_w) sell_w[at] = has ? sw[b + k] : 0u;
         }
         if (lane == 0) desc[s] = SellSlice{part, (uint32_t)(s * 32), wd, 0u, o};
     }
@@ -630,19 +636,20 @@ cudaError_t launch_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H,
 
 cudaError_t launch_sell_slices(const uint32_t* col_ptr, uint32_t n, const uint32_t* rows_out,
                                const uint32_t* nonhub_cnt, const uint32_t* slice_base, uint32_t* perm,
-                               uint32_t* width, uint64_t* off, uint32_t n_slices, cudaStream_t s) {
+                               uint32_t* width, uint64_t* off, uint32_t n_slices, bool g4, cudaStream_t s) {
     const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
     if (nw) k_sell_slices<<<nw, 256, 0, s>>>(col_ptr, rows_out, nonhub_cnt, slice_base, perm, width);
-    k_scan_widths<<<1, 1024, 0, s>>>(width, n_slices, off);
+    k_scan_widths<<<1, 1024, 0, s>>>(width, n_slices, g4, off);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sell_fill(const uint32_t* col_ptr, const uint32_t* ssrc, const uint32_t* sw, const uint32_t* perm,
                              const uint32_t* width, const uint64_t* off, uint32_t n_slices, uint32_t part,
-                             uint32_t pad_id, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc, cudaStream_t s) {
+                             uint32_t pad_id, bool g4, uint32_t* sell_src, uint32_t* sell_w, SellSlice* desc,
+                             cudaStream_t s) {
     if (n_slices == 0) return cudaSuccess;
     k_sell_fill<<<grid_warps(n_slices, 256), 256, 0, s>>>(col_ptr, ssrc, sw, perm, width, off, n_slices, part,
-                                                          pad_id, sell_src, sell_w, desc);
+                                                          pad_id, g4, sell_src, sell_w, desc);
     return cudaGetLastError();
 }
 

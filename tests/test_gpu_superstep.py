@@ -267,6 +267,31 @@ def test_pagerank_degenerate():
         assert c.values()[0] == pytest.approx(1.0, rel=1e-6)
 
 
+@pytest.mark.parametrize("n_zero", [1, 32, 32 * 5 + 7, 32 * 9 + 31])
+@pytest.mark.parametrize("keep", [False, True])
+def test_pagerank_rows_without_in_edges(n_zero, keep):
+    # the slices of rows without in-edges are applied several per warp: ragged
+    # group counts, pad rows in the last slice, and personalized PageRank from
+    # a source that has no in-edges
+    rng = np.random.default_rng(n_zero + 17 * keep)
+    k = 300                                        # vertices with in-edges
+    n = k + n_zero
+    m = 4000
+    src = rng.integers(0, n, m, dtype=np.uint32)
+    dst = rng.integers(0, k, m, dtype=np.uint32)
+    r_ref, _, _ = oracle.pagerank(n, src, dst, 0.85, 20)
+    s = n - 1                                      # no in-edges
+    p_ref = oracle.ppr(n, src, dst, s, 0.85, 20)
+    with gxp.Context(0, keep_ids=keep, check_bounds=True) as c:
+        c.create_graph(n, 1)
+        c.load_coo(src, dst)
+        c.run(gxp.GXP_ALGO_PAGERANK, damping=0.85, max_steps=20)
+        _pr_check(c.values(), r_ref)
+        c.run(gxp.GXP_ALGO_PPR, s, 0.85, 20)
+        p = c.values().astype(np.float64)
+        assert np.all(np.abs(p - p_ref) <= 1e-4 * p_ref + 1e-9)
+
+
 def test_pagerank_rmat22_full_and_deterministic():
     wl = synth.PAGERANK_RMAT22
     src, dst, _ = wl.edges()
