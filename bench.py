@@ -233,6 +233,16 @@ def run_msssp(args):
     _, runs["resident"] = ctx.sssp_batch(sources, out=dist)
     best = runs["streamed_autotuned"]
     sec = best["ms_total"] * 1e-3
+    # roofline of k_msssp on the resident run (SURVEY 8(d)'s bytes: 8 B per
+    # scanned edge, 256 B per active edge's row gather, 524 B per vertex per
+    # superstep), and the host link of the streamed run against a pinned copy
+    peaks = measured_peaks()
+    res = runs["resident"]
+    res_bytes = 8 * m * res["supersteps"] + 256 * res["active_edges"] + 524 * n * res["supersteps"]
+    res_gbs = res_bytes / (res["ms_total"] * 1e-3) / 1e9
+    esize = 4 if wl.w_hi < 256 and n <= (1 << 24) else 8   # packed (weight << 24 | source) edges
+    h2d = esize * m * best["supersteps"]
+    line_gbs = pinned_h2d_gbs(torch)
     line = {
         "metric": METRIC, "value": best["supersteps"] * m / sec / 1e9, "unit": "GTEPS",
         "source_gteps": 64 * best["supersteps"] * m / sec / 1e9, "n_gpus": 1, "steps": args.steps,
@@ -242,9 +252,32 @@ def run_msssp(args):
                    "step": "one batched run to convergence, edges streamed from pinned host memory"},
         "runs": {k: {kk: (round(vv, 9) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                  for k, v in runs.items()},
+        "roofline": {"bound": "hbm", "achieved": res_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": res_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                     "kernel": "k_msssp (resident run)", "algorithmic_bytes_per_run": res_bytes,
+                     "active_edges": res["active_edges"], "supersteps": res["supersteps"]},
+        "link": {"h2d_bytes_per_superstep": esize * m, "achieved_gbs": h2d / sec / 1e9,
+                 "pinned_copy_gbs": line_gbs, "frac": h2d / sec / 1e9 / line_gbs if line_gbs else None},
     }
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def pinned_h2d_gbs(torch) -> float:
+    """Host-to-device bandwidth of one 1 GiB copy from pinned memory (best of 3)."""
+    h = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    d = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    best = None
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        d.copy_(h, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) * 1e-3
+        best = t if best is None else min(best, t)
+    del h, d
+    return (1 << 30) / best / 1e9
 
 
 def run_sssp(args):

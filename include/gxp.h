@@ -355,7 +355,9 @@ typedef struct gxp_batch_report {
     double   sweep_best_ms;  /* measured superstep time at the chosen block size (autotuner) */
     uint64_t edges_per_superstep;
     uint64_t tune_from_cache;   /* 1: the coefficients and block size came from the tune cache */
-    uint64_t reserved[5];
+    uint64_t active_edges;      /* in-edges whose source was in the frontier, summed over the
+                                   supersteps (each gathered a 256-byte distance row) */
+    uint64_t reserved[4];
 } gxp_batch_report;
 
 /* One autotuner record (Section III-A): the per-edge download, compute and

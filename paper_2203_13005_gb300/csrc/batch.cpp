@@ -155,6 +155,7 @@ void Engine::superstep_batch(const std::vector<uint64_t>& cuts, bool streamed, b
     a.dist = b.d_dist;
     a.frontier_cur = fr_cur;
     a.frontier_next = fr_next;
+    a.active = dry ? nullptr : b.d_active;
     if (!streamed) {
         a.u_begin = 0;
         a.u_end = b.units.size();
@@ -390,6 +391,7 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
             b.ring_edges = mx;
         }
     }
+    if (!b.d_active) b.d_active = (unsigned long long*)dalloc(8);
     if (cuts.size() - 1 > b.max_blocks || !b.d_changed) {
         const size_t nb = std::max<size_t>(cuts.size() - 1, 1);
         b.d_changed = (unsigned long long*)dalloc(8 * nb);
@@ -427,6 +429,7 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
         b.graph_pipelined = pipelined;
     }
 
+    cuda_check(cudaMemsetAsync(b.d_active, 0, 8, stream_), "memset");
     cuda_check(cudaEventRecord(b.ev_t0, stream_), "event");
     int parity = 0;
     uint32_t steps = 0;
@@ -447,10 +450,13 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
     cuda_check(cudaEventElapsedTime(&ms, b.ev_t0, b.ev_t1), "elapsed");
     r.ms_total = ms;
     r.supersteps = steps;
+    unsigned long long active = 0;
+    cuda_check(cudaMemcpyAsync(&active, b.d_active, 8, cudaMemcpyDeviceToHost, stream_), "read counts");
     if (dist_out)
         cuda_check(cudaMemcpy2DAsync(dist_out, 4ull * n_src, b.d_dist, 256, 4ull * n_src, V, cudaMemcpyDefault, stream_),
                    "copy distances");
     cuda_check(cudaStreamSynchronize(stream_), "copy distances");
+    r.active_edges = active;
     if (rep) *rep = r;
 }
 

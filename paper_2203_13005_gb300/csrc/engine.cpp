@@ -62,6 +62,13 @@ Engine::Engine(int device, const gxp_config* cfg) : device_(device) {
     cuda_check(cudaSetDevice(device), "cudaSetDevice");
     cuda_check(cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking), "cudaStreamCreate");
     stream_ = own_stream_;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cuda_check(cudaMemPoolCreate(&pool_, &props), "cudaMemPoolCreate");
+    uint64_t keep = ~0ull;
+    cuda_check(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep), "memory pool");
     cuda_check(cudaEventCreate(&ev_a_), "cudaEventCreate");
     cuda_check(cudaEventCreate(&ev_b_), "cudaEventCreate");
     cuda_check(cudaEventCreate(&ev_k_), "cudaEventCreate");
@@ -77,13 +84,35 @@ Engine::~Engine() {
     if (ev_k_) cudaEventDestroy(ev_k_);
     if (h_ctl_) cudaFreeHost(h_ctl_);
     if (h_ring_) cudaFreeHost(h_ring_);
+    if (stream_) cudaStreamSynchronize(stream_);   // the frees above
+    if (pool_) cudaMemPoolDestroy(pool_);
     if (own_stream_) cudaStreamDestroy(own_stream_);
 }
 
+// Device memory comes from the context's own memory pool, which keeps what
+// is freed for reuse (release threshold: never), so reloading a graph of the
+// same size maps no new pages: a first load pays cudaMalloc's page mapping,
+// later ones take the pool's blocks at once. The allocation is made complete
+// (the stream synchronized) before it returns, so any stream may use it, and
+// frees are ordered after the context stream's work; every free happens once
+// the buffer's users are done, as it did with cudaFree. When the pool cannot
+// grow, it is trimmed and the allocation tried once more.
 cudaError_t Engine::device_malloc(void** p, size_t bytes) {
     ++n_allocs_;
     if (faults_.alloc_at == n_allocs_) return cudaErrorMemoryAllocation;   // injected fault
-    return cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool_, stream_);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        cudaStreamSynchronize(stream_);
+        cudaMemPoolTrimTo(pool_, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, pool_, stream_);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    return e;
+}
+
+void Engine::device_free(void* p) {
+    if (p) cudaFreeAsync(p, stream_);
 }
 
 void Engine::before_h2d(const char* what) {
@@ -104,6 +133,7 @@ void* Engine::dalloc(size_t bytes) {
 }
 
 void Engine::free_graph_device() {
+    if (stream_) cudaStreamSynchronize(stream_);
     free_batch();   // graphs and pinned buffers that refer to the device buffers below
     for (auto& g : run_graph_) {
         if (g) cudaGraphExecDestroy(g);
@@ -113,7 +143,7 @@ void Engine::free_graph_device() {
     h_old2new_.clear();
     lp_ = LpLists{};
     lru_ = Lru{};
-    for (void* p : graph_allocs_) cudaFree(p);
+    for (void* p : graph_allocs_) device_free(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
     for (auto& hp : parts_)
@@ -328,15 +358,15 @@ void Engine::load_csc_device(HostPart& hp, uint64_t E, const void* cp_in, const 
         uint32_t bad = 0;
         cuda_check(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, stream_), "read check");
         cuda_check(cudaStreamSynchronize(stream_), "check CSC");
-        cudaFree(cp64);
-        cudaFree(flag);
+        device_free(cp64);
+        device_free(flag);
         cp64 = nullptr;
         flag = nullptr;
         if (bad & 1u) fail(GXP_E_INVAL, "CSC col_ptr must run from 0 to n_edges, non-decreasing");
         if (bad & 2u) fail(GXP_E_INVAL, "source id out of range");
     } catch (...) {
-        if (cp64) cudaFree(cp64);
-        if (flag) cudaFree(flag);
+        if (cp64) device_free(cp64);
+        if (flag) device_free(flag);
         release_part(hp);
         throw;
     }
@@ -348,9 +378,9 @@ void Engine::load_csc_device(HostPart& hp, uint64_t E, const void* cp_in, const 
 void Engine::release_part(HostPart& hp) {
     if (hp.on_device) {
         if (stream_) cudaStreamSynchronize(stream_);
-        cudaFree(hp.d_col_ptr);
-        cudaFree(hp.d_src);
-        if (hp.d_w) cudaFree(hp.d_w);
+        device_free(hp.d_col_ptr);
+        device_free(hp.d_src);
+        if (hp.d_w) device_free(hp.d_w);
         hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
         hp.on_device = false;
         hp.dev_edges = 0;
@@ -417,7 +447,7 @@ void Engine::build_sell() {
         cudaStream_t s;
         ~FreeTmp() {
             cudaStreamSynchronize(s);
-            for (void* q : v) cudaFree(q);
+            for (void* q : v) cudaFreeAsync(q, s);   // pool blocks (device_malloc)
         }
     } free_tmp{tmp, stream_};
     auto d2h = [&](void* h, const void* d, size_t bytes) {
@@ -612,7 +642,7 @@ void Engine::finalize() {
         cudaError_t e = device_malloc(&scratch, relabel_scratch_bytes(V));
         if (e == cudaSuccess) e = launch_relabel(hp.d_col_ptr, V, d_new2old_, d_old2new_, rcol, (uint32_t*)scratch, stream_);
         cudaError_t e2 = cudaStreamSynchronize(stream_);
-        if (scratch) cudaFree(scratch);
+        if (scratch) device_free(scratch);
         cuda_check(e, "relabel");
         cuda_check(e2, "relabel");
         work_[0].col = rcol;
@@ -1123,7 +1153,7 @@ void Engine::build_out_edges() {
         cudaStream_t s;
         ~FreeTmp() {
             cudaStreamSynchronize(s);
-            for (void* q : v) cudaFree(q);
+            for (void* q : v) cudaFreeAsync(q, s);   // pool blocks (device_malloc)
         }
     } free_tmp{tmp, stream_};
     RowSource in = work_[0].in;

@@ -77,6 +77,8 @@ private:
     // every device allocation and host-to-device copy of the context goes
     // through these, so that an injected fault can fail the n-th one
     cudaError_t device_malloc(void** p, size_t bytes);
+    void device_free(void* p);
+    cudaMemPool_t pool_ = nullptr;   // the context's device memory (device_malloc)
     void before_h2d(const char* what);
     FaultPlan faults_;
     uint64_t n_allocs_ = 0, n_h2d_ = 0, n_exchanges_ = 0;
@@ -172,6 +174,7 @@ private:
         uint32_t* d_dist = nullptr;        // [V][64]
         uint32_t* d_frontier[2] = {nullptr, nullptr};
         unsigned long long* d_changed = nullptr;   // per-block counters
+        unsigned long long* d_active = nullptr;    // active in-edges over a run (the roofline's row gathers)
         unsigned long long* h_changed = nullptr;   // pinned mirror (upload stage)
         uint32_t* d_sources = nullptr;
         size_t max_blocks = 0;

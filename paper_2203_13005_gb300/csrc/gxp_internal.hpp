@@ -243,6 +243,7 @@ struct MsArgs {
     const uint32_t* frontier_cur;
     uint32_t* frontier_next;
     unsigned long long* changed; // units that improved a slot (this block's counter)
+    unsigned long long* active;  // nullable: running count of in-edges whose source was in the frontier
     uint32_t* slot_improved;     // nullable: [2] bit s of word 0 / s - 32 of word 1 = slot s improved
     uint64_t idle_mask;          // slots to skip (no query in them); 0 = compute all 64
 };

@@ -52,11 +52,12 @@ __device__ __forceinline__ uint2 load_edge(const void* base, uint64_t i) {
 template <bool kDry, bool kPacked>
 __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
     __shared__ uint32_t s_imp[2], s_done;
-    __shared__ unsigned long long s_changed;
+    __shared__ unsigned long long s_changed, s_active;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 2) s_imp[threadIdx.x] = 0u;
     if (threadIdx.x == 0) {
         s_changed = 0ull;
+        s_active = 0ull;
         s_done = 0u;
     }
     __syncthreads();
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
     const uint32_t warp0 = (blockIdx.x * kMsBlock + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * kMsBlock) >> 5;
     uint32_t changed_units = 0;
+    unsigned long long n_active = 0;   // active in-edges this warp walked (the same in every lane)
     for (uint64_t k = a.u_begin + warp0; k < a.u_end; k += n_warps) {
         const uint4 un = a.units[k];   // v, first edge (global), edges, split flag
         const uint32_t v = un.x, len = un.z;
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
             }
             uint32_t mask = __ballot_sync(kFull, act);
             any |= mask != 0u;
+            n_active += (unsigned)__popc(mask);
             while (mask) {
                 // the active edges, kRowsInFlight source rows loaded at a time
                 int idx[kRowsInFlight];
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
     // one global atomic per word (no barrier: early warps leave at once)
     if (lane == 0) {
         if (changed_units) atomicAdd(&s_changed, (unsigned long long)changed_units);
+        if (n_active && a.active) atomicAdd(&s_active, n_active);
         if (imp_lo) atomicOr(&s_imp[0], imp_lo);
         if (imp_hi) atomicOr(&s_imp[1], imp_hi);
         __threadfence_block();
@@ -145,6 +149,10 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
             __threadfence_block();
             const unsigned long long c = atomicAdd(&s_changed, 0ull);
             if (c) atomicAdd(a.changed, c);
+            if (a.active) {
+                const unsigned long long na = atomicAdd(&s_active, 0ull);
+                if (na) atomicAdd(a.active, na);
+            }
             const uint32_t i0 = atomicOr(&s_imp[0], 0u), i1 = atomicOr(&s_imp[1], 0u);
             if (!kDry && a.slot_improved != nullptr) {
                 if (i0) atomicOr(&a.slot_improved[0], i0);

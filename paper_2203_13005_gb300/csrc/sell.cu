@@ -69,14 +69,18 @@ template <> struct Ops<Algo::CC> {
     __device__ static T gen(uint32_t lu, uint32_t) { return lu; }
 };
 
+// PageRank: 12 gathers in flight per lane at 5 CTAs per SM (48 registers)
+// measured 181 us per R-MAT 22 superstep against 197 us for 8 at 6 CTAs
+// (same box); 16 at 5 or 4 CTAs, 20 at 4, 8 at 7, and a separate unroll of
+// 16 for the hub parts were all slower.
 #ifndef PR_UNROLL
-#define PR_UNROLL 8
+#define PR_UNROLL 12
 #endif
 template <> struct Ops<Algo::PR> {
     using T = float;
     static constexpr bool kWeighted = false;
     static constexpr int kUnroll = PR_UNROLL;
-    static constexpr int kMinBlocks = 6;
+    static constexpr int kMinBlocks = 5;
     static constexpr int kItems = PR_ITEMS;   // work items per warp
     __device__ static T ident() { return 0.0f; }
     __device__ static T combine(T a, T b) { return a + b; }

@@ -45,6 +45,22 @@ def test_batch_resident_64_sources(g12):
     _check(n, src, dst, w, sources, dist)
 
 
+@pytest.mark.parametrize("streamed", [False, True])
+def test_batch_counts_active_edges(g12, streamed):
+    # the report's active in-edges (those whose source is in the frontier):
+    # the first superstep's frontier is the sources, so one superstep walks
+    # exactly their out-edges; a whole run walks at least that and at most
+    # every edge per superstep
+    n, src, dst, w, sources = g12
+    outdeg = np.bincount(src, minlength=n)
+    first = int(outdeg[np.unique(sources)].sum())
+    with _ctx(n, src, dst, w) as c:
+        _, rep1 = c.sssp_batch(sources, streamed=streamed, block_edges=3000 if streamed else 0, max_steps=1)
+        _, rep = c.sssp_batch(sources, streamed=streamed, block_edges=3000 if streamed else 0)
+    assert rep1["supersteps"] == 1 and rep1["active_edges"] == first
+    assert first <= rep["active_edges"] <= rep["supersteps"] * len(src)
+
+
 @pytest.mark.parametrize("pipelined,use_graph", [(True, False), (False, False), (True, True)])
 def test_batch_streamed_small_blocks(g12, pipelined, use_graph):
     n, src, dst, w, sources = g12

@@ -292,6 +292,27 @@ def test_pagerank_rows_without_in_edges(n_zero, keep):
         assert np.all(np.abs(p - p_ref) <= 1e-4 * p_ref + 1e-9)
 
 
+def test_reloads_reuse_device_memory():
+    # the context keeps freed device memory in its pool: graphs of different
+    # sizes loaded one after another into one context, each run checked
+    # against the oracle, and the same graph twice holds the same bytes
+    held = {}
+    with gxp.Context(0) as c:
+        for scale, seed in [(12, 1), (10, 2), (13, 3), (12, 1)]:
+            src, dst = synth.rmat(scale, 16 << scale, seed)
+            n = 1 << scale
+            r_ref, _, _ = oracle.pagerank(n, src, dst, 0.85, 20)
+            lab_ref, steps_ref, _ = oracle.cc(n, src, dst)
+            c.create_graph(n, 1)
+            c.load_coo(src, dst)
+            c.run(gxp.GXP_ALGO_PAGERANK, damping=0.85, max_steps=20)
+            _pr_check(c.values(), r_ref)
+            assert c.run(gxp.GXP_ALGO_CC) == steps_ref
+            assert np.array_equal(c.values(), lab_ref)
+            b = c.stats()["device_bytes"]
+            assert held.setdefault((scale, seed), b) == b
+
+
 def test_pagerank_rmat22_full_and_deterministic():
     wl = synth.PAGERANK_RMAT22
     src, dst, _ = wl.edges()
