@@ -367,7 +367,10 @@ def run_sssp(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl.name, "vertices": n, "edges": m, "source": 0, "supersteps": steps,
-                   "step": "one gxp_run to convergence (supersteps enqueued in chunks of 4, 8, 16)",
+                   "step": ("one gxp_run to convergence: " + (
+                       f"{st['persistent_launches']} persistent cooperative launch(es), grid barrier between "
+                       "supersteps" if st["persistent_launches"] else
+                       "a CUDA graph whose WHILE node repeats superstep + control")),
                    "value": "supersteps x edges / run time (the Jacobi sweeps the run stands for)",
                    "l2": (f"{bytes_sweep / 1e6:.0f} MB working set: "
                           + ("L2-resident" if bytes_sweep < 129e6 else "larger than L2")),
@@ -382,7 +385,9 @@ def run_sssp(args):
                      "algorithmic_bytes_per_launch": bytes_sweep},
         "e2e": {"value": steps * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 8 * (n + 1) + 8 * m,
                 "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": reps * steps,
+        # per run: initial values, identity slot and frontier seed, then the
+        # persistent loop's launches or the graph's superstep + control kernels
+        "gpu_launches": reps * (3 + (st["persistent_launches"] or 2 * steps)),
         "clocks": clk.summary(),
     }
     line.update(cpu)

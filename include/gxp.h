@@ -203,7 +203,10 @@ typedef struct gxp_stats {
     double   last_kernel_ms;        /* device time of the last superstep's compute kernel alone
                                        (MSGGen + MSGMerge + MSGApply, without its sync); gxp_run's
                                        device-driven loop: the average superstep */
-    uint64_t reserved[3];
+    uint64_t persistent_launches;   /* gxp_run launches of the persistent superstep loop since
+                                       gxp_begin (small single-partition SSSP / CC graphs: one
+                                       cooperative kernel runs up to 32 supersteps) */
+    uint64_t reserved[2];
 } gxp_stats;
 
 /* ------------------------------------------------------------ lifecycle -- */

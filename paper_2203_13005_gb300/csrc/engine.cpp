@@ -140,12 +140,31 @@ void Engine::free_graph_device() {
         g = nullptr;
     }
     d_ctl_ = nullptr;
+    d_bar_ = nullptr;
     h_old2new_.clear();
     lp_ = LpLists{};
     lru_ = Lru{};
     for (void* p : graph_allocs_) device_free(p);
     graph_allocs_.clear();
     graph_bytes_ = 0;
+    // every pointer into the buffers just freed (a later graph may not
+    // allocate all of them again: one partition has no exchange buffers)
+    d_parts_ = nullptr;
+    d_slices_ = nullptr;
+    d_hubs_ = nullptr;
+    n_slices_ = n_hubs_ = n_zero_slices_ = 0;
+    d_hub_val_ = d_hub_arrive_ = nullptr;
+    d_outdeg_ = nullptr;
+    d_own_[0] = d_own_[1] = nullptr;
+    d_rank_[0] = d_rank_[1] = nullptr;
+    d_ghost_ = d_ghost_gid_ = nullptr;
+    d_changed_ = d_boundary_ = nullptr;
+    d_gdq_ids_ = d_gdq_vals_ = nullptr;
+    d_gdq_base_ = nullptr;
+    d_block_counts_ = d_block_offsets_ = d_part_counts_ = nullptr;
+    d_done_ctr_ = nullptr;
+    d_stats_ = nullptr;
+    d_err_ = nullptr;
     for (auto& hp : parts_)
         if (!hp.on_device) hp.d_col_ptr = hp.d_src = hp.d_w = nullptr;
     work_.clear();
@@ -1378,24 +1397,48 @@ uint32_t Engine::run(gxp_algo algo, uint32_t source, float damping, uint32_t max
         account(false);
         return steps;
     }
-    // SSSP / CC on one partition: the loop runs on the device (a graph whose
-    // WHILE node repeats superstep + control until the first superstep that
-    // changes nothing, at most kRunChunk per launch); one host read per launch
-    if (n_parts_ == 1 && algo_ != Algo::LP && run_graph_ready()) {
-        const cudaGraphExec_t ge = run_graph_[algo_ == Algo::SSSP ? 0 : 1];
+    // SSSP / CC on one partition: the loop runs on the device until the first
+    // superstep that changes nothing, at most kRunChunk supersteps per launch
+    // and one host read per launch. A graph whose superstep is a few waves of
+    // CTAs runs all of them in one persistent cooperative kernel (grid
+    // barrier between supersteps); larger ones through a CUDA graph whose
+    // WHILE node repeats superstep + control.
+    const bool one = n_parts_ == 1 && algo_ != Algo::LP;
+    SellArgs la{};
+    if (one) {
+        la = sell_args();
+        la.early_exit = 0u;   // the loop stops at the first quiet superstep
+    }
+    const bool loop = one && sell_loop_fits(algo_, la);
+    if (loop) {
+        if (!h_ctl_) cuda_check(cudaMallocHost(&h_ctl_, 2 * sizeof(RunCtl)), "pinned run control");
+        if (!h_ring_) cuda_check(cudaMallocHost(&h_ring_, sizeof(StepStats) * kStatRing), "pinned stats");
+        if (!d_ctl_) d_ctl_ = (RunCtl*)dalloc(sizeof(RunCtl));
+        if (!d_bar_) d_bar_ = (GridBar*)dalloc(sizeof(GridBar));
+    }
+    if (loop || (one && run_graph_ready())) {
+        const cudaGraphExec_t ge = loop ? nullptr : run_graph_[algo_ == Algo::SSSP ? 0 : 1];
         while (steps < max_steps) {
             const uint32_t k = std::min<uint32_t>(kRunChunk, max_steps - steps);
             h_ctl_[0] = RunCtl{step_, step_ + k, 1u, 0u};
             before_h2d("run control");
             cuda_check(cudaMemcpyAsync(d_ctl_, h_ctl_, sizeof(RunCtl), cudaMemcpyHostToDevice, stream_), "run control");
+            if (loop) cuda_check(cudaMemsetAsync(d_bar_, 0, sizeof(GridBar), stream_), "memset");
             cuda_check(cudaEventRecord(ev_a_, stream_), "event");
-            cuda_check(cudaGraphLaunch(ge, stream_), "run graph");
+            if (loop) {
+                cuda_check(launch_sell_loop(algo_, la, d_ctl_, d_bar_, cfg_.timeout_ns, faults_.timeout, stream_),
+                           "run loop");
+                ++st_.persistent_launches;
+            } else {
+                cuda_check(cudaGraphLaunch(ge, stream_), "run graph");
+            }
             cuda_check(cudaEventRecord(ev_b_, stream_), "event");
             cuda_check(cudaMemcpyAsync(h_ctl_ + 1, d_ctl_, sizeof(RunCtl), cudaMemcpyDeviceToHost, stream_),
                        "run control");
             cuda_check(cudaMemcpyAsync(h_ring_, d_stats_, sizeof(StepStats) * kStatRing, cudaMemcpyDeviceToHost,
                                        stream_), "read stats");
             cuda_check(cudaStreamSynchronize(stream_), "run");
+            if (loop) check_device_error();   // a grid barrier that ran out of time
             ring_host_.assign(h_ring_, h_ring_ + kStatRing);
             const uint64_t done = h_ctl_[1].step;
             if (done <= step_ || done > step_ + k) fail(GXP_E_CUDA, "device-driven run lost its step counter");

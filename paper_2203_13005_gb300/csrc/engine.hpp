@@ -224,6 +224,7 @@ private:
     cudaGraphExec_t run_graph_[2] = {nullptr, nullptr};   // SSSP, CC
     bool run_graph_failed_ = false;
     RunCtl* d_ctl_ = nullptr;
+    GridBar* d_bar_ = nullptr;     // the persistent run's grid barrier
     RunCtl* h_ctl_ = nullptr;      // pinned: [0] to the device, [1] back
     StepStats* h_ring_ = nullptr;  // pinned copy of the stat ring
     std::vector<uint32_t> h_old2new_;   // host copy of the renumbering (source ids)

@@ -125,7 +125,9 @@ __device__ __forceinline__ uint32_t push_message(uint32_t du, uint32_t w) {
 // consecutive items, scans their lengths and walks the concatenated edges
 // 32 at a time, each lane finding its item by binary search over the scan.
 // Returns the vertices this warp appended (changed), counted on every lane.
-template <bool kW>
+// kNC: the previous values may be read through the non-coherent path (a
+// launch that runs one superstep); a persistent loop passes false.
+template <bool kW, bool kNC = true>
 __device__ __forceinline__ uint32_t push_superstep(const FrontierCfg& f, const uint32_t* out_ptr,
                                                    const uint32_t* out_dst, const uint32_t* out_w,
                                                    const uint32_t* own_cur, uint32_t* own_nxt,
@@ -171,7 +173,7 @@ __device__ __forceinline__ uint32_t push_superstep(const FrontierCfg& f, const u
             if (k < total) {
                 v = out_dst[e];
                 const uint32_t m = push_message<kW>(dj, kW ? out_w[e] : 0u);
-                const uint32_t nv = __ldcg(own_nxt + v), cv = __ldg(own_cur + v);   // both in flight
+                const uint32_t nv = __ldcg(own_nxt + v), cv = kNC ? __ldg(own_cur + v) : __ldca(own_cur + v);
                 if (m < nv && m < cv) app = atomicMin(own_nxt + v, m) >= cv;
                 if (app) {
                     deg = __ldg(out_ptr + v + 1) - __ldg(out_ptr + v);

@@ -413,6 +413,21 @@ struct RunCtl {
     uint32_t pad;
 };
 cudaError_t launch_run_control(RunCtl* ctl, const StepStats* ring, cudaGraphConditionalHandle h, cudaStream_t s);
+// Grid barrier state of the persistent run (zeroed before each launch).
+struct GridBar {
+    uint32_t count;   // CTAs arrived at the current barrier
+    uint32_t gen;     // barriers passed
+};
+// Persistent device-driven run of SSSP / CC on one partition (k_sell_loop):
+// the supersteps of ctl in one cooperative launch of at most one CTA per
+// co-resident slot. Returns cudaErrorNotSupported, launching nothing, when
+// a superstep needs more than kLoopWaves grids of co-resident CTAs (the
+// graph-driven loop then serves); a barrier wait past timeout_ns (or any,
+// with `force`) sets kErrTimeout in args.err and ends the launch.
+constexpr uint32_t kLoopWaves = 2;
+bool sell_loop_fits(Algo a, const SellArgs& args);
+cudaError_t launch_sell_loop(Algo a, const SellArgs& args, RunCtl* ctl, GridBar* bar, uint64_t timeout_ns,
+                             bool force, cudaStream_t s);
 size_t superstep_smem_bytes(Algo a, uint32_t max_items);
 
 cudaError_t launch_sync(const SyncArgs& args, uint32_t max_words, cudaStream_t s);

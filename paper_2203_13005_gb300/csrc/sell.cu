@@ -135,12 +135,23 @@ struct Source {
     }
 };
 
-// Superstep over the sliced-ELL layout (see the top of the file). kOne: a
-// single partition (no cached copies); kCheck: range-check every source id
-// (gxp_config.check_bounds), setting kErrBounds instead of loading.
-template <Algo A, bool kOne, bool kCheck>
-__global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : Ops<A>::kMinBlocks)
-    k_sell(const SellArgs a) {
+// The gathered values. A kernel that runs one superstep reads them through
+// the non-coherent path (nothing writes them during the launch); the
+// persistent loop, which writes in superstep t what superstep t + 1 reads,
+// uses coherent loads, ordered by its grid barrier.
+template <bool kLoop>
+__device__ __forceinline__ uint32_t vload(const uint32_t* p) {
+    if constexpr (kLoop) return __ldca(p);
+    else return ld_value(p);
+}
+
+// One CTA's share of superstep t over the sliced-ELL layout (see the top of
+// the file): work block vb of n_vb. kOne: a single partition (no cached
+// copies); kCheck: range-check every source id (gxp_config.check_bounds),
+// setting kErrBounds instead of loading; kLoop: called by the persistent
+// loop (k_sell_loop).
+template <Algo A, bool kOne, bool kCheck, bool kLoop>
+__device__ __forceinline__ void sell_cta(const SellArgs& a, const uint64_t t, const uint32_t vb, const uint32_t n_vb) {
     using Op = Ops<A>;
     using T = typename Op::T;
     constexpr int kU = Op::kUnroll;
@@ -151,7 +162,6 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // superstep t reads value buffer t & 1 and stat slot t, writes the others
-    const uint64_t t = a.step_dev ? *a.step_dev : a.step;
     const uint32_t* const own_cur = a.own[t & 1];
     uint32_t* const own_nxt = a.own[(t + 1) & 1];
     const float* const rank_cur = a.rank[t & 1];
@@ -161,7 +171,7 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
     FrontierCfg fc = a.fc;
     fc.list_in = a.lists[t & 1];
     if (fc.list_out) fc.list_out = a.lists[(t + 1) & 1];
-    if (blockIdx.x == 0) {
+    if (vb == 0) {
         // zero the ring slot two supersteps ahead (never read or written by this one)
         unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats + (t + 2) % kStatRing);
         for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
@@ -230,17 +240,17 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
     // a CTA takes kSellWarps * kItems consecutive work items, warp w the items
     // w, w + kSellWarps, ...: the heavy-first order still spreads over the warps
     constexpr int kItems = Op::kItems;
-    const uint32_t gw0 = blockIdx.x * (kSellWarps * kItems) + (uint32_t)warp;
+    const uint32_t gw0 = vb * (kSellWarps * kItems) + (uint32_t)warp;
     const uint32_t gw = gw0;
     bool f_has = false;   // pull direction with frontier lists: this lane's changed vertex
     uint32_t f_v = 0;
     bool pushed = false;
     if constexpr (A != Algo::PR) {
         if (push_chosen(fc, stats_in)) {   // same choice in every thread of the grid
-            const uint32_t c = push_superstep<Op::kWeighted>(fc, a.out_ptr, a.out_dst, a.out_w, own_cur,
-                                                             own_nxt, a.ghost, a.n_vertices,
-                                                             kOne ? nullptr : a.changed_bits, stats_in, stats_out,
-                                                             gw, (uint64_t)gridDim.x * kSellWarps, lane);
+            const uint32_t c = push_superstep<Op::kWeighted, !kLoop>(fc, a.out_ptr, a.out_dst, a.out_w, own_cur,
+                                                                     own_nxt, a.ghost, a.n_vertices,
+                                                                     kOne ? nullptr : a.changed_bits, stats_in,
+                                                                     stats_out, gw, (uint64_t)n_vb * kSellWarps, lane);
             if (lane == 0) n_changed += c;
             pushed = true;
         }
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
             for (int q = 0; q < kU; ++q)
                 if (j0 + (uint32_t)q * 32u + (uint32_t)lane < hp.ne) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
         };
-        for (uint32_t jb = 0; jb < hp.ne; jb += 32u * kU) hbatch(jb, [](const uint32_t* p) { return ld_value(p); });
+        for (uint32_t jb = 0; jb < hp.ne; jb += 32u * kU) hbatch(jb, [](const uint32_t* p) { return vload<kLoop>(p); });
         T total = warp_all<Op>(acc);
         bool do_apply = hp.nparts == 1u;
         if (!do_apply) {
@@ -354,7 +364,7 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
             }
 #pragma unroll
             for (int q = 0; q < kU; ++q)
-                x[q] = (uint32_t)q < ncols ? ld_value(S.at(checked(P, u[q]))) : Op::to_bits(Op::ident());
+                x[q] = (uint32_t)q < ncols ? vload<kLoop>(S.at(checked(P, u[q]))) : Op::to_bits(Op::ident());
 #pragma unroll
             for (int q = 0; q < kU; ++q)
                 if ((uint32_t)q < ncols) acc = Op::combine(acc, Op::gen(x[q], wv[q]));
@@ -461,10 +471,105 @@ __global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : O
             __threadfence_block();
             const unsigned long long x0 = atomicAdd(&s_acc[0], 0ull), x1 = atomicAdd(&s_acc[1], 0ull),
                                      x2 = atomicAdd(&s_acc[2], 0ull);
-            const uint32_t ln = blockIdx.x % kStatLanes;
+            const uint32_t ln = vb % kStatLanes;
             if (x0) atomicAdd(&stats_out->changed[ln], x0);
             if (x1) atomicAdd(&stats_out->l1_fx[ln], x1);
             if (x2) atomicAdd(&stats_out->dangling_fx[ln], x2);
+        }
+    }
+}
+
+template <Algo A, bool kOne, bool kCheck>
+__global__ void __launch_bounds__(kSellBlock, (A == Algo::SSSP && !kOne) ? 5 : Ops<A>::kMinBlocks)
+    k_sell(const SellArgs a) {
+    sell_cta<A, kOne, kCheck, false>(a, a.step_dev ? *a.step_dev : a.step, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier of all CTAs of a cooperative grid: arrival counter and generation
+// (the last CTA to arrive resets the counter, then releases the next
+// generation). A wait that runs past timeout_ns, or any wait when `force`
+// (an injected fault), sets kErrTimeout and gives up; the caller then
+// returns. Returns false when this CTA gave up or another one had.
+__device__ bool grid_barrier(GridBar* b, uint32_t n_ctas, uint64_t timeout_ns, bool force, uint32_t* err) {
+    __shared__ uint32_t s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t gen = ld_acquire_gpu(&b->gen);
+        __threadfence();
+        uint32_t ok = 1u;
+        if (atomicAdd(&b->count, 1u) == n_ctas - 1u) {
+            b->count = 0u;   // the others wait on gen, not on the counter
+            st_release_gpu(&b->gen, gen + 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (ld_acquire_gpu(&b->gen) == gen) {
+                if (force || global_ns() - t0 > timeout_ns) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0u;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence();
+        }
+        if (ok && (ld_acquire_gpu(err) & kErrTimeout)) ok = 0u;   // another CTA gave up
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0u;
+}
+
+// Persistent form of a device-driven run (one partition, SSSP / CC, graphs
+// whose superstep is a few waves of CTAs): one cooperative launch runs the
+// supersteps from ctl->step until ctl->limit, or until the first superstep
+// that changed nothing when ctl->quiet_stop. Each CTA takes the work blocks
+// vb = blockIdx.x, blockIdx.x + gridDim.x, ... of a superstep (the blocks a
+// one-superstep launch would run as CTAs), then all CTAs meet at a grid
+// barrier: the Jacobi order of supersteps is the same as one launch per
+// superstep, without a launch and a control kernel in between.
+template <Algo A, bool kCheck>
+__global__ void __launch_bounds__(kSellBlock, Ops<A>::kMinBlocks)
+    k_sell_loop(const SellArgs a, RunCtl* ctl, GridBar* bar, uint32_t n_vb, uint64_t timeout_ns, uint32_t force) {
+    __shared__ uint32_t s_more;
+    uint64_t t = ctl->step;
+    const uint64_t limit = ctl->limit;
+    const uint32_t quiet_stop = ctl->quiet_stop;
+    for (;;) {
+        for (uint32_t vb = blockIdx.x; vb < n_vb; vb += gridDim.x) {
+            sell_cta<A, true, kCheck, true>(a, t, vb, n_vb);
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, gridDim.x, timeout_ns, force != 0u, a.err)) return;
+        ++t;   // supersteps done; slot t holds the last one's counts
+        if (threadIdx.x < 32) {
+            bool more = t < limit;
+            if (more && quiet_stop) {
+                const StepStats* st = a.stats + t % kStatRing;
+                unsigned long long c = __ldcg(&st->changed[threadIdx.x]) + __ldcg(&st->changed[threadIdx.x + 32]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+                more = c != 0ull;
+            }
+            if (threadIdx.x == 0) s_more = more ? 1u : 0u;
+        }
+        __syncthreads();
+        if (!s_more) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->step = t;
+            return;
         }
     }
 }
@@ -508,6 +613,66 @@ static void launch_sell(const SellArgs& args, bool one, uint32_t grid, cudaStrea
     } else {
         if (args.check_bounds) k_sell<A, false, true><<<grid, kSellBlock, 0, s>>>(args);
         else k_sell<A, false, false><<<grid, kSellBlock, 0, s>>>(args);
+    }
+}
+
+// Co-resident CTAs of k_sell_loop<A, kCheck> on the current device (queried
+// on every call: the device, hence the SM count, may differ between calls).
+template <Algo A, bool kCheck>
+static cudaError_t loop_resident(uint64_t* resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell_loop<A, kCheck>, kSellBlock, 0);
+    *resident = e == cudaSuccess ? (uint64_t)sms * (uint64_t)per_sm : 0;
+    return e;
+}
+
+template <Algo A, bool kCheck>
+static cudaError_t launch_loop_t(const SellArgs& args, RunCtl* ctl, GridBar* bar, uint32_t n_vb, uint64_t timeout_ns,
+                                 uint32_t force, cudaStream_t s) {
+    uint64_t resident = 0;
+    const cudaError_t e = loop_resident<A, kCheck>(&resident);
+    if (e != cudaSuccess) return e;
+    if (resident == 0 || n_vb > kLoopWaves * resident) return cudaErrorNotSupported;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(n_vb, resident);
+    SellArgs a = args;
+    void* params[] = {&a, &ctl, &bar, &n_vb, &timeout_ns, &force};
+    return cudaLaunchCooperativeKernel((const void*)k_sell_loop<A, kCheck>, dim3(grid), dim3(kSellBlock), params, 0, s);
+}
+
+static uint32_t loop_blocks(const SellArgs& args) {
+    const uint64_t work = (uint64_t)args.n_hubs + args.n_slices;
+    return (uint32_t)std::max<uint64_t>(1, (work + kSellWarps - 1) / kSellWarps);
+}
+
+bool sell_loop_fits(Algo alg, const SellArgs& args) {
+    if (args.n_parts != 1 || args.n_zero != 0 || args.early_exit || (alg != Algo::SSSP && alg != Algo::CC)) return false;
+    uint64_t resident = 0;
+    cudaError_t e;
+    if (alg == Algo::SSSP) e = args.check_bounds ? loop_resident<Algo::SSSP, true>(&resident)
+                                                 : loop_resident<Algo::SSSP, false>(&resident);
+    else e = args.check_bounds ? loop_resident<Algo::CC, true>(&resident) : loop_resident<Algo::CC, false>(&resident);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return resident > 0 && loop_blocks(args) <= kLoopWaves * resident;
+}
+
+cudaError_t launch_sell_loop(Algo alg, const SellArgs& args, RunCtl* ctl, GridBar* bar, uint64_t timeout_ns,
+                             bool force, cudaStream_t s) {
+    if (args.n_parts != 1 || args.n_zero != 0 || args.early_exit) return cudaErrorInvalidValue;
+    const uint32_t n_vb = loop_blocks(args);
+    const uint32_t f = force ? 1u : 0u;
+    switch (alg) {
+        case Algo::SSSP:
+            return args.check_bounds ? launch_loop_t<Algo::SSSP, true>(args, ctl, bar, n_vb, timeout_ns, f, s)
+                                     : launch_loop_t<Algo::SSSP, false>(args, ctl, bar, n_vb, timeout_ns, f, s);
+        case Algo::CC:
+            return args.check_bounds ? launch_loop_t<Algo::CC, true>(args, ctl, bar, n_vb, timeout_ns, f, s)
+                                     : launch_loop_t<Algo::CC, false>(args, ctl, bar, n_vb, timeout_ns, f, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -59,7 +59,8 @@ class gxp_stats(C.Structure):
                 ("syncs_skipped", C.c_uint64), ("sync_pairs", C.c_uint64), ("last_l1_delta", C.c_double),
                 ("last_dangling", C.c_double), ("last_superstep_ms", C.c_double),
                 ("device_bytes", C.c_uint64), ("push_supersteps", C.c_uint64), ("cache_downloads", C.c_uint64),
-                ("last_kernel_ms", C.c_double), ("reserved", C.c_uint64 * 3)]
+                ("last_kernel_ms", C.c_double), ("persistent_launches", C.c_uint64),
+                ("reserved", C.c_uint64 * 2)]
 
 
 # (name, restype, argtypes) of every exported symbol

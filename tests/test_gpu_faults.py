@@ -4,8 +4,8 @@ GXP_FAULT environment variable).
 Every fault here is made on the host: a device allocation that reports
 out-of-memory, a host-to-device copy that is not enqueued, an exchange
 between partitions whose kernels are not launched (a lost message), and, for
-the allocation-free entry point (tests/test_zz_no_alloc.py), a bounded
-device wait that gives up at once. None of them faults, traps or hangs the
+the allocation-free entry point (tests/test_zz_no_alloc.py) and the
+persistent run's grid barrier, a bounded device wait that gives up at once. None of them faults, traps or hangs the
 GPU. The tests check the exact status code, that a poisoning code leaves the
 context answering GXP_E_STATE until gxp_destroy, that gxp_destroy is clean,
 and that the context (allocation faults) or a fresh one (the others) then
@@ -181,6 +181,28 @@ def test_dropped_exchange_in_a_run(gpu, cc_graph):
         ctx.run(gxp.GXP_ALGO_CC)
     assert _code(ei) == gxp.GXP_E_LOST
     ctx.close()
+
+
+@pytest.mark.parametrize("algo", [gxp.GXP_ALGO_SSSP, gxp.GXP_ALGO_CC])
+def test_persistent_run_barrier_gives_up(gpu, sssp_graph, algo):
+    """A small single-partition run goes through the persistent kernel, whose
+    CTAs meet at a bounded grid barrier after each superstep. With the
+    timeout fault every barrier wait gives up at once (no wait runs out on
+    its own): the run returns GXP_E_TIMEOUT, the context is poisoned, and a
+    fresh context reaches the oracle's result through the same kernel."""
+    n, src, dst, w, d_ref, steps_ref = sssp_graph
+    ctx = gxp.Context(0, fault=gxp.GXP_FAULT_TIMEOUT)
+    ctx.create_graph(n, 1)
+    ctx.load_coo(src, dst, w)
+    with pytest.raises(gxp.GxpError) as ei:
+        ctx.run(algo, source=0)
+    assert _code(ei) == gxp.GXP_E_TIMEOUT
+    _assert_poisoned(ctx, sssp_graph)
+    ctx.close()
+    with gxp.Context(0) as fresh:
+        d, steps = _sssp_run(fresh, sssp_graph)
+        assert fresh.stats()["persistent_launches"] >= 1   # the same kernel, waits intact
+    assert np.array_equal(d, d_ref) and steps == steps_ref
 
 
 def test_unknown_fault_kinds_are_ignored(gpu, sssp_graph, monkeypatch):

@@ -313,6 +313,20 @@ def test_reloads_reuse_device_memory():
             assert held.setdefault((scale, seed), b) == b
 
 
+def test_partitioned_then_single_partition_graph():
+    # one context: a graph in 4 partitions (exchange buffers), then graphs in
+    # one partition (none), then partitions again, each against the oracle
+    with gxp.Context(0, check_bounds=True) as c:
+        for parts, scale, seed in [(4, 11, 5), (1, 12, 6), (1, 10, 7), (4, 12, 8)]:
+            n = 1 << scale
+            src, dst = synth.erdos_renyi(n, 4 << scale, seed)
+            lab_ref, steps_ref, _ = oracle.cc(n, src, dst)
+            c.create_graph(n, parts)
+            c.load_coo(src, dst)
+            assert c.run(gxp.GXP_ALGO_CC) == steps_ref, (parts, scale)
+            assert np.array_equal(c.values(), lab_ref), (parts, scale)
+
+
 def test_pagerank_rmat22_full_and_deterministic():
     wl = synth.PAGERANK_RMAT22
     src, dst, _ = wl.edges()
