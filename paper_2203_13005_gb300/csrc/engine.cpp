@@ -490,7 +490,9 @@ void Engine::build_sell() {
         uint32_t* sw = weighted ? (uint32_t*)dalloc(4 * pad4(E)) : nullptr;
         uint2* big = (uint2*)talloc(8 * ((size_t)n + E / 2048 + 1));
         uint32_t* cnt = (uint32_t*)talloc(4);
-        cuda_check(launch_sort_rows(col_ptr, n, work_[p].in, ssrc, sw, big, cnt, stream_), "sort rows");
+        cuda_check(launch_sort_rows(col_ptr, n, work_[p].in, pd_[p].n_own + pd_[p].n_ghost, ssrc, sw, big, cnt,
+                                    stream_),
+                   "sort rows");
         // 2. windows
         const uint32_t nw = (n + kSellWindow - 1) / kSellWindow;
         uint32_t* rows_out = (uint32_t*)talloc(4 * (size_t)n);

@@ -511,9 +511,11 @@ struct RowSource {
     const uint32_t* row_map;    // nullptr: identity
     const uint32_t* src_map;    // nullptr: identity
 };
-// rows of col_ptr (the result's offsets) sorted by (source, weight) into ssrc / sw
-cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const RowSource& in, uint32_t* ssrc, uint32_t* sw,
-                             uint2* scratch_runs, uint32_t* scratch_cnt,
+// rows of col_ptr (the result's offsets) sorted by source into ssrc / sw
+// (rows of up to 256 edges by (source, weight), longer ones stably by
+// source); sources are below n_src
+cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const RowSource& in, uint32_t n_src,
+                             uint32_t* ssrc, uint32_t* sw, uint2* scratch_runs, uint32_t* scratch_cnt,
                              cudaStream_t s);   // scratch_runs: n + n_edges / 2048 + 1 entries
 cudaError_t launch_sell_windows(const uint32_t* col_ptr, uint32_t n, uint32_t H, uint32_t* rows_out,
                                 uint32_t* hub_out, uint32_t* nonhub_cnt, uint32_t* hub_cnt, cudaStream_t s);

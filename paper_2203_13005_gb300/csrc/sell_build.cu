@@ -2,11 +2,12 @@
 // blocks of Section II-B, in the form the superstep kernel reads):
 //
 //  1. k_sort_rows_warp / k_sort_rows_block: each row's in-edges sorted by
-//     (source, weight) (by source when unweighted), so the k-th sources of a slice's rows fall in
-//     similar id ranges. Rows of up to 32 / 256 edges are bitonic-sorted in
-//     a warp's registers, rows of up to kSortMax edges in shared memory;
-//     longer (hub) rows are sorted in runs of kSortMax edges, so each run a
-//     warp gathers is ordered.
+//     source, so the k-th sources of a slice's rows fall in similar id
+//     ranges. Rows of up to 32 / 256 edges are bitonic-sorted in a warp's
+//     registers (by (source, weight)), rows of up to kSortMax edges
+//     radix-sorted in shared memory (stably by source); longer (hub) rows
+//     are sorted in runs of kSortMax edges, so each run a warp gathers is
+//     ordered.
 //  2. k_sell_windows: per window of kSellWindow rows, a stable counting sort
 //     of the rows with at most H in-edges by descending in-degree (one CTA
 //     per window, per-warp bins in shared memory; degrees above kExactBins
@@ -121,73 +122,150 @@ __device__ __forceinline__ void sort_row_in_warp(uint32_t b, uint32_t ib, uint32
     }
 }
 
-// one warp per row: sorts rows of up to 256 edges, lists the runs of
-// kSortMax edges of longer rows ({row, first edge of the run}) for the block sort
+// A warp takes 32 consecutive rows at a time: their offsets (and, through
+// the row map, where their edges come from) are read by one lane each, so
+// the rows' headers cost one round of loads rather than a chain per row, and
+// rows without edges cost nothing more. Then the warp sorts the rows of up to
+// 256 edges one after another and lists the runs of kSortMax edges of longer
+// rows ({row, first edge of the run}) for the block sort.
 template <bool kW>
 __global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const RowSource in, uint32_t* ssrc,
                                  uint32_t* sw, uint2* big_runs, uint32_t* n_big) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = warp0; v < n; v += n_warps) {
-        const uint32_t b = col_ptr[v], d = col_ptr[v + 1] - b;
-        const uint32_t ib = in.col_ptr[in.row_map ? in.row_map[v] : (uint32_t)v];
-        if (d <= 32) {
-            sort_row_in_warp<1, kW>(b, ib, d, in.src, in.w, in.src_map, ssrc, sw, lane);
-        } else if (d <= 256) {
-            sort_row_in_warp<8, kW>(b, ib, d, in.src, in.w, in.src_map, ssrc, sw, lane);
-        } else {
-            const uint32_t runs = (d + kSortMax - 1) / kSortMax;
-            uint32_t at = 0;
-            if (lane == 0) at = atomicAdd(n_big, runs);
-            at = __shfl_sync(kFull, at, 0);
-            for (uint32_t r = lane; r < runs; r += 32) big_runs[at + r] = make_uint2((uint32_t)v, r * kSortMax);
+    for (uint64_t v0 = warp0 * 32; v0 < n; v0 += n_warps * 32) {
+        const uint64_t v = v0 + (uint32_t)lane;
+        uint32_t b = 0, d = 0, ib = 0;
+        if (v < n) {
+            b = col_ptr[v];
+            d = col_ptr[v + 1] - b;
+            if (d) ib = in.col_ptr[in.row_map ? in.row_map[v] : (uint32_t)v];
+        }
+        for (unsigned todo = __ballot_sync(kFull, d != 0u); todo; todo &= todo - 1u) {
+            const int r = __ffs(todo) - 1;
+            const uint32_t rb = __shfl_sync(kFull, b, r), rd = __shfl_sync(kFull, d, r), rib = __shfl_sync(kFull, ib, r);
+            if (rd <= 32) {
+                sort_row_in_warp<1, kW>(rb, rib, rd, in.src, in.w, in.src_map, ssrc, sw, lane);
+            } else if (rd <= 256) {
+                sort_row_in_warp<8, kW>(rb, rib, rd, in.src, in.w, in.src_map, ssrc, sw, lane);
+            } else {
+                const uint32_t runs = (rd + kSortMax - 1) / kSortMax;
+                uint32_t at = 0;
+                if (lane == 0) at = atomicAdd(n_big, runs);
+                at = __shfl_sync(kFull, at, 0);
+                for (uint32_t k = lane; k < runs; k += 32)
+                    big_runs[at + k] = make_uint2((uint32_t)(v0 + (uint32_t)r), k * kSortMax);
+            }
         }
     }
 }
 
-// one CTA per listed run (257 .. kSortMax edges): bitonic sort in shared memory
+// One CTA per listed run (257 .. kSortMax edges): a stable LSD radix sort of
+// the run's sources in shared memory, 8 bits per pass (ceil(key_bits / 8)
+// passes), carrying each edge's position in the run so that weights follow.
+// Equal sources keep their input order. Warp w owns positions [256 w, 256 w
+// + 256) and walks them 32 at a time in order: per pass it counts the digits
+// of its keys (match_any groups), a scan over (digit, warp) gives every
+// warp's first slot per digit, and the second walk places each key at its
+// slot plus its rank among the equal digits of its 32.
+constexpr int kRadixWarps = 8;
+constexpr uint32_t kRadixPerWarp = kSortMax / kRadixWarps;   // 256
+static_assert(kRadixPerWarp % 32 == 0, "whole warp steps");
+
 template <bool kW>
-__global__ void __launch_bounds__(256) k_sort_rows_block(const uint32_t* col_ptr, const RowSource in, uint32_t* ssrc,
-                                                         uint32_t* sw, const uint2* big_runs, const uint32_t* n_big) {
-    using K = SortKey<kW>;
-    __shared__ typename K::T x[kSortMax];
+__global__ void __launch_bounds__(kRadixWarps * 32) k_sort_rows_block(const uint32_t* col_ptr, const RowSource in,
+                                                                      uint32_t* ssrc, uint32_t* sw,
+                                                                      const uint2* big_runs, const uint32_t* n_big,
+                                                                      uint32_t key_bits) {
+    __shared__ uint32_t key[2][kSortMax];
+    __shared__ uint16_t pos[2][kSortMax];
+    __shared__ uint32_t hist[kRadixWarps][256];
+    __shared__ uint32_t warp_tot[kRadixWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t cnt = *n_big;
+    const uint32_t passes = (key_bits + 7) / 8;
     for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
         const uint2 run = big_runs[r];
         const uint32_t b = col_ptr[run.x] + run.y;
         const uint32_t d = min(kSortMax, col_ptr[run.x + 1] - b);
         const uint32_t ib = in.col_ptr[in.row_map ? in.row_map[run.x] : run.x] + run.y;
-        uint32_t N = 32;
-        while (N < d) N <<= 1;
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-            if (i < d) {
-                const uint32_t u = in.src[ib + i];
-                x[i] = K::make(in.src_map ? in.src_map[u] : u, in.w, ib + i);
-            } else {
-                x[i] = K::kMax;
-            }
+        __syncthreads();   // the previous run's buffers are read out
+        for (uint32_t i = tid; i < d; i += blockDim.x) {
+            const uint32_t u = in.src[ib + i];
+            key[0][i] = in.src_map ? in.src_map[u] : u;
+            pos[0][i] = (uint16_t)i;
         }
-        __syncthreads();
-        for (uint32_t k = 2; k <= N; k <<= 1)
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-                    const uint32_t p = i ^ j;
-                    if (p > i) {
-                        const bool up = (i & k) == 0;
-                        const typename K::T a = x[i], c = x[p];
-                        if ((a > c) == up) {
-                            x[i] = c;
-                            x[p] = a;
-                        }
-                    }
+        int cur = 0;
+        // this warp's positions (runs shorter than kSortMax leave the last warps idle)
+        const uint32_t w_end = min((uint32_t)(warp + 1) * kRadixPerWarp, (d + 31u) & ~31u);
+        for (uint32_t p = 0; p < passes; ++p) {
+            const uint32_t sh = 8u * p;
+            for (uint32_t i = tid; i < kRadixWarps * 256; i += blockDim.x) (&hist[0][0])[i] = 0u;
+            __syncthreads();
+            // counts of each warp's digits
+            for (uint32_t j0 = (uint32_t)warp * kRadixPerWarp; j0 < w_end; j0 += 32) {
+                const uint32_t i = j0 + (uint32_t)lane;
+                const bool has = i < d;
+                const uint32_t dg = has ? (key[cur][i] >> sh) & 255u : 0u;
+                const unsigned act = __ballot_sync(kFull, has);
+                if (has) {
+                    const unsigned grp = __match_any_sync(act, dg);
+                    if (lane == __ffs(grp) - 1) hist[warp][dg] += (uint32_t)__popc(grp);
                 }
-                __syncthreads();
+                __syncwarp();
             }
-        for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
-            ssrc[b + i] = K::src(x[i]);
-            if (kW) sw[b + i] = K::wt(x[i]);
+            __syncthreads();
+            // first slot of (digit, warp): digits ascending, warps in order
+            {
+                const uint32_t dg = (uint32_t)tid;   // 256 threads, one digit each
+                uint32_t c[kRadixWarps], tot = 0;
+#pragma unroll
+                for (int w = 0; w < kRadixWarps; ++w) {
+                    c[w] = hist[w][dg];
+                    tot += c[w];
+                }
+                uint32_t incl = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane == 31) warp_tot[warp] = incl;
+                __syncthreads();
+                uint32_t base = incl - tot;
+                for (int w = 0; w < warp; ++w) base += warp_tot[w];
+#pragma unroll
+                for (int w = 0; w < kRadixWarps; ++w) {
+                    hist[w][dg] = base;
+                    base += c[w];
+                }
+            }
+            __syncthreads();
+            // place: each warp's keys in order, equal digits ranked by lane
+            for (uint32_t j0 = (uint32_t)warp * kRadixPerWarp; j0 < w_end; j0 += 32) {
+                const uint32_t i = j0 + (uint32_t)lane;
+                const bool has = i < d;
+                const uint32_t k = has ? key[cur][i] : 0u;
+                const uint32_t dg = (k >> sh) & 255u;
+                const unsigned act = __ballot_sync(kFull, has);
+                unsigned grp = 0;
+                if (has) {
+                    grp = __match_any_sync(act, dg);
+                    const uint32_t at = hist[warp][dg] + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+                    key[cur ^ 1][at] = k;
+                    pos[cur ^ 1][at] = pos[cur][i];
+                }
+                __syncwarp();
+                if (has && lane == __ffs(grp) - 1) hist[warp][dg] += (uint32_t)__popc(grp);
+                __syncwarp();
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        for (uint32_t i = tid; i < d; i += blockDim.x) {
+            ssrc[b + i] = key[cur][i];
+            if (kW) sw[b + i] = in.w[ib + pos[cur][i]];
         }
     }
 }
@@ -611,17 +689,23 @@ uint32_t grid_warps(uint64_t warps, uint32_t block) {
 
 }  // namespace
 
-cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const RowSource& in, uint32_t* ssrc, uint32_t* sw,
-                             uint2* scratch_runs, uint32_t* scratch_cnt, cudaStream_t s) {
+cudaError_t launch_sort_rows(const uint32_t* col_ptr, uint32_t n, const RowSource& in, uint32_t n_src,
+                             uint32_t* ssrc, uint32_t* sw, uint2* scratch_runs, uint32_t* scratch_cnt, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(scratch_cnt, 0, 4, s);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
+    uint32_t key_bits = 1;   // bits of the largest source id
+    while (key_bits < 32 && ((uint64_t)(n_src ? n_src - 1 : 0) >> key_bits) != 0) ++key_bits;
     if (in.w) {
-        k_sort_rows_warp<true><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, in, ssrc, sw, scratch_runs, scratch_cnt);
-        k_sort_rows_block<true><<<152 * 8, 256, 0, s>>>(col_ptr, in, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_warp<true><<<grid_warps((n + 31) / 32, 256), 256, 0, s>>>(col_ptr, n, in, ssrc, sw, scratch_runs,
+                                                                             scratch_cnt);
+        k_sort_rows_block<true><<<152 * 6, kRadixWarps * 32, 0, s>>>(col_ptr, in, ssrc, sw, scratch_runs, scratch_cnt,
+                                                                      key_bits);
     } else {
-        k_sort_rows_warp<false><<<grid_warps(n, 256), 256, 0, s>>>(col_ptr, n, in, ssrc, sw, scratch_runs, scratch_cnt);
-        k_sort_rows_block<false><<<152 * 8, 256, 0, s>>>(col_ptr, in, ssrc, sw, scratch_runs, scratch_cnt);
+        k_sort_rows_warp<false><<<grid_warps((n + 31) / 32, 256), 256, 0, s>>>(col_ptr, n, in, ssrc, sw, scratch_runs,
+                                                                              scratch_cnt);
+        k_sort_rows_block<false><<<152 * 6, kRadixWarps * 32, 0, s>>>(col_ptr, in, ssrc, sw, scratch_runs, scratch_cnt,
+                                                                       key_bits);
     }
     return cudaGetLastError();
 }
