@@ -145,8 +145,13 @@ __global__ void k_sort_rows_warp(const uint32_t* col_ptr, uint32_t n, const RowS
         for (unsigned todo = __ballot_sync(kFull, d != 0u); todo; todo &= todo - 1u) {
             const int r = __ffs(todo) - 1;
             const uint32_t rb = __shfl_sync(kFull, b, r), rd = __shfl_sync(kFull, d, r), rib = __shfl_sync(kFull, ib, r);
+            // the smallest register network that holds the row
             if (rd <= 32) {
                 sort_row_in_warp<1, kW>(rb, rib, rd, in.src, in.w, in.src_map, ssrc, sw, lane);
+            } else if (rd <= 64) {
+                sort_row_in_warp<2, kW>(rb, rib, rd, in.src, in.w, in.src_map, ssrc, sw, lane);
+            } else if (rd <= 128) {
+                sort_row_in_warp<4, kW>(rb, rib, rd, in.src, in.w, in.src_map, ssrc, sw, lane);
             } else if (rd <= 256) {
                 sort_row_in_warp<8, kW>(rb, rib, rd, in.src, in.w, in.src_map, ssrc, sw, lane);
             } else {
