@@ -360,7 +360,9 @@ typedef struct gxp_batch_report {
     uint64_t tune_from_cache;   /* 1: the coefficients and block size came from the tune cache */
     uint64_t active_edges;      /* in-edges whose source was in the frontier, summed over the
                                    supersteps (each gathered a 256-byte distance row) */
-    uint64_t reserved[4];
+    uint64_t persistent;        /* 1: resident edges, the whole run in one persistent
+                                   cooperative kernel (grid barrier between supersteps) */
+    uint64_t reserved[3];
 } gxp_batch_report;
 
 /* One autotuner record (Section III-A): the per-edge download, compute and

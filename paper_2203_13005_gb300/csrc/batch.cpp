@@ -85,6 +85,10 @@ void Engine::prepare_batch(bool streamed) {
         const size_t words = (V + 31) / 32 + 1;
         b.d_frontier[0] = (uint32_t*)dalloc(4 * words);
         b.d_frontier[1] = (uint32_t*)dalloc(4 * words);
+        b.d_frontier[2] = (uint32_t*)dalloc(4 * words);
+        b.d_loop_changed = (unsigned long long*)dalloc(8 * 4);
+        b.d_bar = (GridBar*)dalloc(sizeof(GridBar));
+        b.d_steps = (uint32_t*)dalloc(4);
         b.d_sources = (uint32_t*)dalloc(4 * 64);
         cuda_check(cudaStreamCreateWithFlags(&b.s_h2d, cudaStreamNonBlocking), "stream");
         cuda_check(cudaStreamCreateWithFlags(&b.s_d2h, cudaStreamNonBlocking), "stream");
@@ -430,11 +434,39 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
     }
 
     cuda_check(cudaMemsetAsync(b.d_active, 0, 8, stream_), "memset");
-    cuda_check(cudaEventRecord(b.ev_t0, stream_), "event");
+    const uint32_t max_steps = opts.max_steps ? opts.max_steps : 0xFFFFFFFFu;
+    // resident edges: the whole run in one persistent cooperative kernel
+    // (k_msssp_loop, a grid barrier between supersteps, the changed count
+    // tested on the device); streamed edges: one superstep (copies and
+    // kernels of the pipeline) per launch, the changed count read between
+    bool persistent = !streamed;
+    if (persistent) {
+        cuda_check(cudaMemsetAsync(b.d_frontier[1], 0, 4 * words, stream_), "memset");
+        cuda_check(cudaMemsetAsync(b.d_loop_changed, 0, 8 * 4, stream_), "memset");
+        cuda_check(cudaMemsetAsync(b.d_bar, 0, sizeof(GridBar), stream_), "memset");
+        MsArgs a{};
+        a.units = b.d_units;
+        a.u_begin = 0;
+        a.u_end = b.units.size();
+        a.edges = b.d_edges;
+        a.packed = 0;
+        a.edge_base = 0;
+        a.dist = b.d_dist;
+        a.active = b.d_active;
+        cuda_check(cudaEventRecord(b.ev_t0, stream_), "event");
+        const cudaError_t e = launch_msssp_loop(a, b.d_frontier, b.d_loop_changed, words, max_steps, b.d_bar,
+                                                cfg_.timeout_ns, faults_.timeout, d_err_, b.d_steps, stream_);
+        if (e == cudaErrorNotSupported || e == cudaErrorCooperativeLaunchTooLarge) {
+            cudaGetLastError();   // launch per superstep instead
+            persistent = false;
+        } else {
+            cuda_check(e, "batch loop");
+        }
+    }
+    if (!persistent) cuda_check(cudaEventRecord(b.ev_t0, stream_), "event");
     int parity = 0;
     uint32_t steps = 0;
-    const uint32_t max_steps = opts.max_steps ? opts.max_steps : 0xFFFFFFFFu;
-    while (steps < max_steps) {
+    while (!persistent && steps < max_steps) {
         if (use_graph) cuda_check(cudaGraphLaunch(b.graph[parity], stream_), "graph launch");
         else superstep_batch(cuts, streamed, pipelined, false, parity);
         cuda_check(cudaStreamSynchronize(stream_), "superstep");
@@ -446,10 +478,15 @@ void Engine::sssp_batch(const uint32_t* sources, uint32_t n_src, uint32_t* dist_
     }
     cuda_check(cudaEventRecord(b.ev_t1, stream_), "event");
     cuda_check(cudaEventSynchronize(b.ev_t1), "sync");
+    if (persistent) {
+        check_device_error();   // a grid barrier that ran out of time
+        cuda_check(cudaMemcpy(&steps, b.d_steps, 4, cudaMemcpyDeviceToHost), "read steps");
+    }
     float ms = 0;
     cuda_check(cudaEventElapsedTime(&ms, b.ev_t0, b.ev_t1), "elapsed");
     r.ms_total = ms;
     r.supersteps = steps;
+    r.persistent = persistent ? 1u : 0u;
     unsigned long long active = 0;
     cuda_check(cudaMemcpyAsync(&active, b.d_active, 8, cudaMemcpyDeviceToHost, stream_), "read counts");
     if (dist_out)

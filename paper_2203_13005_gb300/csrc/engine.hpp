@@ -172,7 +172,10 @@ private:
         bool packed = false;
         uint64_t ring_edges = 0;
         uint32_t* d_dist = nullptr;        // [V][64]
-        uint32_t* d_frontier[2] = {nullptr, nullptr};
+        uint32_t* d_frontier[3] = {nullptr, nullptr, nullptr};   // [2]: the persistent run's third bitmap
+        unsigned long long* d_loop_changed = nullptr;   // [4] the persistent run's changed counters
+        GridBar* d_bar = nullptr;
+        uint32_t* d_steps = nullptr;
         unsigned long long* d_changed = nullptr;   // per-block counters
         unsigned long long* d_active = nullptr;    // active in-edges over a run (the roofline's row gathers)
         unsigned long long* h_changed = nullptr;   // pinned mirror (upload stage)

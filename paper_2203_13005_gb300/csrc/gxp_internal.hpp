@@ -496,6 +496,15 @@ cudaError_t launch_exclusive_scan_u32(const uint32_t* x, uint32_t n, uint32_t* o
                                       cudaStream_t s);
 
 cudaError_t launch_msssp(const MsArgs& a, bool dry, uint32_t grid, cudaStream_t s);
+// Persistent resident run (k_msssp_loop): supersteps over the units of `a`
+// until one improves nothing or max_steps, one cooperative launch; frontier
+// rotates over three bitmaps of `words` words (frontier[0] holds the sources,
+// frontier[1] must be zero), changed over four counters (the first two zero);
+// *steps_out gets the supersteps run. A grid-barrier wait past timeout_ns (or any, with `force`)
+// sets kErrTimeout in *err and ends the launch.
+cudaError_t launch_msssp_loop(const MsArgs& a, uint32_t* const frontier[3], unsigned long long* changed,
+                              uint64_t words, uint32_t max_steps, GridBar* bar, uint64_t timeout_ns, bool force,
+                              uint32_t* err, uint32_t* steps_out, cudaStream_t s);
 cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_t* sources, uint32_t n_sources,
                               uint32_t* frontier, cudaStream_t s);
 cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long* out, cudaStream_t s);

@@ -24,6 +24,7 @@
 // result; superstep counts may be below Jacobi's.
 #include <algorithm>
 
+#include "grid_sync.cuh"
 #include "gxp_internal.hpp"
 
 namespace gxp {
@@ -49,8 +50,11 @@ __device__ __forceinline__ uint2 load_edge(const void* base, uint64_t i) {
     return __ldg(static_cast<const uint2*>(base) + i);
 }
 
-template <bool kDry, bool kPacked>
-__global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
+// One block's share of a superstep (the units u_begin + warp, + n_warps, ...
+// of the grid). kLoop: called by the persistent loop, which reads frontier
+// bits written earlier in the same launch, so through coherent loads.
+template <bool kDry, bool kPacked, bool kLoop>
+__device__ __forceinline__ void msssp_block(const MsArgs& a) {
     __shared__ uint32_t s_imp[2], s_done;
     __shared__ unsigned long long s_changed, s_active;
     const int lane = threadIdx.x & 31;
@@ -79,7 +83,8 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
             bool act = false;
             if (base + lane < len) {
                 my = load_edge<kPacked>(a.edges, e + base + lane);
-                act = (__ldg(a.frontier_cur + (my.x >> 5)) >> (my.x & 31u)) & 1u;
+                const uint32_t fw = kLoop ? __ldca(a.frontier_cur + (my.x >> 5)) : __ldg(a.frontier_cur + (my.x >> 5));
+                act = (fw >> (my.x & 31u)) & 1u;
             }
             uint32_t mask = __ballot_sync(kFull, act);
             any |= mask != 0u;
@@ -162,6 +167,46 @@ __global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
     }
 }
 
+template <bool kDry, bool kPacked>
+__global__ void __launch_bounds__(kMsBlock, 4) k_msssp(const MsArgs a) {
+    msssp_block<kDry, kPacked, false>(a);
+}
+
+// Persistent form of a resident batched run: one cooperative launch runs
+// supersteps until one improves nothing (or max_steps). Superstep t reads
+// frontier F[t % 3], sets bits in F[(t + 1) % 3] and counts its changed
+// units in changed[t % 4]; meanwhile every CTA clears its share of F[(t + 2)
+// % 3], which superstep t - 1 read and superstep t + 1 writes, and block 0
+// clears changed[(t + 2) % 4] (every CTA read the counter of superstep t - 2
+// before it arrived at the barrier that ended superstep t - 1), so one grid
+// barrier per superstep orders everything. The distances are updated in
+// place, as in the launch-per-superstep form.
+template <bool kPacked>
+__global__ void __launch_bounds__(kMsBlock, 4)
+    k_msssp_loop(MsArgs a, uint32_t* f0, uint32_t* f1, uint32_t* f2, unsigned long long* changed, uint64_t words,
+                 uint32_t max_steps, GridBar* bar, uint64_t timeout_ns, uint32_t force, uint32_t* err,
+                 uint32_t* steps_out) {
+    uint32_t* const F[3] = {f0, f1, f2};
+    __shared__ uint32_t s_more;
+    for (uint32_t t = 0; t < max_steps; ++t) {
+        a.frontier_cur = F[t % 3];
+        a.frontier_next = F[(t + 1) % 3];
+        a.changed = changed + t % 4;
+        uint32_t* const clear = F[(t + 2) % 3];
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+            clear[i] = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) changed[(t + 2) % 4] = 0ull;
+        msssp_block<false, kPacked, true>(a);
+        if (!grid_barrier(bar, gridDim.x, timeout_ns, force != 0u, err)) return;
+        if (threadIdx.x == 0) s_more = __ldcg(changed + t % 4) != 0ull ? 1u : 0u;
+        __syncthreads();
+        if (!s_more || t + 1 == max_steps) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *steps_out = t + 1;
+            return;
+        }
+    }
+}
+
 __global__ void k_msssp_init(uint32_t* dist, uint64_t n_vertices) {
     const uint64_t total = n_vertices * 64u;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x)
@@ -209,6 +254,32 @@ cudaError_t launch_msssp_init(uint32_t* dist, uint64_t n_vertices, const uint32_
 cudaError_t launch_popc(const uint32_t* bits, uint64_t words, unsigned long long* out, cudaStream_t s) {
     k_popc<<<608, 256, 0, s>>>(bits, words, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_msssp_loop(const MsArgs& a, uint32_t* const frontier[3], unsigned long long* changed,
+                              uint64_t words, uint32_t max_steps, GridBar* bar, uint64_t timeout_ns, bool force,
+                              uint32_t* err, uint32_t* steps_out, cudaStream_t s) {
+    if (a.u_end <= a.u_begin || max_steps == 0) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = a.packed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msssp_loop<true>, kMsBlock, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msssp_loop<false>, kMsBlock, 0);
+    if (e != cudaSuccess) return e;
+    const uint64_t resident = (uint64_t)sms * (uint64_t)per_sm;
+    if (resident == 0) return cudaErrorNotSupported;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(msssp_grid(a.u_end - a.u_begin), resident);
+    MsArgs args = a;
+    uint32_t* f0 = frontier[0];
+    uint32_t* f1 = frontier[1];
+    uint32_t* f2 = frontier[2];
+    uint32_t fo = force ? 1u : 0u;
+    void* params[] = {&args, &f0, &f1, &f2, &changed, &words, &max_steps, &bar, &timeout_ns, &fo, &err, &steps_out};
+    return a.packed ? cudaLaunchCooperativeKernel((const void*)k_msssp_loop<true>, dim3(grid), dim3(kMsBlock), params,
+                                                  0, s)
+                    : cudaLaunchCooperativeKernel((const void*)k_msssp_loop<false>, dim3(grid), dim3(kMsBlock), params,
+                                                  0, s);
 }
 
 uint32_t msssp_grid(uint64_t units) {

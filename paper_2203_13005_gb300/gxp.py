@@ -170,7 +170,8 @@ class gxp_batch_report(C.Structure):
                 ("ms_total", C.c_double), ("k1", C.c_double), ("k2", C.c_double), ("k3", C.c_double),
                 ("a", C.c_double), ("model_block_edges", C.c_double), ("model_ms", C.c_double),
                 ("sweep_best_ms", C.c_double), ("edges_per_superstep", C.c_uint64),
-                ("tune_from_cache", C.c_uint64), ("active_edges", C.c_uint64), ("reserved", C.c_uint64 * 4)]
+                ("tune_from_cache", C.c_uint64), ("active_edges", C.c_uint64), ("persistent", C.c_uint64),
+                ("reserved", C.c_uint64 * 3)]
 
 
 class gxp_tune_record(C.Structure):

@@ -42,6 +42,7 @@ def test_batch_resident_64_sources(g12):
     with _ctx(n, src, dst, w) as c:
         dist, rep = c.sssp_batch(sources)
         assert rep["supersteps"] >= 2
+        assert rep["persistent"] == 1   # resident edges: one persistent cooperative launch
     _check(n, src, dst, w, sources, dist)
 
 

@@ -205,6 +205,32 @@ def test_persistent_run_barrier_gives_up(gpu, sssp_graph, algo):
     assert np.array_equal(d, d_ref) and steps == steps_ref
 
 
+def test_persistent_batch_barrier_gives_up(gpu, sssp_graph):
+    """The resident batched SSSP runs all its supersteps in one persistent
+    kernel with a bounded grid barrier between them; under the timeout fault
+    every barrier wait gives up at once: GXP_E_TIMEOUT, then GXP_E_STATE
+    until gxp_destroy, and a fresh context's batch matches the oracle."""
+    n, src, dst, w, d_ref, _ = sssp_graph
+    sources = np.array([0, 1, 2], np.uint32)
+    ctx = gxp.Context(0, fault=gxp.GXP_FAULT_TIMEOUT)
+    ctx.create_graph(n, 1)
+    ctx.load_coo(src, dst, w)
+    with pytest.raises(gxp.GxpError) as ei:
+        ctx.sssp_batch(sources)
+    assert _code(ei) == gxp.GXP_E_TIMEOUT
+    _assert_poisoned(ctx, sssp_graph)
+    ctx.close()
+    with gxp.Context(0) as fresh:
+        fresh.create_graph(n, 1)
+        fresh.load_coo(src, dst, w)
+        dist, rep = fresh.sssp_batch(sources)
+        assert rep["persistent"] == 1
+    assert np.array_equal(dist[:, 0], d_ref)
+    for j, s in enumerate(sources[1:], 1):
+        ref, _, _ = oracle.sssp(n, src, dst, w, int(s))
+        assert np.array_equal(dist[:, j], ref)
+
+
 def test_unknown_fault_kinds_are_ignored(gpu, sssp_graph, monkeypatch):
     monkeypatch.setenv("GXP_FAULT", "nothing:3,alsonothing")
     with gxp.Context(0) as ctx:
