@@ -1211,6 +1211,7 @@ void Engine::seed_frontier(uint32_t source_int) {
     f.list_out = d_list_[step_ & 1];
     f.list_cap = list_cap_;
     f.err = d_err_;
+    f.direction = cfg_.direction;   // a forced push reads the items of an all-vertex seed
     if (n_parts_ > 1 && source_int != kInf) {
         cuda_check(launch_seed_finite((uint32_t)n_vertices_, n_ghost_total_, d_own_[cur_], d_ghost_, d_out_ptr_, f,
                                       d_stats_ + (step_ % kStatRing), stream_), "seed frontier");

@@ -195,10 +195,17 @@ __global__ void __launch_bounds__(256) k_cursor_init(const uint32_t* out_ptr, ui
     for (uint64_t u = (uint64_t)kHot + tid; u < n; u += nt) *cur.of((uint32_t)u, 0u) = out_ptr[u];
 }
 
-// items of one vertex, or of all vertices (source == kInf)
+// items of one vertex, or of all vertices (source == kInf). All vertices:
+// CTA c takes a contiguous chunk of them, sums its items and out-edges,
+// reserves its range of the list with one atomic (one per warp made the list
+// counter the bottleneck: a million same-address atomics at 2^22 slots), then
+// writes the items 256 vertices at a time at block-scanned offsets. Under
+// GXP_DIR_AUTO a superstep whose frontier is every vertex always pulls
+// ((items + edges) * push_div exceeds the edges), so only the counts are
+// recorded and the items are not written.
 __global__ void __launch_bounds__(256) k_seed_frontier(uint32_t n, uint32_t source, const uint32_t* out_ptr,
                                                        const FrontierCfg f, StepStats* st) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (source != kInf) {
         if (blockIdx.x == 0 && threadIdx.x < 32) {
             const uint32_t deg = out_ptr[source + 1] - out_ptr[source];
@@ -206,12 +213,50 @@ __global__ void __launch_bounds__(256) k_seed_frontier(uint32_t n, uint32_t sour
         }
         return;
     }
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
-        const uint64_t v = b + (uint64_t)lane;
-        const bool has = v < n;
-        const uint32_t deg = has ? out_ptr[v + 1] - out_ptr[v] : 0u;
-        frontier_append(has, (uint32_t)v, deg, f, st, lane);
+    __shared__ uint32_t s_items[8], s_edges[8];
+    __shared__ unsigned long long s_base;
+    const uint64_t per = ((((uint64_t)n + gridDim.x - 1) / gridDim.x) + 255) & ~255ull;
+    const uint64_t lo = std::min<uint64_t>(n, (uint64_t)blockIdx.x * per), hi = std::min<uint64_t>(n, lo + per);
+    if (lo >= hi) return;   // uniform over the CTA
+    uint32_t items = 0, edges = 0;
+    for (uint64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const uint32_t deg = out_ptr[v + 1] - out_ptr[v];
+        items += frontier_items(deg);
+        edges += deg;
+    }
+    items = __reduce_add_sync(0xFFFFFFFFu, items);
+    edges = __reduce_add_sync(0xFFFFFFFFu, edges);
+    if (lane == 0) {
+        s_items[warp] = items;
+        s_edges[warp] = edges;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ti = 0, te = 0;
+        for (int w = 0; w < 8; ++w) {
+            ti += s_items[w];
+            te += s_edges[w];
+        }
+        s_base = atomicAdd(&st->list_ne, list_pack(ti, te)) >> 32;
+    }
+    __syncthreads();
+    if (f.direction != GXP_DIR_PUSH) return;   // the first superstep pulls: its list is never read
+    unsigned long long run = s_base;
+    for (uint64_t r0 = lo; r0 < hi; r0 += blockDim.x) {
+        const uint64_t v = r0 + threadIdx.x;
+        const bool has = v < hi;
+        const uint32_t nit = has ? frontier_items(out_ptr[v + 1] - out_ptr[v]) : 0u;
+        const uint32_t incl = warp_inclusive_scan(nit, lane);
+        __syncthreads();   // the previous round's totals are read
+        if (lane == 31) s_items[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, round = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) before += s_items[w];
+            round += s_items[w];
+        }
+        frontier_write(f, run + before, incl, nit, (uint32_t)v, lane);
+        run += round;
     }
 }
 
@@ -336,7 +381,7 @@ cudaError_t launch_seed_frontier(uint32_t n, uint32_t source, const uint32_t* ou
                                  StepStats* stats, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&stats->list_ne, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || n == 0) return e;
-    const uint32_t grid = source != kInf ? 1u : (uint32_t)std::min<uint64_t>(((uint64_t)n + 255) / 256, 152ull * 16);
+    const uint32_t grid = source != kInf ? 1u : (uint32_t)std::min<uint64_t>(((uint64_t)n + 255) / 256, 152ull * 8);
     k_seed_frontier<<<grid, 256, 0, s>>>(n, source, out_ptr, f, stats);
     return cudaGetLastError();
 }

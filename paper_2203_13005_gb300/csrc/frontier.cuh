@@ -14,6 +14,9 @@ __device__ __forceinline__ bool push_chosen(const FrontierCfg& f, const StepStat
     if (f.list_out == nullptr) return false;
     if (f.direction == GXP_DIR_PUSH) return true;
     if (f.direction == GXP_DIR_PULL) return false;
+    // partitions: an exchange that did not list its changed copies leaves an
+    // incomplete frontier, which only a pull may follow
+    if (in->exchanged && !in->list_copies) return false;
     const unsigned long long ne = in->list_ne;
     const unsigned long long work = (ne >> 32) + (ne & 0xFFFFFFFFull);
     return work * (unsigned long long)f.push_div <= f.total_edges;

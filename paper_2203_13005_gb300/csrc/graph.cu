@@ -273,6 +273,17 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_count(const SyncArgs a) {
         a.stats_out->boundary_changed = grand;
         a.stats_out->skipped = grand == 0 ? 1ull : 0ull;
         a.stats_out->exchanged = 1ull;
+        // the next superstep pulls anyway when its frontier would be too much
+        // work to push: its own vertices' items and out-edges, plus at least
+        // one item per changed boundary vertex for the copies that would join
+        // (each has a copy somewhere); then the copies are not listed
+        bool list = a.fc.list_out != nullptr;
+        if (list && a.fc.direction == GXP_DIR_AUTO) {
+            const unsigned long long ne = __ldcg(&a.stats_out->list_ne);
+            list = ((ne >> 32) + (ne & 0xFFFFFFFFull) + grand) * (unsigned long long)a.fc.push_div <=
+                   a.fc.total_edges;
+        }
+        a.stats_out->list_copies = list ? 1ull : 0ull;
         *a.done_ctr = 0u;
     }
 }
@@ -314,29 +325,75 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
 // holds it relaxes its in-edges from that vertex if the next superstep pushes.
 __global__ void k_sync_pull(const SyncArgs a) {
     if (a.stats_out->skipped) return;   // uniform: Section III-B3 skip
-    // the next superstep pulls anyway when its frontier's own vertices alone
-    // are too much work to push: then its cached copies are not listed
-    bool list = a.fc.list_out != nullptr;
-    if (list && a.fc.direction == GXP_DIR_AUTO) {
-        const unsigned long long ne = a.stats_out->list_ne;
-        list = ((ne >> 32) + (ne & 0xFFFFFFFFull)) * (unsigned long long)a.fc.push_div <= a.fc.total_edges;
+    const bool list = a.stats_out->list_copies != 0ull;   // decided by k_sync_count for every CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto pull = [&](uint32_t g) -> bool {   // copy g takes its owner's new value if it changed
+        const uint32_t gid = a.ghost_gid[g];
+        const bool ch = ((a.changed_bits[gid >> 5] >> (gid & 31u)) & 1u) != 0u;
+        // not cached: downloaded when used (lru.cu)
+        if (ch && (!a.cached || (a.cached[g] & 1u))) a.ghost[g] = a.own_val[gid];
+        return ch;
+    };
+    if (!list) {
+        const uint32_t stride = gridDim.x * blockDim.x;
+        for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_pull; g += stride) pull(g);
+        return;
     }
-    const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < a.n_pull; b += stride) {
-        const uint32_t g = b + (uint32_t)lane;
+    // The changed copies join the next frontier. A CTA takes a contiguous
+    // chunk: pass 1 pulls and counts their items, one atomic reserves the
+    // CTA's range of the list (one per warp made the list counter a
+    // same-address bottleneck), pass 2 writes the items 256 copies at a time
+    // at block-scanned offsets.
+    __shared__ uint32_t s_items[8], s_edges[8];
+    __shared__ unsigned long long s_base;
+    const uint64_t per = ((((uint64_t)a.n_pull + gridDim.x - 1) / gridDim.x) + 255) & ~255ull;
+    const uint64_t lo = min((uint64_t)a.n_pull, (uint64_t)blockIdx.x * per), hi = min((uint64_t)a.n_pull, lo + per);
+    if (lo >= hi) return;   // uniform over the CTA
+    auto degree = [&](uint32_t g) { return __ldg(a.out_ptr + a.n_vertices + g + 1) - __ldg(a.out_ptr + a.n_vertices + g); };
+    uint32_t items = 0, edges = 0;
+    for (uint64_t g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+        if (pull((uint32_t)g)) {
+            const uint32_t d = degree((uint32_t)g);
+            items += frontier_items(d);
+            edges += d;
+        }
+    }
+    items = __reduce_add_sync(0xFFFFFFFFu, items);
+    edges = __reduce_add_sync(0xFFFFFFFFu, edges);
+    if (lane == 0) {
+        s_items[warp] = items;
+        s_edges[warp] = edges;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t ti = 0, te = 0;
+        for (int w = 0; w < 8; ++w) {
+            ti += s_items[w];
+            te += s_edges[w];
+        }
+        s_base = ti ? atomicAdd(&a.stats_out->list_ne, list_pack(ti, te)) >> 32 : 0ull;
+    }
+    __syncthreads();
+    unsigned long long run = s_base;
+    for (uint64_t r0 = lo; r0 < hi; r0 += blockDim.x) {
+        const uint64_t g = r0 + threadIdx.x;
         bool ch = false;
-        if (g < a.n_pull) {
+        if (g < hi) {
             const uint32_t gid = a.ghost_gid[g];
             ch = ((a.changed_bits[gid >> 5] >> (gid & 31u)) & 1u) != 0u;
-            // not cached: downloaded when used (lru.cu)
-            if (ch && (!a.cached || (a.cached[g] & 1u))) a.ghost[g] = a.own_val[gid];
         }
-        if (list) {
-            const uint32_t slot = a.n_vertices + g;
-            const uint32_t deg = ch ? __ldg(a.out_ptr + slot + 1) - __ldg(a.out_ptr + slot) : 0u;
-            frontier_append(ch, slot, deg, a.fc, a.stats_out, lane);
+        const uint32_t nit = ch ? frontier_items(degree((uint32_t)g)) : 0u;
+        const uint32_t incl = warp_inclusive_scan(nit, lane);
+        __syncthreads();   // the previous round's totals are read
+        if (lane == 31) s_items[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, round = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) before += s_items[w];
+            round += s_items[w];
         }
+        if (round) frontier_write(a.fc, run + before, incl, nit, a.n_vertices + (uint32_t)g, lane);
+        run += round;
     }
 }
 

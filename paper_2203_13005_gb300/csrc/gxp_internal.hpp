@@ -130,7 +130,12 @@ struct StepStats {
     unsigned long long exchanged;                 // 1 once the superstep's exchange between
                                                   // partitions ran (skipped or not)
     unsigned long long downloads;                 // copies the superstep used that were not cached
-    unsigned long long pad[1];
+    // 1: the exchange lists the changed cached copies in the next frontier.
+    // Decided once by k_sync_count from the own vertices' appends and the
+    // changed boundary vertices: the copies' appends then advance list_ne,
+    // so a test each CTA of k_sync_pull made for itself would see a moving
+    // count and the CTAs could disagree (some copies listed, others not).
+    unsigned long long list_copies;
 };
 __host__ __device__ constexpr unsigned long long list_pack(uint32_t items, uint32_t edges) {
     return ((unsigned long long)items << 32) | edges;
