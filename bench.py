@@ -37,6 +37,7 @@ ITERS = 20
 DAMPING = 0.85
 WL = synth.PAGERANK_RMAT22
 PROFILE = os.path.join(REPO, "profiles", "superstep_pagerank_rmat22.txt")
+PROFILE_CC = os.path.join(REPO, "profiles", "superstep_cc_er24_8parts.txt")
 KERNEL_SRC = os.path.join(REPO, "paper_2203_13005_gb300", "csrc", "sell.cu")
 
 
@@ -62,13 +63,15 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def profiled_traffic():
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source (its sha256 is recorded there); else None."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(profile=None):
+    """Per-launch DRAM bytes from a committed ncu summary (the PageRank one by
+    default), if it was taken on the current kernel source (its sha256 is
+    recorded there); else None."""
+    profile = profile or PROFILE
+    if not os.path.exists(profile):
         return None
     kv = {}
-    for ln in open(PROFILE):
+    for ln in open(profile):
         if ":" in ln and not ln.startswith("#"):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
@@ -495,13 +498,18 @@ def run_cc(args):
     # the superstep kernel alone (k_sell<CC>, events around it on the context's
     # stream) and the whole superstep with its exchange, superstep by superstep
     ctx.begin(gxp.GXP_ALGO_CC)
-    k_ms, s_ms = [], []
+    k_ms, s_ms, sweep = [], [], []
     for _ in range(steps):
+        e0 = ctx.stats()["edges_scanned"]
         ctx.superstep()
         sx = ctx.stats()
         k_ms.append(sx["last_kernel_ms"])
         s_ms.append(sx["last_superstep_ms"])
-    k_us = statistics.mean(k_ms) * 1e3
+        sweep.append(sx["edges_scanned"] - e0 == m)
+    # the roofline's launches are the pull supersteps, each reading every edge;
+    # a push superstep reads only its frontier's out-edges
+    k_sweep = [k for k, f in zip(k_ms, sweep) if f] or k_ms
+    k_us = statistics.mean(k_sweep) * 1e3
     bytes_sweep = 8 * m + 12 * n + n // 4   # source id + gathered label per edge; col_ptr, old, new, bitmap
     peaks = measured_peaks()
     line = {
@@ -515,11 +523,15 @@ def run_cc(args):
         "supersteps": steps, "syncs_done": st["syncs_done"], "syncs_skipped": st["syncs_skipped"],
         "sync_pairs": st["sync_pairs"], "cache_downloads": st["cache_downloads"],
         "superstep_kernel_us": [round(x * 1e3, 1) for x in k_ms],
+        "superstep_reads_every_edge": sweep, "push_supersteps": st["push_supersteps"],
         "superstep_with_sync_us": [round(x * 1e3, 1) for x in s_ms],
         "roofline": {"bound": "hbm", "achieved": bytes_sweep / (k_us * 1e-6) / 1e9, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": bytes_sweep / (k_us * 1e-6) / 1e9 / peaks["hbm_gbs"],
-                     "traffic": None, "peak_source": peaks["source"], "kernel": "k_sell<CC>",
-                     "avg_launch_us": k_us, "algorithmic_bytes_per_launch": bytes_sweep},
+                     "traffic": profiled_traffic(PROFILE_CC) if args.cc_scale == 24 else None,
+                     "peak_source": peaks["source"], "kernel": "k_sell<CC>",
+                     "avg_launch_us": k_us, "algorithmic_bytes_per_launch": bytes_sweep,
+                     "launches_averaged": f"the {len(k_sweep)} pull supersteps (every edge read) "
+                                          f"of {steps}"},
         "gpu_launches": None, "clocks": clk.summary(),
     }
     line.update(cpu)

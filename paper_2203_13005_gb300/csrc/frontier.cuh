@@ -17,6 +17,7 @@ __device__ __forceinline__ bool push_chosen(const FrontierCfg& f, const StepStat
     // partitions: an exchange that did not list its changed copies leaves an
     // incomplete frontier, which only a pull may follow
     if (in->exchanged && !in->list_copies) return false;
+    if (in->unlisted) return false;   // the previous pull did not list its changed vertices
     const unsigned long long ne = in->list_ne;
     const unsigned long long work = (ne >> 32) + (ne & 0xFFFFFFFFull);
     return work * (unsigned long long)f.push_div <= f.total_edges;

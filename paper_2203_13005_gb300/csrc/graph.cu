@@ -276,8 +276,9 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_count(const SyncArgs a) {
         // the next superstep pulls anyway when its frontier would be too much
         // work to push: its own vertices' items and out-edges, plus at least
         // one item per changed boundary vertex for the copies that would join
-        // (each has a copy somewhere); then the copies are not listed
-        bool list = a.fc.list_out != nullptr;
+        // (each has a copy somewhere); then the copies are not listed. Nor
+        // are they when the superstep did not list its own vertices.
+        bool list = a.fc.list_out != nullptr && __ldcg(&a.stats_out->unlisted) == 0ull;
         if (list && a.fc.direction == GXP_DIR_AUTO) {
             const unsigned long long ne = __ldcg(&a.stats_out->list_ne);
             list = ((ne >> 32) + (ne & 0xFFFFFFFFull) + grand) * (unsigned long long)a.fc.push_div <=

@@ -136,6 +136,9 @@ struct StepStats {
     // so a test each CTA of k_sync_pull made for itself would see a moving
     // count and the CTAs could disagree (some copies listed, others not).
     unsigned long long list_copies;
+    // 1: the superstep pulled without listing its changed vertices
+    // (FrontierCfg::list_max_changed), so the next one must pull too
+    unsigned long long unlisted;
 };
 __host__ __device__ constexpr unsigned long long list_pack(uint32_t items, uint32_t edges) {
     return ((unsigned long long)items << 32) | edges;
@@ -156,7 +159,16 @@ struct FrontierCfg {
     uint64_t total_edges;
     uint64_t list_cap;           // items each list holds
     uint32_t* err;               // kErrBounds if a list would overflow (never, for valid graphs)
+    // A pull superstep lists the vertices it changes (the next frontier) only
+    // when the frontier it read was small enough to make a push next likely:
+    // at most this many changed vertices, and items + out-edges within
+    // kListSlack times the push limit. Listing costs a pull superstep an
+    // out-degree load and an item write per changed vertex, which pays only
+    // when the next superstep pushes. kAlwaysList: always list.
+    uint64_t list_max_changed;
 };
+constexpr uint64_t kAlwaysList = ~0ull;
+constexpr uint32_t kListSlack = 4;
 
 
 

@@ -177,16 +177,27 @@ __device__ __forceinline__ void sell_cta(const SellArgs& a, const uint64_t t, co
         unsigned long long* z = reinterpret_cast<unsigned long long*>(a.stats + (t + 2) % kStatRing);
         for (uint32_t i = tid; i < sizeof(StepStats) / 8; i += kSellBlock) z[i] = 0ull;
     }
-    __shared__ bool s_quiet;
+    __shared__ bool s_quiet, s_list;
     if (tid == 0) {
         s_acc[0] = s_acc[1] = s_acc[2] = 0ull;
         s_done = 0u;
         s_quiet = false;
+        s_list = true;
     }
-    if (a.early_exit && t > 0 && warp == 0) {
-        // min-label algorithms at a fixed point: nothing can change any more
+    const bool gate = fc.list_out != nullptr && fc.list_max_changed != kAlwaysList;
+    if (((a.early_exit && t > 0) || gate) && warp == 0) {
+        // the vertices the previous superstep changed (this one's frontier)
         const unsigned long long c = warp_sum_u62(stats_in->changed[lane] + stats_in->changed[lane + 32]);
-        if (lane == 0 && c == 0ull) s_quiet = true;
+        if (lane == 0) {
+            // min-label algorithms at a fixed point: nothing can change any more
+            if (a.early_exit && t > 0 && c == 0ull) s_quiet = true;
+            if (gate) {   // the same inputs, so the same choice, in every CTA
+                const unsigned long long ne = stats_in->list_ne;
+                const unsigned long long work = (ne >> 32) + (ne & 0xFFFFFFFFull);
+                s_list = c <= fc.list_max_changed &&
+                         work * (unsigned long long)fc.push_div <= (unsigned long long)kListSlack * fc.total_edges;
+            }
+        }
     }
     // PageRank base terms, from the exact dangling mass of the current ranks
     // (every warp forms them itself: no wait on another warp's loads)
@@ -254,6 +265,8 @@ __device__ __forceinline__ void sell_cta(const SellArgs& a, const uint64_t t, co
                                                                      stats_out, gw, (uint64_t)n_vb * kSellWarps, lane);
             if (lane == 0) n_changed += c;
             pushed = true;
+        } else if (!s_list && vb == 0 && tid == 0) {
+            stats_out->unlisted = 1ull;   // the next superstep pulls
         }
     }
 #pragma unroll 1
@@ -429,7 +442,7 @@ __device__ __forceinline__ void sell_cta(const SellArgs& a, const uint64_t t, co
     }   // work items
 
     if constexpr (A != Algo::PR) {
-        if (fc.list_out && !pushed) {   // uniform over the grid
+        if (fc.list_out && !pushed && s_list) {   // uniform over the grid
             // the changed vertices join the next frontier: one atomic per CTA
             // reserves the CTA's items, each warp writes its own; a vertex's
             // items cover the out-edges of its slot

@@ -39,6 +39,7 @@ def test_traffic_only_while_the_profile_matches_the_kernel(bench, tmp_path, monk
     monkeypatch.setattr(bench, "KERNEL_SRC", str(src))
     monkeypatch.setattr(bench, "PROFILE", str(prof))
     assert bench.profiled_traffic() == 12345.0
+    assert bench.profiled_traffic(str(prof)) == 12345.0
     src.write_text("kernel v2")          # the kernel changed since the counters were taken
     assert bench.profiled_traffic() is None
     monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.txt"))
