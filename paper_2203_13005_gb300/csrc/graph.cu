@@ -305,14 +305,24 @@ __global__ void __launch_bounds__(kSyncBlock) k_sync_write(const SyncArgs a) {
     uint32_t pos = block_excl_scan(__popc(bits), s_warp, total);
     if (P.n_own == 0 || blockIdx.x * kSyncBlock >= w_hi - w_lo) return;
     pos += a.block_offsets[p * a.blocks_x + blockIdx.x] + (uint32_t)a.gdq_base[p];
-    while (bits) {
-        const uint32_t b = __ffs(bits) - 1u;
-        bits &= bits - 1u;
-        const uint32_t gid = w * 32u + b;
-        const uint32_t val = a.own_val[gid];
-        a.gdq_ids[pos] = gid;
-        a.gdq_vals[pos] = val;
-        ++pos;
+    // A warp writes its 32 words' pairs one word at a time, lane l taking the
+    // word's bit l: the word's vertices are 32 consecutive ids, so the value
+    // load is one 128-byte line and the pairs land at consecutive positions
+    // (a thread walking its own word wrote 32 scattered runs per store).
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned todo = __ballot_sync(kFull, bits != 0u);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const uint32_t bj = __shfl_sync(kFull, bits, j);
+        const uint32_t pj = __shfl_sync(kFull, pos, j);
+        const uint32_t wj = __shfl_sync(kFull, w, j);
+        if ((bj >> lane) & 1u) {
+            const uint32_t gid = wj * 32u + lane;
+            const uint32_t at = pj + __popc(bj & ((1u << lane) - 1u));
+            a.gdq_ids[at] = gid;
+            a.gdq_vals[at] = a.own_val[gid];
+        }
     }
 }
 
