@@ -236,7 +236,7 @@ def run_msssp(args):
     _, runs["resident"] = ctx.sssp_batch(sources, out=dist)
     best = runs["streamed_autotuned"]
     sec = best["ms_total"] * 1e-3
-    # roofline of k_msssp on the resident run (SURVEY 8(d)'s bytes: 8 B per
+    # roofline of k_msssp on the resident run (algorithmic bytes: 8 B per
     # scanned edge, 256 B per active edge's row gather, 524 B per vertex per
     # superstep), and the host link of the streamed run against a pinned copy
     peaks = measured_peaks()
