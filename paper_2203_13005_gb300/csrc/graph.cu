@@ -346,8 +346,28 @@ __global__ void k_sync_pull(const SyncArgs a) {
         return ch;
     };
     if (!list) {
-        const uint32_t stride = gridDim.x * blockDim.x;
-        for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_pull; g += stride) pull(g);
+        // four copies per thread and round, their loads issued together: a
+        // thread keeps four independent chains (id -> changed bit -> value)
+        // in flight instead of one
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x, n = a.n_pull;
+        for (uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < n; g0 += 4u * stride) {
+            uint32_t gid[4], word[4], val[4];
+            bool wr[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gid[k] = g0 + k * stride < n ? a.ghost_gid[g0 + k * stride] : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) word[k] = g0 + k * stride < n ? a.changed_bits[gid[k] >> 5] : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t g = g0 + k * stride;
+                // not cached: downloaded when used (lru.cu)
+                wr[k] = g < n && ((word[k] >> (gid[k] & 31u)) & 1u) != 0u && (!a.cached || (a.cached[g] & 1u));
+                val[k] = wr[k] ? a.own_val[gid[k]] : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (wr[k]) a.ghost[g0 + k * stride] = val[k];
+        }
         return;
     }
     // The changed copies join the next frontier. A CTA takes a contiguous
