@@ -173,7 +173,11 @@ typedef struct gxp_config {
  *    min (src-sorted copy of the edges, built at the first gxp_begin that
  *    needs it: 4 bytes per vertex + 4 or 8 bytes per edge);
  *  - AUTO: per superstep on the device, push while the frontier's out-edges
- *    are a small share of all edges (push_div), else pull. */
+ *    are a small share of all edges (push_div), else pull. A push needs the
+ *    previous superstep's changed vertices as a list; with several
+ *    partitions a pull superstep writes that list only when the frontier it
+ *    read was within 4x the push limit, so a frontier that shrinks below the
+ *    limit from above 4x it in one superstep is pulled once more. */
 typedef enum gxp_direction {
     GXP_DIR_AUTO = 0,
     GXP_DIR_PULL = 1,
