@@ -468,6 +468,16 @@ def cpu_cc_baselines(wl, src, dst, n, m) -> dict:
     }, uf
 
 
+def sweep_launch_us(kernel_ms, reads_every_edge):
+    """Average launch time (us) of the supersteps that read every edge, and
+    their count: the roofline's launches are the pull supersteps, since a
+    push superstep reads only its frontier's out-edges. With none, all."""
+    sel = [k for k, f in zip(kernel_ms, reads_every_edge) if f]
+    if not sel:
+        sel = list(kernel_ms)
+    return statistics.mean(sel) * 1e3, len(sel)
+
+
 def run_cc(args):
     """Connected components (min-label propagation) on the Erdős–Rényi graph with
     2^24 vertices and 2^28 directed edges in 8 partitions with sync caching and
@@ -506,10 +516,7 @@ def run_cc(args):
         k_ms.append(sx["last_kernel_ms"])
         s_ms.append(sx["last_superstep_ms"])
         sweep.append(sx["edges_scanned"] - e0 == m)
-    # the roofline's launches are the pull supersteps, each reading every edge;
-    # a push superstep reads only its frontier's out-edges
-    k_sweep = [k for k, f in zip(k_ms, sweep) if f] or k_ms
-    k_us = statistics.mean(k_sweep) * 1e3
+    k_us, n_sweep = sweep_launch_us(k_ms, sweep)
     bytes_sweep = 8 * m + 12 * n + n // 4   # source id + gathered label per edge; col_ptr, old, new, bitmap
     peaks = measured_peaks()
     line = {
@@ -530,7 +537,7 @@ def run_cc(args):
                      "traffic": profiled_traffic(PROFILE_CC) if args.cc_scale == 24 else None,
                      "peak_source": peaks["source"], "kernel": "k_sell<CC>",
                      "avg_launch_us": k_us, "algorithmic_bytes_per_launch": bytes_sweep,
-                     "launches_averaged": f"the {len(k_sweep)} pull supersteps (every edge read) "
+                     "launches_averaged": f"the {n_sweep} pull supersteps (every edge read) "
                                           f"of {steps}"},
         "gpu_launches": None, "clocks": clk.summary(),
     }

@@ -64,3 +64,11 @@ def test_clock_summary_flags_throttling(bench):
     assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
     empty = bench.ClockSampler(0)
     assert empty.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_cc_roofline_averages_the_full_sweeps(bench):
+    # the last superstep pushed (a few out-edges): it is not a sweep of every edge
+    us, n = bench.sweep_launch_us([1.2, 1.0, 0.1], [True, True, False])
+    assert n == 2 and abs(us - 1100.0) < 1e-9
+    us, n = bench.sweep_launch_us([0.2, 0.4], [False, False])
+    assert n == 2 and abs(us - 300.0) < 1e-9
